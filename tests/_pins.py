@@ -1,0 +1,252 @@
+"""Pins for the CPU oracle: checks against what the paper and the mathematics fix, none of
+which re-types the oracle's own arithmetic.
+
+Each pin takes an optional ``impl`` (a compiled oracle variant) so that the same battery
+can be run against deliberately broken copies of the oracle (tests/test_oracle_mutants.py).
+Each returns ``(ok: bool, detail: str)``.
+
+Matrices are scaled (x37) where it matters, so that the Arnoldi normalisations gamma are
+far from 1 and a dropped or doubled division by gamma changes the results.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+import gen
+import oracle
+from gen import csr_from_dense, csr_to_dense
+
+EPS = np.finfo(np.float64).eps
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_examples.json")))
+
+
+def scaled_random(n: int, seed: int, scale: float = 37.0):
+    """Well-conditioned non-normal dense matrix scale * (I + 0.3 G / sqrt(n))."""
+    rng = np.random.default_rng(seed)
+    return csr_from_dense(scale * (np.eye(n) + 0.3 * rng.standard_normal((n, n)) / np.sqrt(n)))
+
+
+def arnoldi_relation(A, out) -> float:
+    """||A V_k - V_{k+1} H_{k+1,k}||_F / (||A||_2 ||V_k||_F)  (eq. "arnoldi")."""
+    D = csr_to_dense(A)
+    k = out["ncols"]
+    V, H = out["V"], out["H"]
+    num = np.linalg.norm(D @ V[:, :k] - V[:, :k + 1] @ H[:k + 1, :k])
+    return float(num / (np.linalg.norm(D, 2) * np.linalg.norm(V[:, :k])))
+
+
+def orth_loss(V, k) -> float:
+    """||I - V_k^T V_k||_F."""
+    Vk = V[:, :k]
+    return float(np.linalg.norm(np.eye(k) - Vk.T @ Vk))
+
+
+# --------------------------------------------------------------------------------------
+def pin_spmv(impl=None):
+    """CSR product against the dense product of the same matrix."""
+    A = gen.random_sparse(300, 9, seed=4)
+    x = np.random.default_rng(1).standard_normal(A.n)
+    y = oracle.spmv(A, x, impl=impl)
+    ref = csr_to_dense(A) @ x
+    err = np.abs(y - ref).max() / np.abs(ref).max()
+    return err < 1e-14, f"spmv rel err {err:.3g}"
+
+
+def pin_arnoldi_relation(impl=None):
+    """A V_k = V_{k+1} H_{k+1,k} to 1e-13 relative (Sec. 1 eq. "arnoldi"; Sec. 4 F_k)."""
+    worst = 0.0
+    cases = [(scaled_random(40, 1), 20), (gen.dense_usv(60, 2, 1e-8)[0], 60)]
+    for A, m in cases:
+        r0 = np.random.default_rng(7).standard_normal(A.n)
+        for method, gs in ((oracle.MGS, 1), (oracle.IGS, 1), (oracle.IGS, 2)):
+            out = oracle.arnoldi(A, r0, m, method, gs, impl=impl)
+            if out["ncols"] != m:
+                return False, f"only {out['ncols']} of {m} columns"
+            worst = max(worst, arnoldi_relation(A, out))
+    return worst <= 1e-13, f"worst Arnoldi relation {worst:.3g}"
+
+
+def pin_krylov_qr(impl=None):
+    """H is unique: with V_{k+1} the Q factor (positive R diagonal) of the Krylov matrix
+    [r0, A r0, ..., A^k r0], H_{k+1,k} = V_{k+1}^T A V_k.  LAPACK's Householder QR gives an
+    independent reference for every entry and sign of H."""
+    A = scaled_random(30, 3)
+    D = csr_to_dense(A)
+    r0 = np.random.default_rng(5).standard_normal(30)
+    k = 6
+    K = np.column_stack([np.linalg.matrix_power(D, i) @ r0 for i in range(k + 1)])
+    Q, R = np.linalg.qr(K)
+    Q = Q * np.sign(np.diag(R))[None, :]
+    Href = Q.T @ D @ Q[:, :k]
+    worst = 0.0
+    for method, gs in ((oracle.MGS, 1), (oracle.IGS, 1), (oracle.IGS, 2)):
+        out = oracle.arnoldi(A, r0, k, method, gs, impl=impl)
+        err = np.linalg.norm(out["H"][:k + 1, :k] - Href) / np.linalg.norm(Href)
+        vd = np.linalg.norm(out["V"][:, :k + 1] - Q)
+        worst = max(worst, err, vd)
+    return worst <= 1e-9, f"H / V vs Krylov QR {worst:.3g}"
+
+
+def pin_L_is_gram(impl=None):
+    """The algorithm's L equals strict_lower(V^T V) (Sec. 4: V_k^T V_k = I + L_k + L_k^T;
+    eq. "katvec" gives its last row)."""
+    worst = 0.0
+    for A, m, gs in ((scaled_random(40, 6), 25, 1), (scaled_random(40, 6), 25, 2),
+                     (gen.dense_usv(60, 3, 1e-9)[0], 60, 1), (gen.dense_usv(60, 3, 1e-9)[0], 60, 2)):
+        r0 = np.random.default_rng(8).standard_normal(A.n)
+        out = oracle.arnoldi(A, r0, m, oracle.IGS, gs, impl=impl)
+        k = out["ncols"] + 1
+        V = out["V"][:, :k]
+        ref = np.tril(V.T @ V, -1)
+        worst = max(worst, float(np.abs(out["L"][:k, :k] - ref).max()))
+    return worst <= 1e-14, f"max |L - strict_lower(V^T V)| {worst:.3g}"
+
+
+def pin_orthogonality_two_gs(impl=None):
+    """Two Gauss-Seidel iterations keep ||I - V_k^T V_k||_F at O(eps) (Sec. 3, 2-iteration
+    bound; abstract) even for kappa(A) = 1e10 and k = n = 200: threshold 1e-13."""
+    A, b, _, _ = gen.dense_usv(200, 0)
+    out = oracle.arnoldi(A, b, 200, oracle.IGS, 2, impl=impl)
+    loss = orth_loss(out["V"], 200)
+    smin = np.linalg.svd(out["V"][:, :200], compute_uv=False)[-1]
+    return loss <= 1e-13 and smin >= 1 - 1e-12, f"||I-V^TV||_F {loss:.3g}, sigma_min {smin:.16f}"
+
+
+def pin_orthogonality_one_gs(impl=None):
+    """One Gauss-Seidel iteration: loss of orthogonality bounded by O(eps) kappa(B_k)
+    (Sec. 3 eq. "onesteploo"): ||I - V_k^T V_k||_F <= eps kappa(B_k) for every k, and
+    clearly above the two-iteration level on an ill-conditioned input."""
+    A, b, _, _ = gen.dense_usv(80, 1, 1e-8)
+    D = csr_to_dense(A)
+    out = oracle.arnoldi(A, b, 80, oracle.IGS, 1, impl=impl)
+    worst = 0.0
+    for k in range(2, 81):
+        kB = np.linalg.cond(np.column_stack([b, D @ out["V"][:, :k]]))
+        worst = max(worst, orth_loss(out["V"], k) / (EPS * kB))
+    final = orth_loss(out["V"], 80)
+    return worst <= 1.0 and final > 1e-10, f"max loss/(eps kappa(B_k)) {worst:.3g}, final {final:.3g}"
+
+
+def pin_givens_lstsq(impl=None):
+    """Givens least squares (eq. "llse") against LAPACK lstsq on random Hessenberg
+    matrices; the residual against ||rho e1 - H y|| evaluated directly."""
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for p in (1, 2, 5, 13, 20):
+        H = np.triu(rng.standard_normal((p + 1, p)), -1)
+        rho = 3.7
+        e1 = np.zeros(p + 1)
+        e1[0] = rho
+        y, res = oracle.hessenberg_lsq(H, p, rho, impl=impl)
+        yref = np.linalg.lstsq(H, e1, rcond=None)[0]
+        rref = np.linalg.norm(e1 - H @ yref)
+        worst = max(worst, np.linalg.norm(y - yref) / np.linalg.norm(yref),
+                    abs(res - rref) / rho)
+    return worst <= 1e-12, f"lstsq mismatch {worst:.3g}"
+
+
+def pin_kn_exact(impl=None):
+    """k = n GMRES on a nonsingular matrix returns A^{-1} b (LAPACK solve) and beta at the
+    rounding level (eq. "nrbe")."""
+    rng = np.random.default_rng(12)
+    n = 40
+    U = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    W = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    D = 11.0 * (U * np.linspace(1, 10, n)[None, :]) @ W.T
+    A = csr_from_dense(D)
+    b = rng.standard_normal(n)
+    xref = np.linalg.solve(D, b)
+    ok, detail = True, []
+    for method, gs in ((oracle.MGS, 1), (oracle.IGS, 1), (oracle.IGS, 2)):
+        out = oracle.gmres(A, b, m=n, method=method, gs=gs, tol=0.0, max_cycles=1,
+                           normA=float(np.linalg.norm(D, 2)), impl=impl)
+        err = np.linalg.norm(out["x"] - xref) / np.linalg.norm(xref)
+        ok &= err <= 1e-12 and out["beta"] <= 1e-15
+        detail.append(f"{method}/{gs}: x err {err:.2g} beta {out['beta']:.2g}")
+    return ok, "; ".join(detail)
+
+
+def pin_backward_error_closed_forms(impl=None):
+    """beta(0) = 1 exactly, and beta = 0 exactly for an exactly representable solution
+    (integer A, x and b = A x)."""
+    A = csr_from_dense(np.array([[2.0, 1.0, 0.0], [0.0, 3.0, -1.0], [4.0, 0.0, 5.0]]))
+    x = np.array([1.0, -2.0, 3.0])
+    b = csr_to_dense(A) @ x
+    b0 = oracle.backward_error(A, b, np.zeros(3), 6.0, impl=impl)
+    bx = oracle.backward_error(A, b, x, 6.0, impl=impl)
+    return b0 == 1.0 and bx == 0.0, f"beta(0)={b0!r}, beta(x*)={bx!r}"
+
+
+def pin_simoncini(impl=None):
+    """Simoncini-Szyld diagonal (Sec. 5): the MGS Arnoldi residual stagnates near 1e-12
+    (paper: 1e-12 after 75 iterations) while IGS with two iterations keeps decreasing far
+    below eps (no stagnation)."""
+    g = GOLDEN["simoncini"]
+    ok, det = True, []
+    for seed in range(3):
+        A, b, _, _ = gen.simoncini(seed)
+        mg = oracle.gmres(A, b, m=100, method=oracle.MGS, tol=0.0, max_cycles=1, normA=g["normA"], impl=impl)
+        ig = oracle.gmres(A, b, m=100, method=oracle.IGS, gs=2, tol=0.0, max_cycles=1, normA=g["normA"], impl=impl)
+        mres = mg["hist_res"] / np.linalg.norm(b)
+        ires = ig["hist_res"] / np.linalg.norm(b)
+        stag = mres[g["mgs_stagnation_after_iter"]:].min()
+        mono = np.all(np.diff(ires) <= 1e-300 + 1e-12 * ires[:-1])
+        ok &= (g["mgs_stagnation_level"] / 10 <= stag <= g["mgs_stagnation_level"] * 10
+               and ires.min() <= 1e-15 and mono)
+        det.append(f"seed {seed}: MGS floor {stag:.2g}, IGS-2 min {ires.min():.2g}, monotone {mono}")
+    return ok, "; ".join(det)
+
+
+def pin_walker(impl=None):
+    """Walker's matrix, alpha = 2000 (Sec. 5): two GS iterations keep O(eps)
+    orthogonality and the Arnoldi residual decreases to far below eps, while MGS's
+    stagnates above it."""
+    A, b, _, _ = gen.walker(10, GOLDEN["walker"]["alpha"])
+    D = csr_to_dense(A)
+    normA = float(np.linalg.norm(D, 2))
+    out = oracle.arnoldi(A, b, 10, oracle.IGS, 2, impl=impl)
+    loss = orth_loss(out["V"], 10)
+    ig = oracle.gmres(A, b, m=10, method=oracle.IGS, gs=2, tol=0.0, max_cycles=1, normA=normA, impl=impl)
+    mg = oracle.gmres(A, b, m=10, method=oracle.MGS, tol=0.0, max_cycles=1, normA=normA, impl=impl)
+    nb = np.linalg.norm(b)
+    ok = loss <= 1e-13 and ig["hist_res"].min() / nb <= 1e-15 and mg["hist_res"].min() / nb >= 1e-14
+    return ok, (f"IGS-2 orth {loss:.2g}, IGS-2 min res {ig['hist_res'].min()/nb:.2g}, "
+                f"MGS min res {mg['hist_res'].min()/nb:.2g}")
+
+
+def pin_embree(impl=None):
+    """Embree delta = 0.1 bidiagonal (Sec. 5): IGS-2 converges in 16 iterations
+    (Arnoldi relative residual <= 1e-16 by iteration 16 +- 2) with O(eps) orthogonality."""
+    g = GOLDEN["embree"]
+    A, b, _, _ = gen.embree(100, g["delta"])
+    out = oracle.gmres(A, b, m=40, method=oracle.IGS, gs=2, tol=0.0, max_cycles=1, normA=1.1, impl=impl)
+    res = out["hist_res"] / np.linalg.norm(b)
+    it = int(np.argmax(res <= 1e-16)) + 1
+    arn = oracle.arnoldi(A, b, 40, oracle.IGS, 2, impl=impl)
+    loss = orth_loss(arn["V"], 40)
+    ok = abs(it - g["iterations_to_converge"]) <= 2 and loss <= 1e-13
+    return ok, f"converged at iteration {it}, orth {loss:.2g}"
+
+
+def pin_mgs_equals_igs1_early(impl=None):
+    """In exact arithmetic one Gauss-Seidel iteration is MGS (Ruhe, Sec. 2): the H columns
+    of IGS-1 agree with MGS's to 1e-12 while kappa(B_k) < 1e4 (rounding differences grow
+    like eps kappa(B_k))."""
+    A = scaled_random(50, 9)
+    D = csr_to_dense(A)
+    r0 = np.random.default_rng(9).standard_normal(50)
+    a = oracle.arnoldi(A, r0, 15, oracle.MGS, 1, impl=impl)
+    b = oracle.arnoldi(A, r0, 15, oracle.IGS, 1, impl=impl)
+    k = 0
+    while k < 15 and np.linalg.cond(np.column_stack([r0, D @ a["V"][:, :k + 1]])) < 1e4:
+        k += 1
+    err = np.linalg.norm(a["H"][:, :k] - b["H"][:, :k]) / np.linalg.norm(a["H"][:, :k])
+    return k >= 3 and err <= 1e-12, f"{k} columns with kappa(B) < 1e4: rel diff {err:.3g}"
+
+
+ALL_PINS = [pin_spmv, pin_arnoldi_relation, pin_krylov_qr, pin_L_is_gram, pin_orthogonality_two_gs,
+            pin_orthogonality_one_gs, pin_givens_lstsq, pin_kn_exact, pin_backward_error_closed_forms,
+            pin_simoncini, pin_walker, pin_embree, pin_mgs_equals_igs1_early]

@@ -1,0 +1,171 @@
+/*
+ * igs.h -- C interface of the GB300 (sm_103a) IGS-GMRES library.
+ *
+ * IGS-GMRES is GMRES (Saad and Schultz) whose Arnoldi process orthogonalises each new
+ * Krylov vector with one or two iterations of Gauss-Seidel on the normal equations of the
+ * Gram-Schmidt projector (Thomas, Carson, Rozloznik, Carr, Swirydowicz, "Iterated
+ * Gauss-Seidel GMRES", arXiv 2205.07805: Sec. 1 states the problem, Alg. 4.1 the method).
+ * All arithmetic is IEEE binary64 on the GPU.
+ *
+ * Conventions shared by every call
+ *  - Return value: one of the IGS_* status codes below; no call throws or aborts.
+ *  - Ownership: the caller owns every pointer it passes; the library never frees or keeps
+ *    one after the call returns (igs_create copies A).
+ *  - Host/device: a flag names whether vector arguments are host or device (CUDA) memory.
+ *    Device pointers must live on the context's device.
+ *  - Layouts: vectors are dense float64 arrays of length n.  Matrices returned to the caller
+ *    are column-major with the stated leading dimension.
+ *  - Streams: all GPU work of a context is ordered on one CUDA stream (given at create, or
+ *    a private one).  Every call below returns only after its results are complete.
+ *  - Thread safety: calls on different contexts may run concurrently; calls on one context
+ *    must be serialised by the caller.
+ */
+#ifndef IGS_H
+#define IGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------------------------- */
+/* Status codes                                                                         */
+/* ----------------------------------------------------------------------------------- */
+enum {
+    IGS_OK = 0,             /* converged: beta(x) <= tol_beta                              */
+    IGS_NOT_CONVERGED = 1,  /* max_restarts cycles ran; x is the last iterate                */
+    IGS_BREAKDOWN = 2,      /* invariant Krylov subspace reached with beta(x) > tol; x valid  */
+    IGS_EINVAL = -1,        /* invalid argument (null pointer, bad size, malformed CSR)       */
+    IGS_ENOMEM = -2,        /* device or host allocation failed                               */
+    IGS_ECUDA = -3,         /* a CUDA runtime call failed (igs_last_error has the text)       */
+    IGS_ENUMERIC = -4,      /* NaN or Inf met (e.g. in b, A or a normalisation)              */
+    IGS_ETIMEOUT = -5,      /* a bounded device-side wait gave up                             */
+    IGS_ENOTIMPL = -6       /* option not supported by this build                             */
+};
+
+/* Orthogonalisation method of an Arnoldi cycle. */
+enum { IGS_METHOD_IGS = 1 };
+
+typedef struct igs_ctx igs_ctx;
+
+/* Options of igs_create (a null pointer means all defaults). */
+typedef struct {
+    void *stream;       /* cudaStream_t to run on; NULL: the library creates a private
+                           non-blocking stream                                            */
+    int device;         /* CUDA device ordinal; < 0: the device current on the calling thread */
+    int max_restart_m;  /* largest restart length m of any later solve; sizes the Krylov basis
+                           (n x (m+1) float64).  <= 0: 100                                  */
+    double A_norm2;     /* ||A||_2 used by the backward error beta (eq. "nrbe", Sec. 1); <= 0:
+                           estimated on the GPU by power iteration on A^T A                 */
+    int norm2_iters;    /* power iterations for that estimate; <= 0: 100                     */
+} igs_create_opts;
+
+/* Options of igs_solve. */
+typedef struct {
+    int restart_m;        /* m, Arnoldi columns per cycle: 1 <= m <= max_restart_m         */
+    int gs_iters;         /* Gauss-Seidel iterations per column: 1 or 2 (Alg. 4.1; with 1,
+                             steps 14-16 are skipped)                                       */
+    double tol_beta;      /* stop when beta(x) <= tol_beta; 0 runs max_restarts full cycles  */
+    int max_restarts;     /* at most this many cycles (>= 1)                                 */
+    int inputs_on_device; /* 1: b, x0 and res->x are device pointers; 0: host pointers        */
+} igs_solve_opts;
+
+/* Results of igs_solve.  Input fields are marked "in". */
+typedef struct {
+    double *x;            /* in: caller-allocated, n entries (host or device per
+                             inputs_on_device); out: the approximate solution x_m           */
+    double *arnoldi_hist; /* in, nullable host array: out |g_{j+1}| = ||rho e1 - H y||, the
+                             Arnoldi residual norm after each completed column, all cycles   */
+    double *lfro_hist;    /* in, nullable host array: out ||L_{j+1}||_F per completed column
+                             (Henrici departure of I+L, eq. "LOO", Sec. 4)                  */
+    int64_t hist_cap;     /* in: capacity of the two history arrays                          */
+    int64_t hist_len;     /* out: history entries written                                    */
+    double *H;            /* in, nullable host array: out the Hessenberg matrix of the last
+                             cycle, (m+1) x m column-major, leading dimension H_ld           */
+    int H_ld;             /* in: >= m+1 when H is given                                      */
+    double beta;          /* out: beta(x) = ||b - A x|| / (||b|| + ||A||_2 ||x||)            */
+    double rho0;          /* out: ||b - A x0||                                               */
+    int64_t steps;        /* out: Arnoldi columns built over all cycles                      */
+    int cycles;           /* out: cycles run                                                 */
+} igs_result;
+
+/* Context information (igs_get_info). */
+typedef struct {
+    int64_t n, nnz;
+    int max_restart_m;
+    int device;
+    double A_norm2;        /* the value beta uses (given or estimated)                      */
+    int A_norm2_estimated; /* 1 when estimated on the GPU                                   */
+    int64_t device_bytes;  /* device memory held by the context                             */
+} igs_info;
+
+/* ----------------------------------------------------------------------------------- */
+/* Calls                                                                                */
+/* ----------------------------------------------------------------------------------- */
+
+/* Create a solver context for the n x n matrix A given in CSR form (Sec. 1: "A x = b with
+ * A an n x n real matrix").  rowptr (n+1 entries, rowptr[0] = 0, non-decreasing,
+ * rowptr[n] = nnz), colind (nnz entries in [0, n)) and vals (nnz) are HOST arrays; they are
+ * validated, copied to the device and may be freed on return.  The context allocates the
+ * Krylov basis and all workspace here; igs_solve allocates nothing on the device.
+ * Errors: IGS_EINVAL (null pointers, n < 1, nnz < 0, nnz >= 2^31, malformed CSR),
+ * IGS_ENOMEM, IGS_ECUDA, IGS_ENUMERIC (non-finite value).  *out is NULL on error. */
+int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr,
+               const int32_t *colind, const double *vals, const igs_create_opts *opts);
+
+/* Release a context and its device memory.  NULL is accepted. */
+void igs_destroy(igs_ctx *ctx);
+
+/* Solve A x = b by restarted IGS-GMRES(m) (Alg. 4.1, then y_m = argmin ||rho e1 - H y||,
+ * x_m = x_0 + V_m y_m; restart from x_m).  b (n entries) and x0 (n entries, NULL = zero)
+ * follow opts->inputs_on_device.  Within a cycle the run stops early once the estimate
+ * |g_{j+1}| / (||b|| + ||A||_2 ||x0||) <= tol_beta; after each cycle the true beta(x) is
+ * computed on the GPU and decides convergence.
+ * Returns IGS_OK, IGS_NOT_CONVERGED or IGS_BREAKDOWN with res filled (x is always
+ * written), or an error code (res->x unspecified). */
+int igs_solve(igs_ctx *ctx, const double *b, const double *x0, const igs_solve_opts *opts,
+              igs_result *res);
+
+/* Run exactly one Arnoldi cycle (Alg. 4.1 steps 1-18 for k = 3..m+1 plus the final
+ * normalisation of w_{m+1}) on the start vector r0 (n entries) and copy out its factors:
+ *   V: n x (m+1) column-major, leading dimension ldv >= n (nullable),
+ *   H: (m+1) x m column-major, leading dimension m+1 (nullable),
+ *   L: (m+1) x (m+1) row-major; row i holds v_{i+1}^T V_i in columns 0..i-1 (nullable).
+ * on_device selects host or device memory for r0, V, H and L.  *ncols receives the number
+ * of completed Hessenberg columns (< m after a breakdown), *rho = ||r0||.
+ * Returns IGS_OK, IGS_BREAKDOWN or an error code. */
+int igs_arnoldi(igs_ctx *ctx, const double *r0, int m, int gs_iters, int on_device,
+                double *V, int64_t ldv, double *H, double *L, int *ncols, double *rho);
+
+/* y = A x with the context's matrix (n entries each; host or device per on_device). */
+int igs_spmv(igs_ctx *ctx, const double *x, double *y, int on_device);
+
+/* Fill *info.  Returns IGS_OK or IGS_EINVAL. */
+int igs_get_info(const igs_ctx *ctx, igs_info *info);
+
+/* Kernel-class timing.  While enabled, igs_solve and igs_arnoldi record CUDA events around
+ * each kernel launch and accumulate per-class device time.  Classes: 0 SpMV, 1 block
+ * reduction (multi-dot), 2 basis update, 3 small serial steps, 4 cycle set-up/finish. */
+enum { IGS_KCLASS_SPMV = 0, IGS_KCLASS_DOTS = 1, IGS_KCLASS_UPDATE = 2, IGS_KCLASS_SMALL = 3,
+       IGS_KCLASS_CYCLE = 4, IGS_KCLASS_COUNT = 5 };
+typedef struct {
+    double ms[IGS_KCLASS_COUNT];        /* summed device time per class                 */
+    int64_t launches[IGS_KCLASS_COUNT]; /* kernel launches per class                    */
+    double bytes[IGS_KCLASS_COUNT];     /* algorithmic bytes moved per class            */
+    double flops[IGS_KCLASS_COUNT];     /* algorithmic floating-point operations        */
+} igs_profile;
+int igs_profile_enable(igs_ctx *ctx, int enable); /* enabling also clears the counters */
+int igs_profile_get(igs_ctx *ctx, igs_profile *out);
+
+/* Total kernel launches issued by this context since creation (for launch accounting). */
+int64_t igs_launch_count(const igs_ctx *ctx);
+
+/* Text of a status code, and of the last error met by ctx (never NULL). */
+const char *igs_status_string(int status);
+const char *igs_last_error(const igs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGS_H */

@@ -397,7 +397,9 @@ double ora_backward_error(int64_t n, const int64_t *rp, const int32_t *ci, const
     if (!r) return NAN;
     ora_spmv(n, rp, ci, va, x, r);
     for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
-    double beta = ora_nrm2(n, r) / (ora_nrm2(n, b) + normA * ora_nrm2(n, x));
+    /* A zero residual is an exact solution: beta = 0 (also for b = 0, x = 0). */
+    double rn = ora_nrm2(n, r);
+    double beta = rn == 0.0 ? 0.0 : rn / (ora_nrm2(n, b) + normA * ora_nrm2(n, x));
     free(r);
     return beta;
 }

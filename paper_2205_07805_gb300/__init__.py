@@ -1,0 +1,283 @@
+"""Python binding of the GB300 IGS-GMRES library (``include/igs.h``, ``_build/libigs.so``).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA kernels.
+There is no CPU fallback; if the library cannot be loaded, every entry point raises.
+
+Vectors may be numpy arrays (host memory) or CUDA ``torch.Tensor`` objects (device
+memory, float64, contiguous); the library is told which through its ``on_device`` flags.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Any
+
+import numpy as np
+
+__all__ = ["Solver", "IGSError", "load_library", "library_path", "status_string",
+           "OK", "NOT_CONVERGED", "BREAKDOWN", "EINVAL", "ENOMEM", "ECUDA", "ENUMERIC",
+           "KCLASS_NAMES", "EXPORTED_SYMBOLS"]
+
+OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
+EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, ENOTIMPL = -1, -2, -3, -4, -5, -6
+KCLASS_NAMES = ["spmv", "dots", "update", "small", "cycle"]
+
+# Every function declared in include/igs.h.
+EXPORTED_SYMBOLS = ["igs_create", "igs_destroy", "igs_solve", "igs_arnoldi", "igs_spmv",
+                    "igs_get_info", "igs_profile_enable", "igs_profile_get", "igs_launch_count",
+                    "igs_status_string", "igs_last_error"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "_build", "libigs.so")
+
+
+class IGSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class _CreateOpts(C.Structure):
+    _fields_ = [("stream", C.c_void_p), ("device", C.c_int), ("max_restart_m", C.c_int),
+                ("A_norm2", C.c_double), ("norm2_iters", C.c_int)]
+
+
+class _SolveOpts(C.Structure):
+    _fields_ = [("restart_m", C.c_int), ("gs_iters", C.c_int), ("tol_beta", C.c_double),
+                ("max_restarts", C.c_int), ("inputs_on_device", C.c_int)]
+
+
+class _Result(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("arnoldi_hist", C.c_void_p), ("lfro_hist", C.c_void_p),
+                ("hist_cap", C.c_int64), ("hist_len", C.c_int64), ("H", C.c_void_p),
+                ("H_ld", C.c_int), ("beta", C.c_double), ("rho0", C.c_double),
+                ("steps", C.c_int64), ("cycles", C.c_int)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("max_restart_m", C.c_int),
+                ("device", C.c_int), ("A_norm2", C.c_double), ("A_norm2_estimated", C.c_int),
+                ("device_bytes", C.c_int64)]
+
+
+class _Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 5), ("launches", C.c_int64 * 5), ("bytes", C.c_double * 5),
+                ("flops", C.c_double * 5)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libigs.so (built by ``paper_2205_07805_gb300.build``).  Raises if missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library not built: {p} is missing (run paper_2205_07805_gb300.build.build())")
+    lib = C.CDLL(p)
+    vp, i64, dbl, i32 = C.c_void_p, C.c_int64, C.c_double, C.c_int
+    lib.igs_create.argtypes = [C.POINTER(vp), i64, i64, vp, vp, vp, C.POINTER(_CreateOpts)]
+    lib.igs_create.restype = i32
+    lib.igs_destroy.argtypes = [vp]
+    lib.igs_destroy.restype = None
+    lib.igs_solve.argtypes = [vp, vp, vp, C.POINTER(_SolveOpts), C.POINTER(_Result)]
+    lib.igs_solve.restype = i32
+    lib.igs_arnoldi.argtypes = [vp, vp, i32, i32, i32, vp, i64, vp, vp, C.POINTER(i32), C.POINTER(dbl)]
+    lib.igs_arnoldi.restype = i32
+    lib.igs_spmv.argtypes = [vp, vp, vp, i32]
+    lib.igs_spmv.restype = i32
+    lib.igs_get_info.argtypes = [vp, C.POINTER(_Info)]
+    lib.igs_get_info.restype = i32
+    lib.igs_profile_enable.argtypes = [vp, i32]
+    lib.igs_profile_enable.restype = i32
+    lib.igs_profile_get.argtypes = [vp, C.POINTER(_Profile)]
+    lib.igs_profile_get.restype = i32
+    lib.igs_launch_count.argtypes = [vp]
+    lib.igs_launch_count.restype = i64
+    lib.igs_status_string.argtypes = [i32]
+    lib.igs_status_string.restype = C.c_char_p
+    lib.igs_last_error.argtypes = [vp]
+    lib.igs_last_error.restype = C.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load_library().igs_status_string(code).decode()
+
+
+def _is_tensor(x: Any) -> bool:
+    return type(x).__module__.startswith("torch") and hasattr(x, "data_ptr")
+
+
+def _vec_arg(x, n: int, name: str):
+    """(pointer, on_device, keepalive) for a float64 vector of length n."""
+    if _is_tensor(x):
+        import torch
+        if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous() or x.numel() != n:
+            raise ValueError(f"{name}: need a contiguous CUDA float64 tensor of length {n}")
+        return C.c_void_p(x.data_ptr()), True, x
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    if a.shape != (n,):
+        raise ValueError(f"{name}: need shape ({n},), got {a.shape}")
+    return C.c_void_p(a.ctypes.data), False, a
+
+
+class Solver:
+    """IGS-GMRES solver context for one sparse matrix (``igs_create``).
+
+    ``A`` is any object with ``n``, ``rowptr`` (int64, n+1), ``colind`` (int32) and ``val``
+    (float64) attributes, or a tuple ``(n, rowptr, colind, val)``."""
+
+    def __init__(self, A, max_restart_m: int = 100, A_norm2: float | None = None,
+                 device: int = 0, stream: int | None = None, norm2_iters: int = 100):
+        self._lib = load_library()
+        if isinstance(A, tuple):
+            n, rowptr, colind, val = A
+        else:
+            n, rowptr, colind, val = A.n, A.rowptr, A.colind, A.val
+        self.n = int(n)
+        rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(colind, dtype=np.int32)
+        va = np.ascontiguousarray(val, dtype=np.float64)
+        opts = _CreateOpts(C.c_void_p(stream) if stream else None, int(device), int(max_restart_m),
+                           float(A_norm2) if A_norm2 else 0.0, int(norm2_iters))
+        h = C.c_void_p()
+        rc = self._lib.igs_create(C.byref(h), self.n, int(rp[-1]), C.c_void_p(rp.ctypes.data),
+                                  C.c_void_p(ci.ctypes.data), C.c_void_p(va.ctypes.data), C.byref(opts))
+        if rc != OK:
+            raise IGSError(rc, "igs_create: " + self._lib.igs_last_error(None).decode())
+        self._h = h
+        self.max_restart_m = int(max_restart_m)
+
+    # ------------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.igs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _err(self, rc: int, what: str):
+        raise IGSError(rc, f"{what}: {self._lib.igs_status_string(rc).decode()}: "
+                           f"{self._lib.igs_last_error(self._h).decode()}")
+
+    @property
+    def info(self) -> dict:
+        inf = _Info()
+        self._lib.igs_get_info(self._h, C.byref(inf))
+        return {k: getattr(inf, k) for k, _ in _Info._fields_}
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.igs_launch_count(self._h))
+
+    # ------------------------------------------------------------------------------
+    def solve(self, b, x0=None, m: int = 30, gs: int = 2, tol: float = 1e-13,
+              max_restarts: int = 10, x_out=None, hist_cap: int | None = None,
+              want_H: bool = False) -> dict:
+        """Restarted IGS-GMRES(m) (``igs_solve``).  Returns ``dict(x, status, beta, rho0,
+        steps, cycles, hist_res, hist_lfro[, H])``.  With a CUDA tensor ``b`` the inputs and
+        ``x`` stay on the device."""
+        bp, dev, kb = _vec_arg(b, self.n, "b")
+        if x0 is not None:
+            xp, dev0, kx = _vec_arg(x0, self.n, "x0")
+            if dev0 != dev:
+                raise ValueError("b and x0 must both be host or both be device arrays")
+        else:
+            xp, kx = None, None
+        if x_out is None:
+            if dev:
+                import torch
+                x_out = torch.empty(self.n, dtype=torch.float64, device=b.device)
+            else:
+                x_out = np.empty(self.n)
+        op, devo, ko = _vec_arg(x_out, self.n, "x_out")
+        if devo != dev:
+            raise ValueError("x_out must live where b lives")
+        cap = hist_cap if hist_cap is not None else m * max_restarts
+        hres = np.full(max(cap, 1), np.nan)
+        hlf = np.full(max(cap, 1), np.nan)
+        H = np.zeros((m + 1, m), order="F") if want_H else None
+        res = _Result(op, C.c_void_p(hres.ctypes.data), C.c_void_p(hlf.ctypes.data), cap, 0,
+                      C.c_void_p(H.ctypes.data) if want_H else None, m + 1, 0.0, 0.0, 0, 0)
+        opts = _SolveOpts(int(m), int(gs), float(tol), int(max_restarts), 1 if dev else 0)
+        rc = self._lib.igs_solve(self._h, bp, xp, C.byref(opts), C.byref(res))
+        if rc < 0:
+            self._err(rc, "igs_solve")
+        k = int(res.hist_len)
+        out = {"x": x_out, "status": rc, "beta": res.beta, "rho0": res.rho0, "steps": int(res.steps),
+               "cycles": int(res.cycles), "hist_res": hres[:k].copy(), "hist_lfro": hlf[:k].copy()}
+        if want_H:
+            out["H"] = H
+        return out
+
+    def arnoldi(self, r0, m: int, gs: int = 2, V=None, H=None, L=None) -> dict:
+        """One Arnoldi cycle (``igs_arnoldi``).  Host input gives numpy outputs
+        (V: n x (m+1), H: (m+1) x m, L: (m+1) x (m+1) row-major); a CUDA tensor input gives
+        CUDA tensor outputs unless output tensors are passed."""
+        rp, dev, kr = _vec_arg(r0, self.n, "r0")
+        if dev:
+            import torch
+            if V is None:
+                V = torch.zeros((m + 1, self.n), dtype=torch.float64, device=r0.device)  # column j = row j
+            if H is None:
+                H = torch.zeros((m, m + 1), dtype=torch.float64, device=r0.device)
+            if L is None:
+                L = torch.zeros((m + 1, m + 1), dtype=torch.float64, device=r0.device)
+            vptr, hptr, lptr = V.data_ptr(), H.data_ptr(), L.data_ptr()
+        else:
+            V = np.zeros((self.n, m + 1), order="F")
+            H = np.zeros((m + 1, m), order="F")
+            L = np.zeros((m + 1, m + 1))
+            vptr, hptr, lptr = V.ctypes.data, H.ctypes.data, L.ctypes.data
+        ncols = C.c_int(0)
+        rho = C.c_double(0.0)
+        rc = self._lib.igs_arnoldi(self._h, rp, int(m), int(gs), 1 if dev else 0, C.c_void_p(vptr),
+                                   self.n, C.c_void_p(hptr), C.c_void_p(lptr), C.byref(ncols), C.byref(rho))
+        if rc < 0:
+            self._err(rc, "igs_arnoldi")
+        if dev:  # tensors were laid out column-major via transposed shapes
+            V, H = V.T, H.T
+        return {"V": V, "H": H, "L": L, "ncols": ncols.value, "rho": rho.value, "status": rc}
+
+    def spmv(self, x, y=None):
+        """y = A x (``igs_spmv``)."""
+        xp, dev, kx = _vec_arg(x, self.n, "x")
+        if y is None:
+            if dev:
+                import torch
+                y = torch.empty(self.n, dtype=torch.float64, device=x.device)
+            else:
+                y = np.empty(self.n)
+        yp, devy, ky = _vec_arg(y, self.n, "y")
+        rc = self._lib.igs_spmv(self._h, xp, yp, 1 if dev else 0)
+        if rc != OK:
+            self._err(rc, "igs_spmv")
+        return y
+
+    # ------------------------------------------------------------------------------
+    def profile_enable(self, on: bool = True):
+        self._lib.igs_profile_enable(self._h, 1 if on else 0)
+
+    def profile(self) -> dict:
+        p = _Profile()
+        self._lib.igs_profile_get(self._h, C.byref(p))
+        return {name: {"ms": p.ms[i], "launches": int(p.launches[i]), "bytes": p.bytes[i],
+                       "flops": p.flops[i]} for i, name in enumerate(KCLASS_NAMES)}

@@ -1,0 +1,704 @@
+// C interface of the GB300 IGS-GMRES library (declared in include/igs.h).
+//
+// A solve is a host loop over restart cycles.  Each cycle -- Alg. 4.1 steps 1-18 for
+// k = 3..m+1, the final normalisation, the Givens least squares, x_m = x_0 + V_m y_m and the
+// backward error of the new x -- is one CUDA graph launch, captured once per (m, gs) and
+// replayed; every per-step scalar stays in device memory, so the host waits only once per
+// cycle.  The Givens rotation of each completed Hessenberg column runs on a parallel graph
+// branch, overlapping the next basis update; its stop decision is consumed one iteration
+// later, and the cycle's least squares uses exactly the columns up to the stop.
+#include "../../include/igs.h"
+#include "igs_internal.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+using igs::KClass;
+
+struct igs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;  // user-visible ordering stream
+    bool own_stream = false;
+    cudaStream_t cap = nullptr;     // private capture stream
+    cudaStream_t side = nullptr;    // private side stream (Givens branch during capture)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    igs::Workspace w;
+    double normA = 0.0;
+    int normA_est = 0;
+    int64_t device_bytes = 0;
+    std::vector<void *> allocs;
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        int kernels = 0;
+    };
+    std::map<std::pair<int, int>, Graph> graphs;
+    // profiling (eager execution with events)
+    bool profiling = false;
+    igs_profile prof{};
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(igs_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? IGS_ENOMEM : IGS_ECUDA,    \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                        \
+    } while (0)
+
+template <class T>
+int dalloc(igs_ctx *ctx, T **p, size_t count)
+{
+    void *q = nullptr;
+    const size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess)
+        return fail(ctx, IGS_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    e = cudaMemset(q, 0, bytes);
+    if (e != cudaSuccess) {
+        cudaFree(q);
+        return fail(ctx, IGS_ECUDA, "cudaMemset failed: %s", cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(q);
+    ctx->device_bytes += (int64_t)bytes;
+    *p = static_cast<T *>(q);
+    return IGS_OK;
+}
+
+// Issues kernels either while a graph is being captured (count only) or eagerly with
+// CUDA events around every kernel (profiling).
+struct Issuer {
+    igs_ctx *ctx;
+    cudaStream_t s;      // main stream
+    cudaStream_t side;   // Givens branch (== s when not capturing)
+    bool capture;
+    int kernels = 0;
+    struct Pending {
+        cudaEvent_t a, b;
+        int cls;
+        double bytes, flops;
+    };
+    std::vector<Pending> pend;
+
+    template <class F>
+    cudaError_t run(int cls, double bytes, double flops, F &&fn, cudaStream_t on)
+    {
+        ++kernels;
+        if (capture || !ctx->profiling) return fn(on);
+        Pending p{};
+        p.cls = cls;
+        p.bytes = bytes;
+        p.flops = flops;
+        cudaEventCreate(&p.a);
+        cudaEventCreate(&p.b);
+        cudaEventRecord(p.a, on);
+        cudaError_t e = fn(on);
+        cudaEventRecord(p.b, on);
+        pend.push_back(p);
+        return e;
+    }
+    void collect()
+    {
+        for (auto &p : pend) {
+            float ms = 0.f;
+            cudaEventSynchronize(p.b);
+            cudaEventElapsedTime(&ms, p.a, p.b);
+            ctx->prof.ms[p.cls] += ms;
+            ctx->prof.launches[p.cls] += 1;
+            ctx->prof.bytes[p.cls] += p.bytes;
+            ctx->prof.flops[p.cls] += p.flops;
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        pend.clear();
+    }
+};
+
+// Algorithmic traffic / work models (FP64, int32 CSR) used by the profile.
+double spmv_bytes(const igs::Workspace &w) { return 12.0 * w.nnz + 4.0 * (w.n + 1) + 16.0 * w.n; }
+double dots_bytes(const igs::Workspace &w, int p, int nq) { return 8.0 * w.n * (p + nq); }
+double upd_bytes(const igs::Workspace &w, int p) { return 8.0 * w.n * (p + 2); }
+
+// Enqueue one restart cycle (see the file comment).  Precondition: ctx->w.r = b - A x,
+// st->rnorm/xnorm/bnorm set (by the solve set-up or the previous cycle's end).
+cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs)
+{
+    const igs::Workspace &w = ctx->w;
+    cudaStream_t s = is.s;
+    const int64_t ld = w.ld;
+    double *V = w.V;
+    auto col = [&](int c) { return V + (int64_t)c * ld; };
+    cudaError_t e;
+#define RUN(cls, bytes, flops, on, expr)                                          \
+    do {                                                                          \
+        e = is.run((cls), (bytes), (flops), [&](cudaStream_t st_) { (void)st_; return (expr); }, (on)); \
+        if (e != cudaSuccess) return e;                                           \
+    } while (0)
+
+    // Step 1: rho = ||r0||, v1 = r0 / rho.
+    RUN(igs::KC_CYCLE, 0, 0, s, igs::launch_cycle_start(w, 0, st_));
+    RUN(igs::KC_CYCLE, 16.0 * w.n, w.n, s, igs::launch_scale(w, w.r, col(0), 0, false, st_));
+    // Step 2: w2 = A v1, H11 = v1^T w2, w2 -= H11 v1.
+    igs::DotsPlan pl{};
+    RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, col(0), col(1), nullptr, false, st_));
+    RUN(igs::KC_DOTS, dots_bytes(w, 1, 1), 2.0 * w.n, s, igs::launch_dots(w, 1, col(1), nullptr, false, st_, &pl));
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_prime(w, pl, st_));
+    RUN(igs::KC_UPDATE, upd_bytes(w, 1), 2.0 * w.n, s,
+        igs::launch_update(w, 1, w.r1v, false, 1.0, col(1), col(1), false, false, false, st_));
+
+    bool pending_join = false;
+    auto join_side = [&]() -> cudaError_t {
+        if (pending_join && is.capture) {
+            cudaError_t ee = cudaStreamWaitEvent(s, ctx->ev_join, 0);
+            if (ee != cudaSuccess) return ee;
+        }
+        pending_join = false;
+        return cudaSuccess;
+    };
+    auto fork_givens = [&](int j) -> cudaError_t {
+        cudaStream_t on = s;
+        if (is.capture) {
+            cudaError_t ee = cudaEventRecord(ctx->ev_fork, s);
+            if (ee == cudaSuccess) ee = cudaStreamWaitEvent(is.side, ctx->ev_fork, 0);
+            if (ee != cudaSuccess) return ee;
+            on = is.side;
+        }
+        cudaError_t ee = is.run(igs::KC_SMALL, 0, 0, [&](cudaStream_t st_) { return igs::launch_givens(w, j, st_); }, on);
+        if (ee != cudaSuccess) return ee;
+        if (is.capture) {
+            ee = cudaEventRecord(ctx->ev_join, is.side);
+            if (ee != cudaSuccess) return ee;
+            pending_join = true;
+        }
+        return cudaSuccess;
+    };
+
+    for (int k = 3; k <= m + 1; ++k) {
+        const int p = k - 1;
+        double *wv = col(p - 1);
+        // Step 4: v_k = A w_{k-1}.
+        RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wv, w.z, nullptr, true, st_));
+        // Step 5: [V_{k-2}, w_{k-1}]^T [w_{k-1}, v_k] (block partial sums).
+        RUN(igs::KC_DOTS, dots_bytes(w, p, 2), 4.0 * w.n * p, s, igs::launch_dots(w, p, wv, w.z, true, st_, &pl));
+        if ((e = join_side()) != cudaSuccess) return e;
+        // Steps 6-12 (+ step 17 for one iteration).
+        RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_a(w, k, gs, pl, st_));
+        // Givens least squares for the column completed by step 6 (column k-2, 1-based).
+        if ((e = fork_givens(k - 3)) != cudaSuccess) return e;
+        // Steps 7, 11, 13: v_{k-1} = w/gamma in place, u_k = v_k/gamma - V_{k-1} r^(1).
+        double *uout = gs == 1 ? col(p) : w.u;
+        RUN(igs::KC_UPDATE, upd_bytes(w, p) + 8.0 * w.n, 2.0 * w.n * p, s,
+            igs::launch_update(w, p, w.r1v, false, 0.0, w.z, uout, true, false, true, st_));
+        if (gs == 2) {
+            // Step 14: r^(2) = V_{k-1}^T u_k.
+            RUN(igs::KC_DOTS, dots_bytes(w, p, 1), 2.0 * w.n * p, s, igs::launch_dots(w, p, w.u, nullptr, true, st_, &pl));
+            // Steps 15, 17.
+            RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_b(w, k, pl, st_));
+            // Step 16: w_k = u_k - V_{k-1} r^(3).
+            RUN(igs::KC_UPDATE, upd_bytes(w, p), 2.0 * w.n * p, s,
+                igs::launch_update(w, p, w.r3v, false, 1.0, w.u, col(p), false, false, true, st_));
+        }
+    }
+    // Flush: gamma_{m+1} = ||w_{m+1}||, H_{m+1,m}, last L row, v_{m+1} = w_{m+1}/gamma.
+    RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
+        igs::launch_dots(w, m + 1, col(m), nullptr, true, st_, &pl));
+    if ((e = join_side()) != cudaSuccess) return e;
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_flush(w, m, pl, st_));
+    RUN(igs::KC_CYCLE, 16.0 * w.n, w.n, s, igs::launch_scale(w, col(m), col(m), 1, true, st_));
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));
+    // Least squares y = argmin ||rho e1 - H y||, x_m = x_0 + V_m y_m.
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_lsq(w, m, st_));
+    RUN(igs::KC_CYCLE, upd_bytes(w, m), 2.0 * w.n * m, s,
+        igs::launch_update(w, 0, w.y, true, 1.0, w.x, w.x, false, true, false, st_));
+    // r = b - A x, ||r||, ||x||, beta(x).
+    RUN(igs::KC_CYCLE, spmv_bytes(w) + 8.0 * w.n, 2.0 * w.nnz, s, igs::launch_spmv(w, w.x, w.r, w.b, false, st_));
+    int nblk = 0;
+    RUN(igs::KC_CYCLE, 16.0 * w.n, 4.0 * w.n, s, igs::launch_norms(w, w.r, w.x, nullptr, &nblk, st_));
+    RUN(igs::KC_CYCLE, 0, 0, s, igs::launch_beta(w, nblk, st_));
+#undef RUN
+    return cudaSuccess;
+}
+
+// Solve-level set-up: state, ||b||, r = b - A x, beta(x).  b and x are already in w.b, w.x.
+cudaError_t enqueue_setup(igs_ctx *ctx, Issuer &is, double tol)
+{
+    const igs::Workspace &w = ctx->w;
+    cudaError_t e;
+    int nblk = 0;
+    e = is.run(igs::KC_CYCLE, 0, 0, [&](cudaStream_t s) { return igs::launch_init_state(w, tol, ctx->normA, s); }, is.s);
+    if (e != cudaSuccess) return e;
+    e = is.run(igs::KC_CYCLE, 8.0 * w.n, 2.0 * w.n, [&](cudaStream_t s) { return igs::launch_norms(w, w.b, nullptr, nullptr, &nblk, s); }, is.s);
+    if (e != cudaSuccess) return e;
+    e = is.run(igs::KC_CYCLE, 0, 0, [&](cudaStream_t s) { return igs::launch_bnorm(w, nblk, s); }, is.s);
+    if (e != cudaSuccess) return e;
+    e = is.run(igs::KC_CYCLE, spmv_bytes(w), 2.0 * w.nnz, [&](cudaStream_t s) { return igs::launch_spmv(w, w.x, w.r, w.b, false, s); }, is.s);
+    if (e != cudaSuccess) return e;
+    e = is.run(igs::KC_CYCLE, 16.0 * w.n, 4.0 * w.n, [&](cudaStream_t s) { return igs::launch_norms(w, w.r, w.x, nullptr, &nblk, s); }, is.s);
+    if (e != cudaSuccess) return e;
+    return is.run(igs::KC_CYCLE, 0, 0, [&](cudaStream_t s) { return igs::launch_beta(w, nblk, s); }, is.s);
+}
+
+int get_graph(igs_ctx *ctx, int m, int gs, igs_ctx::Graph **out)
+{
+    auto key = std::make_pair(m, gs);
+    auto it = ctx->graphs.find(key);
+    if (it != ctx->graphs.end()) {
+        *out = &it->second;
+        return IGS_OK;
+    }
+    Issuer is{ctx, ctx->cap, ctx->side, true};
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_cycle(ctx, is, m, gs);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(ctx, IGS_ECUDA, "capturing the cycle failed: %s", cudaGetErrorString(e));
+    }
+    if (e2 != cudaSuccess) return fail(ctx, IGS_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
+    igs_ctx::Graph gr;
+    e = cudaGraphInstantiate(&gr.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, IGS_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    gr.kernels = is.kernels;
+    auto res = ctx->graphs.emplace(key, gr);
+    *out = &res.first->second;
+    return IGS_OK;
+}
+
+// Run one cycle: replay the graph, or issue eagerly with events when profiling.
+int run_cycle(igs_ctx *ctx, int m, int gs)
+{
+    if (ctx->profiling) {
+        Issuer is{ctx, ctx->stream, ctx->stream, false};
+        cudaError_t e = enqueue_cycle(ctx, is, m, gs);
+        ctx->launches += is.kernels;
+        CK(e);
+        CK(cudaStreamSynchronize(ctx->stream));
+        is.collect();
+        return IGS_OK;
+    }
+    igs_ctx::Graph *g = nullptr;
+    int rc = get_graph(ctx, m, gs, &g);
+    if (rc != IGS_OK) return rc;
+    CK(cudaGraphLaunch(g->exec, ctx->stream));
+    ctx->launches += g->kernels;
+    return IGS_OK;
+}
+
+int run_setup(igs_ctx *ctx, double tol)
+{
+    Issuer is{ctx, ctx->stream, ctx->stream, false};
+    cudaError_t e = enqueue_setup(ctx, is, tol);
+    ctx->launches += is.kernels;
+    CK(e);
+    if (ctx->profiling) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        is.collect();
+    }
+    return IGS_OK;
+}
+
+int copy_vec_in(igs_ctx *ctx, double *dst, const double *src, bool on_device)
+{
+    const size_t bytes = sizeof(double) * (size_t)ctx->w.n;
+    if (!src) {
+        CK(cudaMemsetAsync(dst, 0, bytes, ctx->stream));
+        return IGS_OK;
+    }
+    CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       ctx->stream));
+    return IGS_OK;
+}
+
+int read_state(igs_ctx *ctx, igs::DevState *hs)
+{
+    CK(cudaMemcpyAsync(hs, ctx->w.st, sizeof(igs::DevState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return IGS_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+const char *igs_status_string(int status)
+{
+    switch (status) {
+    case IGS_OK: return "converged";
+    case IGS_NOT_CONVERGED: return "not converged (maximum number of restarts reached)";
+    case IGS_BREAKDOWN: return "breakdown (invariant Krylov subspace; x is valid)";
+    case IGS_EINVAL: return "invalid argument";
+    case IGS_ENOMEM: return "out of memory";
+    case IGS_ECUDA: return "CUDA error";
+    case IGS_ENUMERIC: return "non-finite value met";
+    case IGS_ETIMEOUT: return "device wait timed out";
+    case IGS_ENOTIMPL: return "not implemented";
+    default: return "unknown status";
+    }
+}
+
+const char *igs_last_error(const igs_ctx *ctx)
+{
+    if (!ctx) return g_create_err.c_str();
+    return ctx->err.c_str();
+}
+
+void igs_destroy(igs_ctx *ctx)
+{
+    if (!ctx) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    cudaSetDevice(cur);
+    delete ctx;
+}
+
+int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
+               const double *vals, const igs_create_opts *opts)
+{
+    igs_ctx *ctx = nullptr;
+    if (!out) return fail(nullptr, IGS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!rowptr || (nnz > 0 && (!colind || !vals))) return fail(nullptr, IGS_EINVAL, "null CSR array");
+    if (n < 1 || nnz < 0 || nnz >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31))
+        return fail(nullptr, IGS_EINVAL, "bad sizes n=%lld nnz=%lld", (long long)n, (long long)nnz);
+    if (rowptr[0] != 0 || rowptr[n] != nnz) return fail(nullptr, IGS_EINVAL, "rowptr[0] must be 0 and rowptr[n] = nnz");
+    for (int64_t i = 0; i < n; ++i)
+        if (rowptr[i + 1] < rowptr[i]) return fail(nullptr, IGS_EINVAL, "rowptr decreases at row %lld", (long long)i);
+    for (int64_t q = 0; q < nnz; ++q) {
+        if (colind[q] < 0 || colind[q] >= n) return fail(nullptr, IGS_EINVAL, "column index out of range at %lld", (long long)q);
+        if (!std::isfinite(vals[q])) return fail(nullptr, IGS_ENUMERIC, "non-finite matrix value at %lld", (long long)q);
+    }
+    igs_create_opts o{};
+    o.device = -1;
+    o.max_restart_m = 100;
+    if (opts) o = *opts;
+    if (o.max_restart_m <= 0) o.max_restart_m = 100;
+    if (o.max_restart_m > igs::kMaxRestart)
+        return fail(nullptr, IGS_EINVAL, "max_restart_m %d exceeds %d", o.max_restart_m, igs::kMaxRestart);
+    if (o.norm2_iters <= 0) o.norm2_iters = 100;
+
+    ctx = new igs_ctx();
+    int rc = IGS_OK;
+    auto bail = [&](int code) {
+        if (!ctx->err.empty()) g_create_err = ctx->err;
+        igs_destroy(ctx);
+        return code;
+    };
+    {
+        int dev = o.device;
+        if (dev < 0) {
+            if (cudaGetDevice(&dev) != cudaSuccess) {
+                ctx->err = "no CUDA device";
+                return bail(IGS_ECUDA);
+            }
+        }
+        ctx->device = dev;
+        cudaError_t e = cudaSetDevice(dev);
+        if (e != cudaSuccess) {
+            fail(ctx, IGS_ECUDA, "cudaSetDevice(%d): %s", dev, cudaGetErrorString(e));
+            return bail(IGS_ECUDA);
+        }
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        ctx->w.num_sms = sms > 0 ? sms : 1;
+    }
+    if (o.stream) {
+        ctx->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            ctx->err = "cudaStreamCreate failed";
+            return bail(IGS_ECUDA);
+        }
+        ctx->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        ctx->err = "stream/event creation failed";
+        return bail(IGS_ECUDA);
+    }
+    igs::Workspace &w = ctx->w;
+    w.n = n;
+    w.nnz = nnz;
+    w.ld = (n + 31) & ~int64_t(31);
+    w.mmax = o.max_restart_m;
+    w.spmv_warp_rows = nnz >= 16 * n;
+    const int M = w.mmax;
+    int *rp = nullptr, *ci = nullptr;
+    double *va = nullptr;
+    if ((rc = dalloc(ctx, &rp, (size_t)n + 1)) || (rc = dalloc(ctx, &ci, (size_t)nnz)) ||
+        (rc = dalloc(ctx, &va, (size_t)nnz)) || (rc = dalloc(ctx, &w.V, (size_t)w.ld * (M + 1))) ||
+        (rc = dalloc(ctx, &w.z, (size_t)w.ld)) || (rc = dalloc(ctx, &w.u, (size_t)w.ld)) ||
+        (rc = dalloc(ctx, &w.r, (size_t)w.ld)) || (rc = dalloc(ctx, &w.b, (size_t)w.ld)) ||
+        (rc = dalloc(ctx, &w.x, (size_t)w.ld)) || (rc = dalloc(ctx, &w.t, (size_t)w.ld)) ||
+        (rc = dalloc(ctx, &w.H, (size_t)(M + 1) * M)) || (rc = dalloc(ctx, &w.R, (size_t)(M + 1) * M)) ||
+        (rc = dalloc(ctx, &w.L, (size_t)(M + 1) * (M + 1))) || (rc = dalloc(ctx, &w.cs, (size_t)M)) ||
+        (rc = dalloc(ctx, &w.sn, (size_t)M)) || (rc = dalloc(ctx, &w.g, (size_t)M + 1)) ||
+        (rc = dalloc(ctx, &w.lfro2, (size_t)M + 1)) || (rc = dalloc(ctx, &w.r0v, (size_t)M + 1)) ||
+        (rc = dalloc(ctx, &w.r1v, (size_t)M + 1)) || (rc = dalloc(ctx, &w.r2v, (size_t)M + 1)) ||
+        (rc = dalloc(ctx, &w.r3v, (size_t)M + 1)) || (rc = dalloc(ctx, &w.y, (size_t)M + 1)) ||
+        (rc = dalloc(ctx, &w.hist_res, (size_t)M)) || (rc = dalloc(ctx, &w.hist_lfro, (size_t)M)) ||
+        (rc = dalloc(ctx, &w.st, 1)))
+        return bail(rc);
+    // partial-sum buffer: largest multi-dot launch (two vectors, up to m+1 columns) or norms
+    int64_t cap = 3 * (int64_t)w.num_sms;
+    for (int p = 1; p <= M + 1; ++p) {
+        const igs::DotsPlan pl = igs::plan_dots(w, p);
+        const int64_t need = 2 * (int64_t)p * pl.rblocks;
+        if (need > cap) cap = need;
+    }
+    if ((rc = dalloc(ctx, &w.part, (size_t)cap))) return bail(rc);
+    w.part_cap = cap;
+    {
+        std::vector<int> rp32((size_t)n + 1);
+        for (int64_t i = 0; i <= n; ++i) rp32[(size_t)i] = (int)rowptr[i];
+        cudaError_t e = cudaMemcpy(rp, rp32.data(), sizeof(int) * rp32.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && nnz > 0)
+            e = cudaMemcpy(ci, colind, sizeof(int) * (size_t)nnz, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && nnz > 0)
+            e = cudaMemcpy(va, vals, sizeof(double) * (size_t)nnz, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            fail(ctx, IGS_ECUDA, "copying A: %s", cudaGetErrorString(e));
+            return bail(IGS_ECUDA);
+        }
+    }
+    w.rowptr = rp;
+    w.colind = ci;
+    w.val = va;
+    if (o.A_norm2 > 0.0) {
+        ctx->normA = o.A_norm2;
+    } else {
+        // A^T in CSR (counting sort), uploaded for the power iteration only.
+        std::vector<int> trp((size_t)n + 1, 0), tci((size_t)nnz);
+        std::vector<double> tva((size_t)nnz);
+        for (int64_t q = 0; q < nnz; ++q) trp[(size_t)colind[q] + 1]++;
+        for (int64_t i = 0; i < n; ++i) trp[(size_t)i + 1] += trp[(size_t)i];
+        std::vector<int> pos(trp.begin(), trp.end() - 1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+                const int c = colind[q];
+                tci[(size_t)pos[(size_t)c]] = (int)i;
+                tva[(size_t)pos[(size_t)c]++] = vals[q];
+            }
+        int *d_trp = nullptr, *d_tci = nullptr;
+        double *d_tva = nullptr;
+        cudaError_t e = cudaMalloc(&d_trp, sizeof(int) * (n + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&d_tci, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+        if (e == cudaSuccess) e = cudaMalloc(&d_tva, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+        if (e == cudaSuccess) e = cudaMemcpy(d_trp, trp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(d_tci, tci.data(), sizeof(int) * (size_t)nnz, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(d_tva, tva.data(), sizeof(double) * (size_t)nnz, cudaMemcpyHostToDevice);
+        double est = 0.0;
+        if (e == cudaSuccess) e = igs::estimate_norm2(w, d_trp, d_tci, d_tva, o.norm2_iters, &est, ctx->stream);
+        cudaFree(d_trp);
+        cudaFree(d_tci);
+        cudaFree(d_tva);
+        if (e != cudaSuccess) {
+            fail(ctx, IGS_ECUDA, "norm estimate: %s", cudaGetErrorString(e));
+            return bail(IGS_ECUDA);
+        }
+        ctx->normA = est;
+        ctx->normA_est = 1;
+    }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        ctx->err = "create: stream sync failed";
+        return bail(IGS_ECUDA);
+    }
+    *out = ctx;
+    return IGS_OK;
+}
+
+int igs_get_info(const igs_ctx *ctx, igs_info *info)
+{
+    if (!ctx || !info) return IGS_EINVAL;
+    info->n = ctx->w.n;
+    info->nnz = ctx->w.nnz;
+    info->max_restart_m = ctx->w.mmax;
+    info->device = ctx->device;
+    info->A_norm2 = ctx->normA;
+    info->A_norm2_estimated = ctx->normA_est;
+    info->device_bytes = ctx->device_bytes;
+    return IGS_OK;
+}
+
+int igs_profile_enable(igs_ctx *ctx, int enable)
+{
+    if (!ctx) return IGS_EINVAL;
+    ctx->profiling = enable != 0;
+    if (enable) ctx->prof = igs_profile{};
+    return IGS_OK;
+}
+
+int igs_profile_get(igs_ctx *ctx, igs_profile *out)
+{
+    if (!ctx || !out) return IGS_EINVAL;
+    *out = ctx->prof;
+    return IGS_OK;
+}
+
+int64_t igs_launch_count(const igs_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int igs_spmv(igs_ctx *ctx, const double *x, double *y, int on_device)
+{
+    if (!ctx || !x || !y) return IGS_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    igs::Workspace &w = ctx->w;
+    const size_t bytes = sizeof(double) * (size_t)w.n;
+    const double *xd = x;
+    double *yd = y;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(w.t, x, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        xd = w.t;
+        yd = w.z;
+    }
+    CK(igs::launch_spmv(w, xd, yd, nullptr, false, ctx->stream));
+    ctx->launches += 1;
+    if (!on_device) CK(cudaMemcpyAsync(y, w.z, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return IGS_OK;
+}
+
+int igs_solve(igs_ctx *ctx, const double *b, const double *x0, const igs_solve_opts *opts, igs_result *res)
+{
+    if (!ctx || !b || !opts || !res || !res->x) return ctx ? fail(ctx, IGS_EINVAL, "null argument") : IGS_EINVAL;
+    const int m = opts->restart_m, gs = opts->gs_iters;
+    if (m < 1 || m > ctx->w.mmax) return fail(ctx, IGS_EINVAL, "restart_m %d outside [1, %d]", m, ctx->w.mmax);
+    if (gs != 1 && gs != 2) return fail(ctx, IGS_EINVAL, "gs_iters must be 1 or 2");
+    if (opts->max_restarts < 1) return fail(ctx, IGS_EINVAL, "max_restarts must be >= 1");
+    if (!(opts->tol_beta >= 0.0)) return fail(ctx, IGS_EINVAL, "tol_beta must be >= 0");
+    if (res->H && res->H_ld < m + 1) return fail(ctx, IGS_EINVAL, "H_ld < m+1");
+    CK(cudaSetDevice(ctx->device));
+    igs::Workspace &w = ctx->w;
+    const bool dev = opts->inputs_on_device != 0;
+    int rc;
+    if ((rc = copy_vec_in(ctx, w.b, b, dev)) != IGS_OK) return rc;
+    if ((rc = copy_vec_in(ctx, w.x, x0, dev)) != IGS_OK) return rc;
+    if ((rc = run_setup(ctx, opts->tol_beta)) != IGS_OK) return rc;
+    igs::DevState hs{};
+    if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
+    res->hist_len = 0;
+    res->steps = 0;
+    res->cycles = 0;
+    res->rho0 = hs.rnorm;
+    int status = IGS_NOT_CONVERGED;
+    std::vector<double> hres((size_t)m), hlf((size_t)m);
+    if (!std::isfinite(hs.beta)) {
+        status = IGS_ENUMERIC;
+    } else if (hs.beta <= opts->tol_beta) {
+        status = IGS_OK;
+    } else {
+        for (int cyc = 0; cyc < opts->max_restarts; ++cyc) {
+            if ((rc = run_cycle(ctx, m, gs)) != IGS_OK) return rc;
+            if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
+            res->cycles += 1;
+            const int nc = hs.ncols;
+            res->steps += nc;
+            if ((res->arnoldi_hist || res->lfro_hist) && nc > 0) {
+                CK(cudaMemcpyAsync(hres.data(), w.hist_res, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaMemcpyAsync(hlf.data(), w.hist_lfro, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+                for (int j = 0; j < nc && res->hist_len < res->hist_cap; ++j) {
+                    if (res->arnoldi_hist) res->arnoldi_hist[res->hist_len] = hres[(size_t)j];
+                    if (res->lfro_hist) res->lfro_hist[res->hist_len] = hlf[(size_t)j];
+                    res->hist_len++;
+                }
+            }
+            if (hs.stop_reason < 0 || !std::isfinite(hs.beta)) {
+                status = IGS_ENUMERIC;
+                break;
+            }
+            if (hs.beta <= opts->tol_beta) {
+                status = IGS_OK;
+                break;
+            }
+            if (hs.stop_reason == 2) {
+                status = IGS_BREAKDOWN;
+                break;
+            }
+        }
+    }
+    const size_t bytes = sizeof(double) * (size_t)w.n;
+    CK(cudaMemcpyAsync(res->x, w.x, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (res->H && res->cycles > 0)
+        CK(cudaMemcpy2DAsync(res->H, sizeof(double) * res->H_ld, w.H, sizeof(double) * w.ldh(),
+                             sizeof(double) * (m + 1), m, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    res->beta = hs.beta;
+    return status;
+}
+
+int igs_arnoldi(igs_ctx *ctx, const double *r0, int m, int gs, int on_device, double *V, int64_t ldv,
+                double *H, double *L, int *ncols, double *rho)
+{
+    if (!ctx || !r0) return ctx ? fail(ctx, IGS_EINVAL, "null argument") : IGS_EINVAL;
+    if (m < 1 || m > ctx->w.mmax) return fail(ctx, IGS_EINVAL, "m %d outside [1, %d]", m, ctx->w.mmax);
+    if (gs != 1 && gs != 2) return fail(ctx, IGS_EINVAL, "gs_iters must be 1 or 2");
+    if (V && ldv < ctx->w.n) return fail(ctx, IGS_EINVAL, "ldv < n");
+    CK(cudaSetDevice(ctx->device));
+    igs::Workspace &w = ctx->w;
+    const int M = w.mmax;
+    CK(cudaMemsetAsync(w.H, 0, sizeof(double) * (size_t)(M + 1) * M, ctx->stream));
+    CK(cudaMemsetAsync(w.L, 0, sizeof(double) * (size_t)(M + 1) * (M + 1), ctx->stream));
+    CK(cudaMemsetAsync(w.V, 0, sizeof(double) * (size_t)w.ld * (M + 1), ctx->stream));
+    int rc;
+    if ((rc = copy_vec_in(ctx, w.b, r0, on_device != 0)) != IGS_OK) return rc;
+    if ((rc = copy_vec_in(ctx, w.x, nullptr, false)) != IGS_OK) return rc;
+    if ((rc = run_setup(ctx, 0.0)) != IGS_OK) return rc;
+    if ((rc = run_cycle(ctx, m, gs)) != IGS_OK) return rc;
+    igs::DevState hs{};
+    if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (V)
+        CK(cudaMemcpy2DAsync(V, sizeof(double) * ldv, w.V, sizeof(double) * w.ld, sizeof(double) * w.n,
+                             m + 1, kind, ctx->stream));
+    if (H)
+        CK(cudaMemcpy2DAsync(H, sizeof(double) * (m + 1), w.H, sizeof(double) * w.ldh(),
+                             sizeof(double) * (m + 1), m, kind, ctx->stream));
+    if (L)
+        CK(cudaMemcpy2DAsync(L, sizeof(double) * (m + 1), w.L, sizeof(double) * w.ldl(),
+                             sizeof(double) * (m + 1), m + 1, kind, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ncols) *ncols = hs.ncols;
+    if (rho) *rho = hs.rho;
+    if (hs.stop_reason < 0) return IGS_ENUMERIC;
+    return hs.stop_reason == 2 ? IGS_BREAKDOWN : IGS_OK;
+}
+
+}  // extern "C"

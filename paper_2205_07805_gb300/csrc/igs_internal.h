@@ -1,0 +1,113 @@
+// Internal declarations shared by the kernels (igs_kernels.cu) and the C interface
+// (igs_api.cu) of the GB300 IGS-GMRES library.  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace igs {
+
+// Threads per block of the streaming kernels and of the small single-block kernels.
+constexpr int kStreamThreads = 256;
+constexpr int kSmallThreads = 256;
+constexpr int kGivensThreads = 128;
+// Target columns per block of the multi-dot kernel (few columns per block keep the number of
+// per-block partial sums, which one block must add up afterwards, small).
+constexpr int kDotsColsPerBlock = 4;
+// Resident blocks per SM assumed when sizing grids (256 threads, <= 128 registers).
+constexpr int kBlocksPerSM = 2;
+// Largest restart length supported (shared-memory coefficient arrays are sized from it).
+constexpr int kMaxRestart = 1024;
+// Breakdown threshold factor: gamma <= 64 eps ||H(1:j, j)||.
+constexpr double kBreakdownFactor = 64.0 * 2.220446049250313e-16;
+
+// Scalars of one solve, kept in device memory so that no step needs the host.
+struct DevState {
+    double rho;        // ||r0|| of the current cycle
+    double inv_rho;
+    double inv_gamma;  // 1 / gamma of the current step
+    double stop_den;   // ||b|| + ||A||_2 ||x0|| (in-cycle stop test denominator)
+    double tol;        // tol_beta
+    double normA;      // ||A||_2
+    double bnorm;      // ||b||
+    double rnorm, xnorm, beta;  // end-of-cycle residual norm, ||x||, backward error
+    int halt;          // nonzero: the remaining step kernels of this cycle do nothing
+    int stop_cols;     // > 0: columns the cycle ends with (early stop or breakdown)
+    int stop_reason;   // 0 running, 1 converged, 2 breakdown, -4 numeric error
+    int ncols;         // columns used by the least-squares solve of this cycle
+    int neumann_terms; // terms used by the last (I+L) application (0: substitution)
+    int pad[3];
+};
+
+// Device memory of one context.
+struct Workspace {
+    int64_t n = 0, ld = 0, nnz = 0;
+    int mmax = 0;
+    int num_sms = 0;
+    bool spmv_warp_rows = false;   // warp-per-row SpMV (long rows) instead of thread-per-row
+    const int *rowptr = nullptr, *colind = nullptr;
+    const double *val = nullptr;
+    double *V = nullptr;           // ld x (mmax+1), column-major
+    double *z = nullptr, *u = nullptr, *r = nullptr, *b = nullptr, *x = nullptr, *t = nullptr;
+    double *H = nullptr;           // (mmax+1) x mmax column-major, ldh = mmax+1
+    double *L = nullptr;           // (mmax+1) x (mmax+1) row-major, ldl = mmax+1
+    double *R = nullptr;           // Givens-rotated copy of H, same layout as H
+    double *cs = nullptr, *sn = nullptr, *g = nullptr;  // rotations and rotated rhs
+    double *lfro2 = nullptr;       // cumulative ||L rows 0..i||_F^2, mmax+1 entries
+    double *r0v = nullptr, *r1v = nullptr, *r2v = nullptr, *r3v = nullptr, *y = nullptr;
+    double *part = nullptr;        // per-block partial sums
+    int64_t part_cap = 0;
+    double *hist_res = nullptr, *hist_lfro = nullptr;  // per-cycle history (mmax entries)
+    DevState *st = nullptr;
+    int ldh() const { return mmax + 1; }
+    int ldl() const { return mmax + 1; }
+};
+
+// Launch geometry of the multi-dot kernel for p columns.
+struct DotsPlan {
+    int groups;      // column groups (grid.y)
+    int rblocks;     // row blocks (grid.x)
+    int64_t rows;    // rows per row block (multiple of 4)
+};
+DotsPlan plan_dots(const Workspace &w, int p);
+
+// Kernel classes (match IGS_KCLASS_* in igs.h).
+enum KClass { KC_SPMV = 0, KC_DOTS = 1, KC_UPDATE = 2, KC_SMALL = 3, KC_CYCLE = 4 };
+
+// ---- launchers (enqueue on `s`; return cudaGetLastError()) ----
+// y = A x, or y = b - A x when b != nullptr.
+cudaError_t launch_spmv(const Workspace &w, const double *x, double *y, const double *b,
+                        bool check_halt, cudaStream_t s);
+// Partial sums part[(q*p + c)*rblocks + rb] = sum over row block rb of V[:,c] . X_q, q < nq.
+cudaError_t launch_dots(const Workspace &w, int p, const double *x0, const double *x1,
+                        bool check_halt, cudaStream_t s, DotsPlan *plan_out);
+// out = alpha*src - V[:, 0:p] coef (coef negated when neg_coef); when norm_last, column p-1
+// of V is first scaled in place by st->inv_gamma and alpha is taken as st->inv_gamma.
+// When p_from_state, p = st->ncols.
+cudaError_t launch_update(const Workspace &w, int p, const double *coef, bool neg_coef,
+                          double alpha, const double *src, double *out, bool norm_last,
+                          bool p_from_state, bool check_halt, cudaStream_t s);
+// Partial sums of squares of up to three vectors (part[q*blocks + blk]).
+cudaError_t launch_norms(const Workspace &w, const double *a, const double *b,
+                         const double *c, int *blocks_out, cudaStream_t s);
+// v = scale * w with scale = st->inv_rho (which=0) or st->inv_gamma (which=1).
+cudaError_t launch_scale(const Workspace &w, const double *src, double *dst, int which,
+                         bool check_halt, cudaStream_t s);
+
+// Small single-block steps.
+cudaError_t launch_cycle_start(const Workspace &w, int nblk, cudaStream_t s);
+cudaError_t launch_prime(const Workspace &w, const DotsPlan &pl, cudaStream_t s);
+cudaError_t launch_step_a(const Workspace &w, int k, int gs, const DotsPlan &pl, cudaStream_t s);
+cudaError_t launch_step_b(const Workspace &w, int k, const DotsPlan &pl, cudaStream_t s);
+cudaError_t launch_flush(const Workspace &w, int m, const DotsPlan &pl, cudaStream_t s);
+cudaError_t launch_givens(const Workspace &w, int j, cudaStream_t s);
+cudaError_t launch_lsq(const Workspace &w, int m, cudaStream_t s);
+cudaError_t launch_beta(const Workspace &w, int nblk, cudaStream_t s);
+cudaError_t launch_init_state(const Workspace &w, double tol, double normA, cudaStream_t s);
+cudaError_t launch_bnorm(const Workspace &w, int nblk, cudaStream_t s);
+
+// ||A||_2 estimate: power iteration on A^T A (At in CSR = A^T).
+cudaError_t estimate_norm2(const Workspace &w, const int *at_rowptr, const int *at_colind,
+                           const double *at_val, int iters, double *out, cudaStream_t s);
+
+}  // namespace igs

@@ -44,7 +44,7 @@ MUTANTS = [
     ("priming step skips the projection of w_2",
      "for (int64_t i = 0; i < n; ++i) w2[i] -= h11 * V[i];", ""),
     ("backward error omits ||A|| ||x||",
-     "ora_nrm2(n, r) / (ora_nrm2(n, b) + normA * ora_nrm2(n, x));", "ora_nrm2(n, r) / ora_nrm2(n, b);"),
+     "rn / (ora_nrm2(n, b) + normA * ora_nrm2(n, x));", "rn / ora_nrm2(n, b);"),
 ]
 
 

@@ -161,6 +161,30 @@ int igs_profile_get(igs_ctx *ctx, igs_profile *out);
 /* Total kernel launches issued by this context since creation (for launch accounting). */
 int64_t igs_launch_count(const igs_ctx *ctx);
 
+/* Block multi-dot that allocates no device memory.  The paper has no counterpart: this is a
+ * service for callers that may not call cudaMalloc (a host application that owns all device
+ * memory and forbids plug-ins from allocating; code running while another thread captures
+ * a CUDA graph in global capture mode; loops that cannot take cudaMalloc's implicit device
+ * synchronisation).
+ *   out[c]     = V[:, c]^T x0   for c < p
+ *   out[p + c] = V[:, c]^T x1   for c < p (only when x1 != NULL)
+ * V (n x p column-major, leading dimension ldv), x0, x1 and out are DEVICE pointers on the
+ * current device; V, x0 and x1 must be 16-byte aligned, n a multiple of 4 and ldv even and
+ * >= n.  The work runs on `stream` (a cudaStream_t; NULL = legacy default stream) and the
+ * call returns after it completes.  Same kernel and summation order as the library's
+ * step-5 reduction.
+ * The per-block partial sums live in a fixed file-scope device array of 16384 doubles
+ * (128 KiB) that every GPU loading the library holds until the process exits; a launch
+ * whose partial sums would not fit (more than about 2000 columns) is rejected with
+ * IGS_EINVAL.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  All calls share the array: calls whose GPU work
+ * overlaps race on it.  Nothing in it must start at zero (each call writes every partial it
+ * reads).  Returns IGS_OK, IGS_EINVAL (bad pointer, size, alignment, or too large) or
+ * IGS_ECUDA. */
+int igs_block_dots_static(const double *V, int64_t ldv, int p, int64_t n, const double *x0,
+                          const double *x1, double *out, void *stream);
+
 /* Text of a status code, and of the last error met by ctx (never NULL). */
 const char *igs_status_string(int status);
 const char *igs_last_error(const igs_ctx *ctx);

@@ -25,7 +25,7 @@ KCLASS_NAMES = ["spmv", "dots", "update", "small", "cycle"]
 # Every function declared in include/igs.h.
 EXPORTED_SYMBOLS = ["igs_create", "igs_destroy", "igs_solve", "igs_arnoldi", "igs_spmv",
                     "igs_get_info", "igs_profile_enable", "igs_profile_get", "igs_launch_count",
-                    "igs_status_string", "igs_last_error"]
+                    "igs_status_string", "igs_last_error", "igs_block_dots_static"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -103,6 +103,8 @@ def load_library(path: str | None = None):
     lib.igs_status_string.restype = C.c_char_p
     lib.igs_last_error.argtypes = [vp]
     lib.igs_last_error.restype = C.c_char_p
+    lib.igs_block_dots_static.argtypes = [vp, i64, i32, i64, vp, vp, vp, vp]
+    lib.igs_block_dots_static.restype = i32
     if path is None:
         _lib = lib
     return lib

@@ -54,8 +54,8 @@ typedef struct {
     void *stream;       /* cudaStream_t to run on; NULL: the library creates a private
                            non-blocking stream                                            */
     int device;         /* CUDA device ordinal; < 0: the device current on the calling thread */
-    int max_restart_m;  /* largest restart length m of any later solve; sizes the Krylov basis
-                           (n x (m+1) float64).  <= 0: 100                                  */
+    int max_restart_m;  /* largest restart length m of any later solve, 1..232; sizes the
+                           Krylov basis (n x (m+1) float64).  <= 0: 100                     */
     double A_norm2;     /* ||A||_2 used by the backward error beta (eq. "nrbe", Sec. 1); <= 0:
                            estimated on the GPU by power iteration on A^T A                 */
     int norm2_iters;    /* power iterations for that estimate; <= 0: 100                     */

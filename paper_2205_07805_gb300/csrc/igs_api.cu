@@ -42,6 +42,7 @@ struct igs_ctx {
     bool profiling = false;
     igs_profile prof{};
     int64_t launches = 0;
+    bool fused_update = false;  // fused steps 7/11/13 + step-14 partials (two GS iterations)
     std::string err;
 };
 
@@ -209,6 +210,21 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs)
         RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_a(w, k, gs, pl, st_));
         // Givens least squares for the column completed by step 6 (column k-2, 1-based).
         if ((e = fork_givens(k - 3)) != cudaSuccess) return e;
+        if (gs == 2 && ctx->fused_update && igs::update_dots_fits(p)) {
+            // Steps 7, 11, 13 with the partial sums of step 14 (r^(2) = V_{k-1}^T u_k) in one
+            // pass over V_{k-1}.
+            int ngroups = 0;
+            RUN(igs::KC_UPDATE, upd_bytes(w, p) + 8.0 * w.n, 4.0 * w.n * p, s,
+                igs::launch_update_dots(w, p, w.r1v, w.z, w.u, st_, &ngroups));
+            igs::DotsPlan gp{};
+            gp.rblocks = ngroups;
+            // Steps 15, 17.
+            RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_b(w, k, gp, st_));
+            // Step 16: w_k = u_k - V_{k-1} r^(3).
+            RUN(igs::KC_UPDATE, upd_bytes(w, p), 2.0 * w.n * p, s,
+                igs::launch_update(w, p, w.r3v, false, 1.0, w.u, col(p), false, false, true, st_));
+            continue;
+        }
         // Steps 7, 11, 13: v_{k-1} = w/gamma in place, u_k = v_k/gamma - V_{k-1} r^(1).
         double *uout = gs == 1 ? col(p) : w.u;
         RUN(igs::KC_UPDATE, upd_bytes(w, p) + 8.0 * w.n, 2.0 * w.n * p, s,
@@ -469,7 +485,8 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
         (rc = dalloc(ctx, &w.r, (size_t)w.ld)) || (rc = dalloc(ctx, &w.b, (size_t)w.ld)) ||
         (rc = dalloc(ctx, &w.x, (size_t)w.ld)) || (rc = dalloc(ctx, &w.t, (size_t)w.ld)) ||
         (rc = dalloc(ctx, &w.H, (size_t)(M + 1) * M)) || (rc = dalloc(ctx, &w.R, (size_t)(M + 1) * M)) ||
-        (rc = dalloc(ctx, &w.L, (size_t)(M + 1) * (M + 1))) || (rc = dalloc(ctx, &w.cs, (size_t)M)) ||
+        (rc = dalloc(ctx, &w.L, (size_t)(M + 1) * (M + 1))) ||
+        (rc = dalloc(ctx, &w.Lout, (size_t)(M + 1) * (M + 1))) || (rc = dalloc(ctx, &w.cs, (size_t)M)) ||
         (rc = dalloc(ctx, &w.sn, (size_t)M)) || (rc = dalloc(ctx, &w.g, (size_t)M + 1)) ||
         (rc = dalloc(ctx, &w.lfro2, (size_t)M + 1)) || (rc = dalloc(ctx, &w.r0v, (size_t)M + 1)) ||
         (rc = dalloc(ctx, &w.r1v, (size_t)M + 1)) || (rc = dalloc(ctx, &w.r2v, (size_t)M + 1)) ||
@@ -478,7 +495,12 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
         (rc = dalloc(ctx, &w.st, 1)))
         return bail(rc);
     // partial-sum buffer: largest multi-dot launch (two vectors, up to m+1 columns) or norms
+    // (also holds the fused update's group partials: <= 2*SMs/kFusedGroup + 1 groups x p)
     int64_t cap = 3 * (int64_t)w.num_sms;
+    {
+        const int64_t groups = (2 * (int64_t)w.num_sms + igs::kFusedGroup - 1) / igs::kFusedGroup + 1;
+        if (groups * (M + 1) > cap) cap = groups * (M + 1);
+    }
     for (int p = 1; p <= M + 1; ++p) {
         const igs::DotsPlan pl = igs::plan_dots(w, p);
         const int64_t need = 2 * (int64_t)p * pl.rblocks;
@@ -486,6 +508,10 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
     }
     if ((rc = dalloc(ctx, &w.part, (size_t)cap))) return bail(rc);
     w.part_cap = cap;
+    // fused update: per-block partials (<= 2 blocks per SM) and group counters
+    if ((rc = dalloc(ctx, &w.bpart, (size_t)2 * w.num_sms * (M + 1))) ||
+        (rc = dalloc(ctx, &w.counters, (size_t)(2 * w.num_sms + igs::kFusedGroup - 1) / igs::kFusedGroup + 1)))
+        return bail(rc);
     {
         std::vector<int> rp32((size_t)n + 1);
         for (int64_t i = 0; i <= n; ++i) rp32[(size_t)i] = (int)rowptr[i];
@@ -502,6 +528,13 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
     w.rowptr = rp;
     w.colind = ci;
     w.val = va;
+    {
+        cudaError_t e = igs::configure_kernels(w);
+        if (e != cudaSuccess) {
+            fail(ctx, IGS_ECUDA, "kernel configuration: %s", cudaGetErrorString(e));
+            return bail(IGS_ECUDA);
+        }
+    }
     if (o.A_norm2 > 0.0) {
         ctx->normA = o.A_norm2;
     } else {
@@ -691,9 +724,15 @@ int igs_arnoldi(igs_ctx *ctx, const double *r0, int m, int gs, int on_device, do
     if (H)
         CK(cudaMemcpy2DAsync(H, sizeof(double) * (m + 1), w.H, sizeof(double) * w.ldh(),
                              sizeof(double) * (m + 1), m, kind, ctx->stream));
-    if (L)
-        CK(cudaMemcpy2DAsync(L, sizeof(double) * (m + 1), w.L, sizeof(double) * w.ldl(),
-                             sizeof(double) * (m + 1), m + 1, kind, ctx->stream));
+    if (L) {
+        // the device keeps L column-major; hand it out row-major
+        double *dst = on_device ? L : w.Lout;
+        CK(igs::launch_transpose(w.L, w.ldl(), m + 1, m + 1, dst, m + 1, ctx->stream));
+        ctx->launches += 1;
+        if (!on_device)
+            CK(cudaMemcpyAsync(L, w.Lout, sizeof(double) * (size_t)(m + 1) * (m + 1),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     if (ncols) *ncols = hs.ncols;
     if (rho) *rho = hs.rho;

@@ -16,8 +16,16 @@ constexpr int kGivensThreads = 128;
 constexpr int kDotsColsPerBlock = 4;
 // Resident blocks per SM assumed when sizing grids (256 threads, <= 128 registers).
 constexpr int kBlocksPerSM = 2;
-// Largest restart length supported (shared-memory coefficient arrays are sized from it).
-constexpr int kMaxRestart = 1024;
+// Resident blocks per SM of the multi-dot kernel (256 threads, <= 80 registers).
+constexpr int kDotsBlocksPerSM = 3;
+// Fused update + second reduction: rows per tile (= threads per block), blocks per combine
+// group, and the largest dynamic shared memory it may use (p up to ~216 columns).
+constexpr int kFusedRows = 128;
+constexpr int kFusedGroup = 16;
+constexpr size_t kFusedMaxSmem = 220 * 1024;  // under the 227 KiB opt-in, minus static smem
+// Largest restart length supported.  The small single-block steps hold L_p packed in shared
+// memory: 8 (5p + p(p-1)/2) bytes <= 227 KiB gives p <= 232.
+constexpr int kMaxRestart = 232;
 // Breakdown threshold factor: gamma <= 64 eps ||H(1:j, j)||.
 constexpr double kBreakdownFactor = 64.0 * 2.220446049250313e-16;
 
@@ -50,13 +58,16 @@ struct Workspace {
     double *V = nullptr;           // ld x (mmax+1), column-major
     double *z = nullptr, *u = nullptr, *r = nullptr, *b = nullptr, *x = nullptr, *t = nullptr;
     double *H = nullptr;           // (mmax+1) x mmax column-major, ldh = mmax+1
-    double *L = nullptr;           // (mmax+1) x (mmax+1) row-major, ldl = mmax+1
+    double *L = nullptr;           // (mmax+1) x (mmax+1) column-major: L(i,c) at L[c*ldl + i]
+    double *Lout = nullptr;        // (mmax+1)^2 staging for the row-major copy handed out
     double *R = nullptr;           // Givens-rotated copy of H, same layout as H
     double *cs = nullptr, *sn = nullptr, *g = nullptr;  // rotations and rotated rhs
     double *lfro2 = nullptr;       // cumulative ||L rows 0..i||_F^2, mmax+1 entries
     double *r0v = nullptr, *r1v = nullptr, *r2v = nullptr, *r3v = nullptr, *y = nullptr;
     double *part = nullptr;        // per-block partial sums
     int64_t part_cap = 0;
+    double *bpart = nullptr;       // per-block partials of the fused update (blocks x p)
+    int *counters = nullptr;       // group arrival counters of the fused update
     double *hist_res = nullptr, *hist_lfro = nullptr;  // per-cycle history (mmax entries)
     DevState *st = nullptr;
     int ldh() const { return mmax + 1; }
@@ -78,7 +89,7 @@ enum KClass { KC_SPMV = 0, KC_DOTS = 1, KC_UPDATE = 2, KC_SMALL = 3, KC_CYCLE = 
 // y = A x, or y = b - A x when b != nullptr.
 cudaError_t launch_spmv(const Workspace &w, const double *x, double *y, const double *b,
                         bool check_halt, cudaStream_t s);
-// Partial sums part[(q*p + c)*rblocks + rb] = sum over row block rb of V[:,c] . X_q, q < nq.
+// Partial sums part[rb*(nq*p) + q*p + c] = sum over row block rb of V[:,c] . X_q, q < nq.
 cudaError_t launch_dots(const Workspace &w, int p, const double *x0, const double *x1,
                         bool check_halt, cudaStream_t s, DotsPlan *plan_out);
 // out = alpha*src - V[:, 0:p] coef (coef negated when neg_coef); when norm_last, column p-1
@@ -87,7 +98,14 @@ cudaError_t launch_dots(const Workspace &w, int p, const double *x0, const doubl
 cudaError_t launch_update(const Workspace &w, int p, const double *coef, bool neg_coef,
                           double alpha, const double *src, double *out, bool norm_last,
                           bool p_from_state, bool check_halt, cudaStream_t s);
-// Partial sums of squares of up to three vectors (part[q*blocks + blk]).
+// Fused steps 7, 11, 13 + step-14 partial sums (two GS iterations): writes u and the group
+// partials part[g*p + c]; *ngroups_out = groups.  update_dots_fits(p) tells whether the
+// tile of p columns fits in shared memory.
+size_t update_dots_smem(int p);
+bool update_dots_fits(int p);
+cudaError_t launch_update_dots(const Workspace &w, int p, const double *coef, const double *z,
+                               double *u, cudaStream_t s, int *ngroups_out);
+// Partial sums of squares of up to three vectors (part[blk*nvec + q]).
 cudaError_t launch_norms(const Workspace &w, const double *a, const double *b,
                          const double *c, int *blocks_out, cudaStream_t s);
 // v = scale * w with scale = st->inv_rho (which=0) or st->inv_gamma (which=1).
@@ -105,6 +123,14 @@ cudaError_t launch_lsq(const Workspace &w, int m, cudaStream_t s);
 cudaError_t launch_beta(const Workspace &w, int nblk, cudaStream_t s);
 cudaError_t launch_init_state(const Workspace &w, double tol, double normA, cudaStream_t s);
 cudaError_t launch_bnorm(const Workspace &w, int nblk, cudaStream_t s);
+
+// dst(i, c) = src(i, c) for i < rows, c < cols: src column-major (ld_src), dst row-major
+// (ld_dst).
+cudaError_t launch_transpose(const double *src, int ld_src, int rows, int cols, double *dst,
+                             int ld_dst, cudaStream_t s);
+
+// Per-context kernel configuration (dynamic shared-memory limits); call before any capture.
+cudaError_t configure_kernels(const Workspace &w);
 
 // ||A||_2 estimate: power iteration on A^T A (At in CSR = A^T).
 cudaError_t estimate_norm2(const Workspace &w, const int *at_rowptr, const int *at_colind,

@@ -42,85 +42,133 @@ __device__ double block_sum(double v, double *sh)
     return r;
 }
 
-// out[v] = sum_{rb < nrb} part[v * nrb + rb] for v < nv (fixed order; block-wide).
-// Threads per value grow with fewer values so that long partial lists are split.
+// out[v] = sum_{rb < nrb} part[rb * nv + v] for v < nv (fixed order; block-wide, ends with
+// a barrier).  The layout is row-block major, so consecutive threads read consecutive
+// partials.  Each value is split over tpv threads (a power of two) so that no thread has
+// more than kRedRegs partials; a thread issues all of its loads before its first add (one
+// memory round trip), and the tpv sums are combined by a fixed shuffle tree.
+constexpr int kRedRegs = 24;
 __device__ void reduce_partials(const double *__restrict__ part, int nv, int nrb, double *out)
 {
     const int T = blockDim.x, t = threadIdx.x;
     int tpv = 1;
-    while (tpv < 32 && tpv * 2 * nv <= T) tpv *= 2;
+    while (tpv < 32 && (nrb + tpv - 1) / tpv > kRedRegs) tpv <<= 1;
     const int vpr = T / tpv;
     for (int v0 = 0; v0 < nv; v0 += vpr) {
         const int v = v0 + t / tpv, sub = t % tpv;
-        double a0 = 0.0, a1 = 0.0;
+        if (v0 + (t & ~31) / tpv >= nv) continue;  // whole warp idle: no FP64 issue slots spent
+        double s = 0.0;
         if (v < nv) {
-            const double *pv = part + (int64_t)v * nrb;
-            int rb = sub;
-            for (; rb + tpv < nrb; rb += 2 * tpv) {
-                a0 += pv[rb];
-                a1 += pv[rb + tpv];
+            double a[kRedRegs];
+            int rb0 = sub;
+            double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+            for (; rb0 < nrb; rb0 += kRedRegs * tpv) {  // one pass unless nrb > kRedRegs * 32
+#pragma unroll
+                for (int j = 0; j < kRedRegs; ++j) {
+                    const int rb = rb0 + j * tpv;
+                    a[j] = rb < nrb ? part[(int64_t)rb * nv + v] : 0.0;
+                }
+#pragma unroll
+                for (int j = 0; j < kRedRegs; j += 4) {
+                    acc0 += a[j];
+                    acc1 += a[j + 1];
+                    acc2 += a[j + 2];
+                    acc3 += a[j + 3];
+                }
             }
-            if (rb < nrb) a0 += pv[rb];
+            s = (acc0 + acc1) + (acc2 + acc3);
         }
-        double s = a0 + a1;
         for (int o = tpv >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, tpv);
         if (sub == 0 && v < nv) out[v] = s;
     }
     __syncthreads();
 }
 
+// Packed strictly-lower triangle of L_p in shared memory: column c holds rows c+1..p-1
+// starting at colstart(c) = c(2p - c - 1)/2.
+__device__ __forceinline__ int packed_col(int c, int p) { return c * (2 * p - c - 1) / 2; }
+
+// Copy rows/columns 0..p-1 of the device L (column-major, Lc[c*ldl + i] = L(i,c)) into the
+// packed shared layout.  The element loop is flattened and keeps eight loads in flight per
+// thread, so the copy costs a few L2 round trips rather than one per column.  Ends with a
+// barrier.
+__device__ void stage_lower(const double *__restrict__ Lc, int ldl, int p, double *Lsm)
+{
+    const int T = blockDim.x, t = threadIdx.x;
+    const int total = p * (p - 1) / 2;
+    int c = 0, cstart = 0, clen = p - 1;  // column c occupies [cstart, cstart + clen)
+    for (int e0 = 0; e0 < total; e0 += 8 * T) {
+        double v[8];
+        int dst[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int e = e0 + t + j * T;
+            dst[j] = -1;
+            v[j] = 0.0;
+            if (e < total) {
+                while (e >= cstart + clen) {
+                    cstart += clen;
+                    ++c;
+                    --clen;
+                }
+                v[j] = Lc[(int64_t)c * ldl + c + 1 + (e - cstart)];
+                dst[j] = e;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (dst[j] >= 0) Lsm[dst[j]] = v[j];
+    }
+    __syncthreads();
+}
+
 // x = (I + L_p)^{-1} rhs for the unit lower-triangular I + L (Alg. 4.1 steps 12 and 15).
-// L is row-major (leading dimension ldl), rows 0..p-1.  rhs and x live in shared memory
-// (x must not alias rhs; `tmp` is scratch of p entries).  Block-wide.
+// Lsm is the packed shared copy of L_p (stage_lower).  rhs and x live in shared memory (x
+// must not alias rhs; `tmp` is scratch of p entries).  Block-wide.
 //
 // When ||L||_F is small the solve is evaluated as the truncated Neumann series
 // sum_{i<t} (-L)^i rhs (Horner form), whose truncation error ||L||^t ||rhs|| / (1-||L||) is
 // kept below 2^-60 ||rhs|| -- far under the FP64 rounding of the substitution itself.  Each
-// term is one lane-parallel matrix-vector product, instead of p dependent steps.  With
-// two Gauss-Seidel iterations ||L||_F is O(eps) and t = 2.  Otherwise the classical
-// column-oriented forward substitution runs.  Returns the number of terms (0 =
-// substitution).
-__device__ int unit_lower_solve(const double *__restrict__ L, int ldl, int p,
-                                const double *rhs, double *x, double *tmp, double lfro2)
+// term is one lane-parallel matrix-vector product instead of p dependent steps.  With two
+// Gauss-Seidel iterations ||L||_F is O(eps) and t = 2.  Otherwise the classical
+// column-oriented forward substitution runs (terms = 0; see neumann_terms).
+__device__ void unit_lower_solve(const double *Lsm, int p, const double *rhs, double *x,
+                                 double *tmp, int terms)
 {
     const int T = blockDim.x, t = threadIdx.x;
-    int terms = 0;
-    if (lfro2 <= 0.0) {
-        terms = 1;
-    } else if (lfro2 < 0x1p-30) {  // ||L||_F < 2^-15
-        // need ||L||^terms <= 2^-60:  terms >= 120 / (-log2 lfro2)
-        const double bits = -log2(lfro2);  // > 30
-        terms = (int)ceil(120.0 / bits);
-        if (terms < 2) terms = 2;
-    }
-    if (terms >= 1 && terms <= 4) {
+    if (terms >= 1) {
         for (int i = t; i < p; i += T) x[i] = rhs[i];
         __syncthreads();
+        // tmp = rhs - L x.  Thread pair (2a, 2a+1) owns rows a and p-1-a (equal total
+        // length); the two threads of a pair take alternate columns and combine by one
+        // shuffle.  Two rows give two independent FMA chains per thread.
+        const int npair = (p + 1) >> 1;
         for (int it = 1; it < terms; ++it) {
-            // tmp = rhs - L x, rows paired (i, p-1-i) to balance the triangle over threads
-            for (int i = t; i < (p + 1) / 2; i += T) {
-                for (int h = 0; h < 2; ++h) {
-                    const int row = h == 0 ? i : p - 1 - i;
-                    if (h == 1 && row == i) break;
-                    const double *Lr = L + (int64_t)row * ldl;
-                    double a0 = 0.0, a1 = 0.0;
-                    int c = 0;
-                    for (; c + 1 < row; c += 2) {
-                        a0 = fma(Lr[c], x[c], a0);
-                        a1 = fma(Lr[c + 1], x[c + 1], a1);
-                    }
-                    if (c < row) a0 = fma(Lr[c], x[c], a0);
-                    tmp[row] = rhs[row] - (a0 + a1);
+            for (int base = 0; base < 2 * npair; base += T) {
+                const int q = base + t, a = q >> 1, h = q & 1;
+                const bool act = a < npair;
+                const int r0 = a, r1 = p - 1 - a;
+                double s0 = 0.0, s1 = 0.0;
+                if (act) {
+                    for (int c = h; c < r0; c += 2) s0 = fma(Lsm[packed_col(c, p) + r0 - c - 1], x[c], s0);
+                    if (r1 != r0)
+                        for (int c = h; c < r1; c += 2) s1 = fma(Lsm[packed_col(c, p) + r1 - c - 1], x[c], s1);
+                }
+                s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+                if (act && h == 0) {
+                    tmp[r0] = rhs[r0] - s0;
+                    if (r1 != r0) tmp[r1] = rhs[r1] - s1;
                 }
             }
             __syncthreads();
             for (int i = t; i < p; i += T) x[i] = tmp[i];
             __syncthreads();
         }
-        return terms;
+        return;
     }
     // Forward substitution, column oriented: after x[c] is final, every later row subtracts
-    // L[i][c] x[c].  Rows are owned by threads (i = t + T*q, q < 4 covers p <= 4T).
+    // L(i,c) x[c].  Rows are owned by threads (i = t + T*q, q < 4 covers p <= 4T).
     double xi[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -131,14 +179,46 @@ __device__ int unit_lower_solve(const double *__restrict__ L, int ldl, int p,
         if ((c % T) == t) x[c] = xi[c / T];
         __syncthreads();
         const double xc = x[c];
+        const double *Lcol = Lsm + packed_col(c, p) - c - 1;  // Lcol[i] = L(i, c), i > c
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int i = t + T * q;
-            if (i > c && i < p) xi[q] = fma(-L[(int64_t)i * ldl + c], xc, xi[q]);
+            if (i > c && i < p) xi[q] = fma(-Lcol[i], xc, xi[q]);
         }
     }
     __syncthreads();
-    return 0;
+}
+
+// Number of Neumann terms t for (I+L)^{-1}: the smallest t with ||L||_F^t <= 2^-60, from the
+// binary exponent of ||L||_F^2 (integer arithmetic only); 1 when L = 0; 0 (substitution)
+// when ||L||_F >= 2^-15 or the value is not finite.
+__device__ __forceinline__ int neumann_terms(double lfro2)
+{
+    const long long b = __double_as_longlong(lfro2);
+    if (b == 0) return 1;
+    const int ex = (int)((b >> 52) & 0x7ff) - 1023;  // lfro2 in [2^ex, 2^(ex+1))
+    if (b < 0 || ex >= -30) return 0;
+    const int d = -(ex + 1);                          // ||L||_F < 2^(-d/2), d >= 30
+    const int terms = (120 + d - 1) / d;
+    return terms < 2 ? 2 : terms;
+}
+
+// ||col[0:len]||^2 by the block's last warp (fixed shuffle tree), stored in *out.  Called
+// before a block-wide step that ends with a barrier, so that it overlaps that step.
+__device__ void last_warp_sumsq(const double *__restrict__ col, int len, double *out)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid != ((int)blockDim.x >> 5) - 1) return;
+    double a0 = 0.0, a1 = 0.0;
+    int i = lane;
+    for (; i + 32 < len; i += 64) {
+        a0 = fma(col[i], col[i], a0);
+        a1 = fma(col[i + 32], col[i + 32], a1);
+    }
+    if (i < len) a0 = fma(col[i], col[i], a0);
+    double v = a0 + a1;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) *out = v;
 }
 
 }  // namespace
@@ -194,7 +274,7 @@ k_spmv_warp(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ c
 
 // =====================================================================================
 // Block multi-dot (Alg. 4.1 step 5, the one global reduction per iteration; step 14).
-// part[(q*p + c)*gridDim.x + rb] = sum over rows of row block rb of V[:,c] * X_q.
+// part[rb*(NQ*p) + q*p + c] = sum over the rows of row block rb of V[:,c] * X_q.
 // Grid: x = row blocks, y = column groups (p columns split evenly).  Thread t of a block
 // owns column c_lo + t % cw and streams its own contiguous row slice t / cw: no lane ever
 // spends an FP64 add on combining other lanes' products until the slice tree at the end.
@@ -202,7 +282,7 @@ k_spmv_warp(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ c
 // alternate rows keep two independent FMAs in flight.
 // =====================================================================================
 template <int NQ>
-__global__ void __launch_bounds__(kStreamThreads, kBlocksPerSM)
+__global__ void __launch_bounds__(kStreamThreads, kDotsBlocksPerSM)
 k_dots(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t rows,
        const double *__restrict__ x0, const double *__restrict__ x1, double *__restrict__ part,
        const DevState *st, int check_halt)
@@ -259,9 +339,8 @@ k_dots(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t rows
     }
     __syncthreads();
     if (s == 0) {
-        const int nrb = gridDim.x;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) part[((int64_t)q * p + c_lo + cl) * nrb + rb] = red[q][t];
+        for (int q = 0; q < NQ; ++q) part[(int64_t)rb * NQ * p + (int64_t)q * p + c_lo + cl] = red[q][t];
     }
 }
 
@@ -287,17 +366,25 @@ k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coe
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const double *vi = V + i;
-        double acc0 = 0.0, acc1 = 0.0;
+        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
         int c = 0;
-        for (; c + 3 < pc; c += 4) {
-            const double v0 = vi[(int64_t)c * ld], v1 = vi[(int64_t)(c + 1) * ld];
-            const double v2 = vi[(int64_t)(c + 2) * ld], v3 = vi[(int64_t)(c + 3) * ld];
-            acc0 = fma(v0, sc[c], acc0);
-            acc1 = fma(v1, sc[c + 1], acc1);
-            acc0 = fma(v2, sc[c + 2], acc0);
-            acc1 = fma(v3, sc[c + 3], acc1);
+        // eight independent loads in flight per thread, four FMA chains
+        for (; c + 7 < pc; c += 8) {
+            double v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = vi[(int64_t)(c + q) * ld];
+            acc0 = fma(v[0], sc[c], acc0);
+            acc1 = fma(v[1], sc[c + 1], acc1);
+            acc2 = fma(v[2], sc[c + 2], acc2);
+            acc3 = fma(v[3], sc[c + 3], acc3);
+            acc0 = fma(v[4], sc[c + 4], acc0);
+            acc1 = fma(v[5], sc[c + 5], acc1);
+            acc2 = fma(v[6], sc[c + 6], acc2);
+            acc3 = fma(v[7], sc[c + 7], acc3);
         }
         for (; c < pc; ++c) acc0 = fma(vi[(int64_t)c * ld], sc[c], acc0);
+        acc0 += acc2;
+        acc1 += acc3;
         if (norm_last) {
             double *vl = V + (int64_t)(p - 1) * ld + i;
             const double v = *vl * a;
@@ -308,10 +395,153 @@ k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coe
     }
 }
 
-// Partial sums of squares of up to three vectors: part[q * gridDim.x + blockIdx.x].
+// =====================================================================================
+// Fused first Gauss-Seidel update and second reduction (two GS iterations; Alg. 4.1
+// steps 7, 11, 13 and the partial sums of step 14):
+//   v_{k-1} = w_{k-1} / gamma (in place), u_k = z / gamma - V_{k-1} r^(1),
+//   part[blk*p + c] = sum over the block's rows of V[:,c] u_k.
+// Each block streams a contiguous row range in tiles of TR rows.  Phase 1 (thread per row)
+// reads the tile's p columns once from HBM, keeps them in shared memory and forms u; phase 2
+// (thread per column, or per column and row slice) reads the tile back from shared memory
+// against u.  Every basis element thus feeds two FMAs from one HBM read, as in the step-5
+// multi-dot.  Blocks then combine their partials in groups: the last block of each group to
+// finish (atomic counter; nobody waits) adds the group's partials in block order and writes
+// gpart[g*p + c] -- few enough partials for one block to finish the reduction quickly.
+// =====================================================================================
+template <int TR>
+__global__ void __launch_bounds__(TR, 2)
+k_update_dots(double *V, int64_t ld, int p, int64_t n, int64_t rows_per_block,
+              const double *__restrict__ coef, const double *__restrict__ z, double *__restrict__ u,
+              double *__restrict__ bpart, double *__restrict__ gpart, int *__restrict__ counters,
+              int group, DevState *st)
+{
+    if (halted(st)) return;
+    extern __shared__ double smem[];
+    constexpr int ldt = TR + 1;          // padded tile stride
+    double *tile = smem;                 // p columns x ldt
+    double *sc = tile + (size_t)p * ldt; // p coefficients
+    double *us = sc + p;                 // u of the tile's rows
+    double *red = us + TR;               // slice tree
+    __shared__ int s_last;
+    const int t = threadIdx.x;
+    const double ig = st->inv_gamma;
+    for (int c = t; c < p; c += TR) sc[c] = coef[c];
+    // phase-2 mapping
+    const bool narrow = p <= TR;
+    const int S = narrow ? TR / p : 1;   // row slices per column
+    const int cmine = narrow ? t % p : t;
+    const int s = narrow ? t / p : 0;
+    const bool act = narrow ? s < S : true;
+    double a0 = 0.0, a1 = 0.0;           // narrow: two chains of column cmine; wide: columns t, t+TR
+    __syncthreads();
+    const int64_t r_lo = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r_hi = r_lo + rows_per_block < n ? r_lo + rows_per_block : n;
+    for (int64_t t0 = r_lo; t0 < r_hi; t0 += TR) {
+        const int len = (int)(r_hi - t0 < TR ? r_hi - t0 : TR);
+        if (t < len) {
+            const int64_t i = t0 + t;
+            const double *vi = V + i;
+            double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+            int c = 0;
+            const int pc = p - 1;
+            for (; c + 7 < pc; c += 8) {
+                double v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = vi[(int64_t)(c + q) * ld];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) tile[(size_t)(c + q) * ldt + t] = v[q];
+                b0 = fma(v[0], sc[c], b0);
+                b1 = fma(v[1], sc[c + 1], b1);
+                b2 = fma(v[2], sc[c + 2], b2);
+                b3 = fma(v[3], sc[c + 3], b3);
+                b0 = fma(v[4], sc[c + 4], b0);
+                b1 = fma(v[5], sc[c + 5], b1);
+                b2 = fma(v[6], sc[c + 6], b2);
+                b3 = fma(v[7], sc[c + 7], b3);
+            }
+            for (; c < pc; ++c) {
+                const double v = vi[(int64_t)c * ld];
+                tile[(size_t)c * ldt + t] = v;
+                b0 = fma(v, sc[c], b0);
+            }
+            double *vl = V + (int64_t)pc * ld + i;
+            const double vlast = *vl * ig;  // step 7, in place
+            *vl = vlast;
+            tile[(size_t)pc * ldt + t] = vlast;
+            b1 = fma(vlast, sc[pc], b1);
+            const double ui = fma(ig, z[i], -((b0 + b2) + (b1 + b3)));  // steps 11, 13
+            u[i] = ui;
+            us[t] = ui;
+        }
+        __syncthreads();
+        if (narrow) {
+            if (act) {
+                const int rs = s * len / S, re = (s + 1) * len / S;
+                const double *tc = tile + (size_t)cmine * ldt;
+                int r = rs;
+                for (; r + 1 < re; r += 2) {
+                    a0 = fma(tc[r], us[r], a0);
+                    a1 = fma(tc[r + 1], us[r + 1], a1);
+                }
+                if (r < re) a0 = fma(tc[r], us[r], a0);
+            }
+        } else {
+            const double *t0c = tile + (size_t)t * ldt;
+            const double *t1c = tile + (size_t)(t + TR) * ldt;
+            const bool second = t + TR < p;
+            for (int r = 0; r < len; ++r) {
+                a0 = fma(t0c[r], us[r], a0);
+                if (second) a1 = fma(t1c[r], us[r], a1);
+            }
+        }
+        __syncthreads();
+    }
+    // block partials (slice tree when narrow)
+    if (narrow) {
+        red[t] = a0 + a1;
+        int Sp = S;
+        while (Sp > 1) {
+            const int h = (Sp + 1) >> 1;
+            __syncthreads();
+            if (act && s < Sp - h) red[t] += red[t + h * p];
+            Sp = h;
+        }
+        __syncthreads();
+        if (act && s == 0) bpart[(int64_t)blockIdx.x * p + cmine] = red[t];
+    } else {
+        if (t < p) bpart[(int64_t)blockIdx.x * p + t] = a0;
+        if (t + TR < p) bpart[(int64_t)blockIdx.x * p + t + TR] = a1;
+    }
+    // group combine by the last block of the group to finish
+    __threadfence();
+    __syncthreads();
+    const int g = blockIdx.x / group;
+    const int gb0 = g * group;
+    const int gb1 = gb0 + group < (int)gridDim.x ? gb0 + group : (int)gridDim.x;
+    if (t == 0) {
+        const int prev = atomicAdd(&counters[g], 1);
+        s_last = prev == gb1 - gb0 - 1;
+        if (s_last) counters[g] = 0;  // ready for the next launch
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int c = t; c < p; c += TR) {
+        double s0 = 0.0, s1 = 0.0;
+        int b = gb0;
+        for (; b + 1 < gb1; b += 2) {
+            s0 += __ldcg(bpart + (int64_t)b * p + c);
+            s1 += __ldcg(bpart + (int64_t)(b + 1) * p + c);
+        }
+        if (b < gb1) s0 += __ldcg(bpart + (int64_t)b * p + c);
+        gpart[(int64_t)g * p + c] = s0 + s1;
+    }
+}
+
+// Partial sums of squares of up to three vectors: part[blockIdx.x * nvec + q].
 __global__ void __launch_bounds__(kStreamThreads)
 k_norms(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
-        const double *__restrict__ c, double *__restrict__ part)
+        const double *__restrict__ c, double *__restrict__ part, int nvec)
 {
     __shared__ double sh[kStreamThreads];
     const double *vs[3] = {a, b, c};
@@ -327,7 +557,7 @@ k_norms(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
         }
         if (i < n) s0 = fma(v[i], v[i], s0);
         const double tot = block_sum(s0 + s1, sh);
-        if (threadIdx.x == 0) part[q * gridDim.x + blockIdx.x] = tot;
+        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * nvec + q] = tot;
     }
 }
 
@@ -445,20 +675,22 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
         if (threadIdx.x == 0) st->halt = 1;
         return;
     }
-    __shared__ double buf[2 * (kMaxRestart + 1)];
-    __shared__ double r0s[kMaxRestart + 1], r1s[kMaxRestart + 1], tmp[kMaxRestart + 1];
-    __shared__ double sh[kSmallThreads];
+    extern __shared__ double dsm[];
+    const int pp = k - 1;
+    double *buf = dsm;              // 2p combined partials
+    double *r0s = buf + 2 * pp;     // r^(0)
+    double *r1s = r0s + pp;         // r^(1)
+    double *tmp = r1s + pp;         // solve scratch
+    double *Lsm = tmp + pp;         // packed L_p
     __shared__ double s_inv_gamma;
-    __shared__ int s_stop;
+    __shared__ int s_stop, s_terms;
+    __shared__ double s_hn2;
     const int p = k - 1, t = threadIdx.x;
+    const double lf2_prev = t == 0 ? a.lfro2[p - 2] : 0.0;  // issued early
+    // breakdown test needs ||H(0:p-2, p-2)||^2 (overlapped with the partial combine)
+    last_warp_sumsq(a.H + (int64_t)(p - 2) * a.ldh, p - 1, &s_hn2);
     reduce_partials(a.part, 2 * p, nrb, buf);
-    // breakdown test needs ||H(0:p-2, p-2)||^2
-    double hv = 0.0;
-    for (int i = t; i <= p - 2; i += blockDim.x) {
-        const double h = a.H[(int64_t)(p - 2) * a.ldh + i];
-        hv = fma(h, h, hv);
-    }
-    const double hn2 = block_sum(hv, sh);
+    const double hn2 = s_hn2;
     if (t == 0) {
         const double ww = buf[p - 1];
         int stop = 0;
@@ -485,23 +717,33 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
     __syncthreads();
     if (s_stop != 0) return;
     const double ig = s_inv_gamma;
-    // steps 8-10
-    double rowsq = 0.0;
-    for (int c = t; c < p; c += blockDim.x) {
-        double r = buf[p + c] * ig;
-        if (c == p - 1) r *= ig;
-        r0s[c] = r;
-        if (c < p - 1) {
+    if (t < 32) {
+        // step 10 (warp 0): the new L row, its squared norm and the Neumann term count
+        double rowsq = 0.0;
+        for (int c = t; c < p - 1; c += 32) {
             const double l = buf[c] * ig;
-            a.L[(int64_t)(p - 1) * a.ldl + c] = l;
+            a.L[(int64_t)c * a.ldl + (p - 1)] = l;
             rowsq = fma(l, l, rowsq);
         }
+        for (int o = 16; o > 0; o >>= 1) rowsq += __shfl_down_sync(0xffffffffu, rowsq, o);
+        if (t == 0) {
+            const double lf2 = lf2_prev + rowsq;
+            a.lfro2[p - 1] = lf2;
+            s_terms = neumann_terms(lf2);
+        }
+    } else {
+        // steps 8-9 (other warps): r^(0) / gamma, its last entry once more
+        for (int c = t - 32; c < p; c += blockDim.x - 32) {
+            double r = buf[p + c] * ig;
+            if (c == p - 1) r *= ig;
+            r0s[c] = r;
+        }
     }
-    const double rs = block_sum(rowsq, sh);  // also a barrier for r0s
-    const double lf2 = a.lfro2[p - 2] + rs;
-    if (t == 0) a.lfro2[p - 1] = lf2;
+    __syncthreads();
     // step 12
-    const int terms = unit_lower_solve(a.L, a.ldl, p, r0s, r1s, tmp, lf2);
+    stage_lower(a.L, a.ldl, p, Lsm);
+    const int terms = s_terms;
+    unit_lower_solve(Lsm, p, r0s, r1s, tmp, terms);
     for (int c = t; c < p; c += blockDim.x) {
         a.r1v[c] = r1s[c];
         if (gs == 1) a.H[(int64_t)(p - 1) * a.ldh + c] = r1s[c];
@@ -515,10 +757,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_b(SmallArgs a, int k, in
 {
     DevState *st = a.st;
     if (halted(st)) return;
-    __shared__ double r2s[kMaxRestart + 1], r3s[kMaxRestart + 1], tmp[kMaxRestart + 1];
+    extern __shared__ double dsm[];
     const int p = k - 1, t = threadIdx.x;
+    double *r2s = dsm, *r3s = r2s + p, *tmp = r3s + p, *Lsm = tmp + p;
     reduce_partials(a.part, p, nrb, r2s);
-    unit_lower_solve(a.L, a.ldl, p, r2s, r3s, tmp, a.lfro2[p - 1]);
+    stage_lower(a.L, a.ldl, p, Lsm);
+    unit_lower_solve(Lsm, p, r2s, r3s, tmp, neumann_terms(a.lfro2[p - 1]));
     for (int c = t; c < p; c += blockDim.x) {
         a.r3v[c] = r3s[c];
         a.H[(int64_t)(p - 1) * a.ldh + c] = a.r1v[c] + r3s[c];
@@ -540,14 +784,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_flush(SmallArgs a, int m, int
     __shared__ double sh[kSmallThreads];
     __shared__ double s_ig;
     __shared__ int s_stop;
+    __shared__ double s_hn2;
     const int t = threadIdx.x;
+    last_warp_sumsq(a.H + (int64_t)(m - 1) * a.ldh, m, &s_hn2);
     reduce_partials(a.part, m + 1, nrb, buf);
-    double hv = 0.0;
-    for (int i = t; i <= m - 1; i += blockDim.x) {
-        const double h = a.H[(int64_t)(m - 1) * a.ldh + i];
-        hv = fma(h, h, hv);
-    }
-    const double hn2 = block_sum(hv, sh);
+    const double hn2 = s_hn2;
     if (t == 0) {
         const double ww = buf[m];
         int stop = 0;
@@ -577,7 +818,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_flush(SmallArgs a, int m, int
     double rowsq = 0.0;
     for (int c = t; c < m; c += blockDim.x) {
         const double l = buf[c] * s_ig;
-        a.L[(int64_t)m * a.ldl + c] = l;
+        a.L[(int64_t)c * a.ldl + m] = l;
         rowsq = fma(l, l, rowsq);
     }
     const double rs = block_sum(rowsq, sh);
@@ -716,6 +957,18 @@ __global__ void __launch_bounds__(kSmallThreads) k_lsq(SmallArgs a, int m)
     for (int i = t; i < p; i += T) a.y[i] = ys[i];
 }
 
+// Column-major -> row-major copy of a small matrix (the L factor handed to the caller).
+__global__ void k_transpose(const double *__restrict__ src, int ld_src, int rows, int cols,
+                            double *__restrict__ dst, int ld_dst)
+{
+    const int64_t total = (int64_t)rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / cols), c = (int)(e % cols);
+        dst[(int64_t)i * ld_dst + c] = src[(int64_t)c * ld_src + i];
+    }
+}
+
 // -------------------------------------------------------------------------------------
 // Power iteration for ||A||_2 (create time): x <- A^T A x / ||A^T A x||.
 // -------------------------------------------------------------------------------------
@@ -752,10 +1005,15 @@ static int stream_grid(const Workspace &w)
     return w.num_sms * kBlocksPerSM;
 }
 
+static int dots_slots(const Workspace &w)
+{
+    return w.num_sms * kDotsBlocksPerSM;
+}
+
 DotsPlan plan_dots(const Workspace &w, int p)
 {
     DotsPlan pl;
-    const int slots = stream_grid(w);
+    const int slots = dots_slots(w);
     int groups = (p + kDotsColsPerBlock - 1) / kDotsColsPerBlock;
     if (groups > slots) groups = slots;
     if (groups < 1) groups = 1;
@@ -777,7 +1035,11 @@ DotsPlan plan_dots(const Workspace &w, int p)
 cudaError_t launch_spmv(const Workspace &w, const double *x, double *y, const double *b,
                         bool check_halt, cudaStream_t s)
 {
-    const int grid = stream_grid(w);
+    // one thread (short rows) or one warp (long rows) per row, so that every row's three
+    // dependent loads (row pointer, column index, x) are in flight at once
+    const int64_t per_block = w.spmv_warp_rows ? kStreamThreads / 32 : kStreamThreads;
+    const int64_t want = (w.n + per_block - 1) / per_block;
+    const int grid = (int)(want < (int64_t)1 << 30 ? want : (int64_t)1 << 30);
     if (w.spmv_warp_rows)
         k_spmv_warp<<<grid, kStreamThreads, 0, s>>>(w.n, w.rowptr, w.colind, w.val, x, y, b, w.st,
                                                     check_halt);
@@ -809,10 +1071,43 @@ cudaError_t launch_update(const Workspace &w, int p, const double *coef, bool ne
 {
     const int pmax = p_from_state ? w.mmax + 1 : p;
     const size_t smem = sizeof(double) * (size_t)(pmax > 0 ? pmax : 1);
-    k_update<<<stream_grid(w), kStreamThreads, smem, s>>>(w.V, w.ld, p, w.n, coef, neg_coef ? 1 : 0,
+    // one row per thread: the whole vector is resident at once (occupancy, not a grid-stride
+    // loop, hides the loads' latency)
+    const int grid = (int)((w.n + kStreamThreads - 1) / kStreamThreads);
+    k_update<<<grid, kStreamThreads, smem, s>>>(w.V, w.ld, p, w.n, coef, neg_coef ? 1 : 0,
                                                           alpha, src, out, norm_last ? 1 : 0,
                                                           p_from_state ? 1 : 0, w.st,
                                                           check_halt ? 1 : 0);
+    return cudaGetLastError();
+}
+
+size_t update_dots_smem(int p)
+{
+    return sizeof(double) * ((size_t)p * (kFusedRows + 1) + (size_t)p + 2 * (size_t)kFusedRows);
+}
+
+bool update_dots_fits(int p)
+{
+    return update_dots_smem(p) <= kFusedMaxSmem;
+}
+
+cudaError_t launch_update_dots(const Workspace &w, int p, const double *coef, const double *z,
+                               double *u, cudaStream_t s, int *ngroups_out)
+{
+    const size_t smem = update_dots_smem(p);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_dots<kFusedRows>,
+                                                                  kFusedRows, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2) per_sm = 2;
+    const int blocks = w.num_sms * per_sm;
+    const int64_t rows = (w.n + blocks - 1) / blocks;
+    const int nblk = (int)((w.n + rows - 1) / rows);
+    const int ngroups = (nblk + kFusedGroup - 1) / kFusedGroup;
+    k_update_dots<kFusedRows><<<nblk, kFusedRows, smem, s>>>(w.V, w.ld, p, w.n, rows, coef, z, u, w.bpart,
+                                                             w.part, w.counters, kFusedGroup, w.st);
+    if (ngroups_out) *ngroups_out = ngroups;
     return cudaGetLastError();
 }
 
@@ -820,7 +1115,8 @@ cudaError_t launch_norms(const Workspace &w, const double *a, const double *b, c
                          int *blocks_out, cudaStream_t s)
 {
     const int grid = w.num_sms;
-    k_norms<<<grid, kStreamThreads, 0, s>>>(w.n, a, b, c, w.part);
+    const int nvec = !a ? 0 : !b ? 1 : !c ? 2 : 3;
+    k_norms<<<grid, kStreamThreads, 0, s>>>(w.n, a, b, c, w.part, nvec);
     if (blocks_out) *blocks_out = grid;
     return cudaGetLastError();
 }
@@ -862,15 +1158,49 @@ cudaError_t launch_prime(const Workspace &w, const DotsPlan &pl, cudaStream_t s)
     return cudaGetLastError();
 }
 
+size_t small_solve_smem(int p, int vecs)
+{
+    return sizeof(double) * ((size_t)vecs * p + (size_t)p * (p - 1) / 2);
+}
+
+static cudaError_t allow_smem(const void *fn, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t configure_kernels(const Workspace &w)
+{
+    // Dynamic shared-memory limits are set once per context, before any graph capture, to
+    // what the context's largest restart length needs.
+    cudaError_t e = allow_smem((const void *)k_step_a, small_solve_smem(w.mmax, 5));
+    if (e == cudaSuccess) e = allow_smem((const void *)k_step_b, small_solve_smem(w.mmax, 3));
+    if (e == cudaSuccess) {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa{};
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_update_dots<kFusedRows>);
+        if (e == cudaSuccess) {
+            size_t lim = (size_t)optin - fa.sharedSizeBytes;
+            if (lim > kFusedMaxSmem) lim = kFusedMaxSmem;
+            e = cudaFuncSetAttribute(k_update_dots<kFusedRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        }
+    }
+    return e;
+}
+
 cudaError_t launch_step_a(const Workspace &w, int k, int gs, const DotsPlan &pl, cudaStream_t s)
 {
-    k_step_a<<<1, kSmallThreads, 0, s>>>(small_args(w), k, gs, pl.rblocks);
+    const size_t smem = small_solve_smem(k - 1, 5);
+    k_step_a<<<1, kSmallThreads, smem, s>>>(small_args(w), k, gs, pl.rblocks);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_b(const Workspace &w, int k, const DotsPlan &pl, cudaStream_t s)
 {
-    k_step_b<<<1, kSmallThreads, 0, s>>>(small_args(w), k, pl.rblocks);
+    const size_t smem = small_solve_smem(k - 1, 3);
+    k_step_b<<<1, kSmallThreads, smem, s>>>(small_args(w), k, pl.rblocks);
     return cudaGetLastError();
 }
 
@@ -892,6 +1222,17 @@ cudaError_t launch_lsq(const Workspace &w, int m, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_transpose(const double *src, int ld_src, int rows, int cols, double *dst,
+                             int ld_dst, cudaStream_t s)
+{
+    const int64_t total = (int64_t)rows * cols;
+    int grid = (int)((total + 255) / 256);
+    if (grid < 1) grid = 1;
+    if (grid > 4096) grid = 4096;
+    k_transpose<<<grid, 256, 0, s>>>(src, ld_src, rows, cols, dst, ld_dst);
+    return cudaGetLastError();
+}
+
 cudaError_t estimate_norm2(const Workspace &w, const int *at_rowptr, const int *at_colind,
                            const double *at_val, int iters, double *out, cudaStream_t s)
 {
@@ -910,7 +1251,7 @@ cudaError_t estimate_norm2(const Workspace &w, const int *at_rowptr, const int *
             k_spmv_rows<<<grid, kStreamThreads, 0, s>>>(w.n, at_rowptr, at_colind, at_val, w.z, w.u,
                                                         nullptr, w.st, 0);
         }
-        k_norms<<<w.num_sms, kStreamThreads, 0, s>>>(w.n, w.u, nullptr, nullptr, w.part);
+        k_norms<<<w.num_sms, kStreamThreads, 0, s>>>(w.n, w.u, nullptr, nullptr, w.part, 1);
         k_power_norm<<<1, kSmallThreads, 0, s>>>(w.part, w.num_sms, w.y);
         k_power_scale<<<grid, kStreamThreads, 0, s>>>(w.n, w.u, w.y);
         cudaMemcpyAsync(w.t, w.u, sizeof(double) * (size_t)w.n, cudaMemcpyDeviceToDevice, s);

@@ -28,19 +28,19 @@ static __device__ __align__(256) double g_dots_scratch[kStaticScratch];
 std::mutex g_mu;
 double *g_scratch_ptr[kMaxDevices] = {};
 
-// out[v] = sum over rb of part[v * nrb + rb], fixed order (one block).
+// out[v] = sum over rb of part[rb * nv + v] (the multi-dot's row-block-major partials),
+// fixed order (one block).
 __global__ void __launch_bounds__(256) k_sum_partials(const double *__restrict__ part, int nv, int nrb,
                                                      double *__restrict__ out)
 {
     for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-        const double *pv = part + (int64_t)v * nrb;
         double a0 = 0.0, a1 = 0.0;
         int rb = 0;
         for (; rb + 1 < nrb; rb += 2) {
-            a0 += pv[rb];
-            a1 += pv[rb + 1];
+            a0 += part[(int64_t)rb * nv + v];
+            a1 += part[(int64_t)(rb + 1) * nv + v];
         }
-        if (rb < nrb) a0 += pv[rb];
+        if (rb < nrb) a0 += part[(int64_t)rb * nv + v];
         out[v] = a0 + a1;
     }
 }

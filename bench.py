@@ -102,6 +102,20 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def reduce_replicas(ms, e2e_s, steps, dist=None, device=None):
+    """Whole-job figures over N independent replicas (one per rank): the slowest rank's
+    device time and end-to-end time, and the Arnoldi steps of all ranks.  Without a process
+    group, the local figures."""
+    if dist is None:
+        return ms, e2e_s, steps
+    import torch
+    t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([float(steps)], dtype=torch.float64, device=device)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return float(t[0].item()), float(t[1].item()), int(round(s.item()))
+
+
 def oracle_cycle_rate(A, b, m):
     """Arnoldi steps/s of the CPU oracle (as it stands, one thread) over one cycle."""
     import oracle
@@ -208,12 +222,6 @@ def main():
     ms = ev0.elapsed_time(ev1)
     launches = solver.launches - launches0
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    steps_total = args.steps * M * ws
-    value = steps_total / (ms / 1e3)
 
     # ---- end to end through the C interface with host buffers ----
     b_host = np.ascontiguousarray(b)
@@ -225,10 +233,8 @@ def main():
     for _ in range(args.steps):
         solver.solve(b_host, m=M, gs=args.gs, tol=0.0, max_restarts=1, x_out=x_host, hist_cap=0)
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    ms, e2e_s, steps_total = reduce_replicas(ms, e2e_s, args.steps * M, dist, "cuda")
+    value = steps_total / (ms / 1e3)
     e2e = {"value": steps_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * A.n,
            "d2h_bytes_per_step": 8 * A.n + 2 * 96}
 

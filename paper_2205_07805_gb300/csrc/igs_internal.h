@@ -23,6 +23,9 @@ constexpr int kDotsBlocksPerSM = 3;
 constexpr int kFusedRows = 128;
 constexpr int kFusedGroup = 16;
 constexpr size_t kFusedMaxSmem = 220 * 1024;  // under the 227 KiB opt-in, minus static smem
+// TMA-pipelined basis kernels: largest dynamic shared memory and blocks per SM they use.
+constexpr size_t kTmaMaxSmem = 220 * 1024;
+constexpr int kTmaMaxBlocksPerSM = 8;
 // Largest restart length supported.  The small single-block steps hold L_p packed in shared
 // memory: 8 (5p + p(p-1)/2) bytes <= 227 KiB gives p <= 232.
 constexpr int kMaxRestart = 232;
@@ -105,6 +108,15 @@ size_t update_dots_smem(int p);
 bool update_dots_fits(int p);
 cudaError_t launch_update_dots(const Workspace &w, int p, const double *coef, const double *z,
                                double *u, cudaStream_t s, int *ngroups_out);
+// TMA-pipelined versions (igs_stream_tma.cu).  tma_fits(p): the double-buffered tile of p
+// columns fits in shared memory.
+size_t tma_smem(int p, bool with_dots);
+bool tma_fits(int p);
+cudaError_t launch_update_dots_tma(const Workspace &w, int p, const double *coef, const double *z,
+                                   double *u, cudaStream_t s, int *ngroups_out);
+cudaError_t launch_update_tma(const Workspace &w, int p, const double *coef, double alpha,
+                              const double *src, double *out, bool norm_last, cudaStream_t s);
+cudaError_t configure_tma_kernels();
 // Partial sums of squares of up to three vectors (part[blk*nvec + q]).
 cudaError_t launch_norms(const Workspace &w, const double *a, const double *b,
                          const double *c, int *blocks_out, cudaStream_t s);

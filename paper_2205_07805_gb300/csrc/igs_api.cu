@@ -452,6 +452,8 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
     // Basis-update implementation (all compute the same steps): "plain" (row per thread,
     // default: fastest measured), "tma" (bulk-copy pipelined), "fused" (non-pipelined fused
     // update + reduction).
+    // Programmatic dependent launch between the cycle's kernels (default on; IGS_PDL=0 off).
+    if (const char *pdl = getenv("IGS_PDL")) ctx->w.pdl = strcmp(pdl, "0") != 0;
     if (const char *path = getenv("IGS_UPDATE_PATH")) {
         ctx->use_tma = strcmp(path, "tma") == 0;
         ctx->fused_update = strcmp(path, "fused") == 0;

@@ -32,6 +32,33 @@ constexpr int kMaxRestart = 232;
 // Breakdown threshold factor: gamma <= 64 eps ||H(1:j, j)||.
 constexpr double kBreakdownFactor = 64.0 * 2.220446049250313e-16;
 
+// Programmatic dependent launch: every kernel of a cycle first waits for its predecessor's
+// results (griddepcontrol.wait; a no-op without PDL) and immediately allows its own
+// dependents to be launched, so that a kernel's launch overlaps the tail of the previous one.
+#define IGS_PDL_ENTER()                                              \
+    do {                                                             \
+        asm volatile("griddepcontrol.wait;" ::: "memory");           \
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
+    } while (0)
+
+// Launch with the programmatic-stream-serialization attribute when `pdl` is set.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Scalars of one solve, kept in device memory so that no step needs the host.
 struct DevState {
     double rho;        // ||r0|| of the current cycle
@@ -56,6 +83,7 @@ struct Workspace {
     int mmax = 0;
     int num_sms = 0;
     bool spmv_warp_rows = false;   // warp-per-row SpMV (long rows) instead of thread-per-row
+    bool pdl = true;               // programmatic dependent launch of the single-block steps
     const int *rowptr = nullptr, *colind = nullptr;
     const double *val = nullptr;
     double *V = nullptr;           // ld x (mmax+1), column-major

@@ -232,6 +232,7 @@ k_spmv_rows(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ c
             const double *__restrict__ val, const double *__restrict__ x, double *__restrict__ y,
             const double *__restrict__ b, const DevState *st, int check_halt)
 {
+    IGS_PDL_ENTER();
     if (check_halt && halted(st)) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -254,6 +255,7 @@ k_spmv_warp(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ c
             const double *__restrict__ val, const double *__restrict__ x, double *__restrict__ y,
             const double *__restrict__ b, const DevState *st, int check_halt)
 {
+    IGS_PDL_ENTER();
     if (check_halt && halted(st)) return;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -287,6 +289,7 @@ k_dots(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t rows
        const double *__restrict__ x0, const double *__restrict__ x1, double *__restrict__ part,
        const DevState *st, int check_halt)
 {
+    IGS_PDL_ENTER();
     if (check_halt && halted(st)) return;
     __shared__ double red[NQ][kStreamThreads];
     const int rb = blockIdx.x, G = gridDim.y, cg = blockIdx.y;
@@ -356,6 +359,7 @@ k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coe
          double alpha, const double *src, double *out, int norm_last, int p_from_state,
          DevState *st, int check_halt)
 {
+    IGS_PDL_ENTER();
     if (check_halt && halted(st)) return;
     extern __shared__ double sc[];
     if (p_from_state) p = st->ncols;
@@ -415,6 +419,7 @@ k_update_dots(double *V, int64_t ld, int p, int64_t n, int64_t rows_per_block,
               double *__restrict__ bpart, double *__restrict__ gpart, int *__restrict__ counters,
               int group, DevState *st)
 {
+    IGS_PDL_ENTER();
     if (halted(st)) return;
     extern __shared__ double smem[];
     constexpr int ldt = TR + 1;          // padded tile stride
@@ -543,6 +548,7 @@ __global__ void __launch_bounds__(kStreamThreads)
 k_norms(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
         const double *__restrict__ c, double *__restrict__ part, int nvec)
 {
+    IGS_PDL_ENTER();
     __shared__ double sh[kStreamThreads];
     const double *vs[3] = {a, b, c};
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -565,6 +571,7 @@ k_norms(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
 __global__ void __launch_bounds__(kStreamThreads)
 k_scale(int64_t n, const double *src, double *dst, int which, const DevState *st, int check_halt)
 {
+    IGS_PDL_ENTER();
     if (check_halt && halted(st)) return;
     const double f = which == 0 ? st->inv_rho : st->inv_gamma;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -595,6 +602,7 @@ static SmallArgs small_args(const Workspace &w)
 // Solve-level initialisation of the device state.
 __global__ void k_init_state(DevState *st, double tol, double normA)
 {
+    IGS_PDL_ENTER();
     if (threadIdx.x == 0) {
         DevState s = {};
         s.tol = tol;
@@ -606,6 +614,7 @@ __global__ void k_init_state(DevState *st, double tol, double normA)
 // ||b|| from its partial sums of squares.
 __global__ void __launch_bounds__(kSmallThreads) k_bnorm(const double *part, int nblk, DevState *st)
 {
+    IGS_PDL_ENTER();
     __shared__ double out[1];
     reduce_partials(part, 1, nblk, out);
     if (threadIdx.x == 0) st->bnorm = sqrt(out[0]);
@@ -616,6 +625,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_bnorm(const double *part, int
 // (eq. "nrbe").
 __global__ void __launch_bounds__(kSmallThreads) k_beta(const double *part, int nblk, DevState *st)
 {
+    IGS_PDL_ENTER();
     __shared__ double out[2];
     reduce_partials(part, 2, nblk, out);
     if (threadIdx.x == 0) {
@@ -629,6 +639,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_beta(const double *part, int 
 // Cycle start (Alg. 4.1 step 1): rho = ||r0||, g = rho e1, stop-test denominator, flags.
 __global__ void __launch_bounds__(kSmallThreads) k_cycle_start(SmallArgs a, int mmax)
 {
+    IGS_PDL_ENTER();
     DevState *st = a.st;
     for (int i = threadIdx.x; i <= mmax; i += blockDim.x) a.g[i] = 0.0;
     if (threadIdx.x == 0) {
@@ -653,6 +664,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_cycle_start(SmallArgs a, int 
 // Step 2 (priming): H_{1,1} = v_1^T w_2; the update w_2 -= H_{1,1} v_1 follows.
 __global__ void __launch_bounds__(kSmallThreads) k_prime(SmallArgs a, int nrb)
 {
+    IGS_PDL_ENTER();
     if (halted(a.st)) return;
     __shared__ double out[1];
     reduce_partials(a.part, 1, nrb, out);
@@ -669,6 +681,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_prime(SmallArgs a, int nrb)
 // Partials: value c < p-1 is V[:,c].w, value p-1 is w.w, value p+c is V[:,c].z.
 __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, int gs, int nrb)
 {
+    IGS_PDL_ENTER();
     DevState *st = a.st;
     if (halted(st)) return;
     if (st->stop_reason != 0) {  // the previous column met the stop test
@@ -755,6 +768,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
 //   r^(3) = (I + L_{k-1})^{-1} r^(2),  H_{1:k-1,k-1} = r^(1) + r^(3).
 __global__ void __launch_bounds__(kSmallThreads) k_step_b(SmallArgs a, int k, int nrb)
 {
+    IGS_PDL_ENTER();
     DevState *st = a.st;
     if (halted(st)) return;
     extern __shared__ double dsm[];
@@ -774,6 +788,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_b(SmallArgs a, int k, in
 // c < m is V[:,c].w, value m is w.w.
 __global__ void __launch_bounds__(kSmallThreads) k_flush(SmallArgs a, int m, int nrb)
 {
+    IGS_PDL_ENTER();
     DevState *st = a.st;
     if (halted(st)) return;
     if (st->stop_reason != 0) {
@@ -834,6 +849,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_flush(SmallArgs a, int m, int
 // |g_{j+1}| <= tol (||b|| + ||A|| ||x0||).
 __global__ void __launch_bounds__(kGivensThreads) k_givens(SmallArgs a, int j)
 {
+    IGS_PDL_ENTER();
     DevState *st = a.st;
     const int stop_cols = st->stop_cols;
     if (st->stop_reason < 0) return;
@@ -924,6 +940,7 @@ __global__ void __launch_bounds__(kGivensThreads) k_givens(SmallArgs a, int j)
 // column oriented over the block), st->ncols = p.
 __global__ void __launch_bounds__(kSmallThreads) k_lsq(SmallArgs a, int m)
 {
+    IGS_PDL_ENTER();
     DevState *st = a.st;
     __shared__ double ys[kMaxRestart + 1];
     __shared__ int s_p;
@@ -961,6 +978,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_lsq(SmallArgs a, int m)
 __global__ void k_transpose(const double *__restrict__ src, int ld_src, int rows, int cols,
                             double *__restrict__ dst, int ld_dst)
 {
+    IGS_PDL_ENTER();
     const int64_t total = (int64_t)rows * cols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -1041,10 +1059,10 @@ cudaError_t launch_spmv(const Workspace &w, const double *x, double *y, const do
     const int64_t want = (w.n + per_block - 1) / per_block;
     const int grid = (int)(want < (int64_t)1 << 30 ? want : (int64_t)1 << 30);
     if (w.spmv_warp_rows)
-        k_spmv_warp<<<grid, kStreamThreads, 0, s>>>(w.n, w.rowptr, w.colind, w.val, x, y, b, w.st,
+        launch_k(false, k_spmv_warp, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.rowptr, w.colind, w.val, x, y, b, w.st,
                                                     check_halt);
     else
-        k_spmv_rows<<<grid, kStreamThreads, 0, s>>>(w.n, w.rowptr, w.colind, w.val, x, y, b, w.st,
+        launch_k(false, k_spmv_rows, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.rowptr, w.colind, w.val, x, y, b, w.st,
                                                     check_halt);
     return cudaGetLastError();
 }
@@ -1057,10 +1075,10 @@ cudaError_t launch_dots(const Workspace &w, int p, const double *x0, const doubl
     const int64_t n4 = (w.n + 3) & ~int64_t(3);
     dim3 grid(pl.rblocks, pl.groups);
     if (x1)
-        k_dots<2><<<grid, kStreamThreads, 0, s>>>(w.V, w.ld, p, n4, pl.rows, x0, x1, w.part, w.st,
+        launch_k(false, k_dots<2>, dim3(grid), dim3(kStreamThreads), 0, s, w.V, w.ld, p, n4, pl.rows, x0, x1, w.part, w.st,
                                                   check_halt);
     else
-        k_dots<1><<<grid, kStreamThreads, 0, s>>>(w.V, w.ld, p, n4, pl.rows, x0, nullptr, w.part,
+        launch_k(false, k_dots<1>, dim3(grid), dim3(kStreamThreads), 0, s, w.V, w.ld, p, n4, pl.rows, x0, nullptr, w.part,
                                                   w.st, check_halt);
     return cudaGetLastError();
 }
@@ -1074,7 +1092,7 @@ cudaError_t launch_update(const Workspace &w, int p, const double *coef, bool ne
     // one row per thread: the whole vector is resident at once (occupancy, not a grid-stride
     // loop, hides the loads' latency)
     const int grid = (int)((w.n + kStreamThreads - 1) / kStreamThreads);
-    k_update<<<grid, kStreamThreads, smem, s>>>(w.V, w.ld, p, w.n, coef, neg_coef ? 1 : 0,
+    launch_k(false, k_update, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef, neg_coef ? 1 : 0,
                                                           alpha, src, out, norm_last ? 1 : 0,
                                                           p_from_state ? 1 : 0, w.st,
                                                           check_halt ? 1 : 0);
@@ -1105,7 +1123,7 @@ cudaError_t launch_update_dots(const Workspace &w, int p, const double *coef, co
     const int64_t rows = (w.n + blocks - 1) / blocks;
     const int nblk = (int)((w.n + rows - 1) / rows);
     const int ngroups = (nblk + kFusedGroup - 1) / kFusedGroup;
-    k_update_dots<kFusedRows><<<nblk, kFusedRows, smem, s>>>(w.V, w.ld, p, w.n, rows, coef, z, u, w.bpart,
+    launch_k(false, k_update_dots<kFusedRows>, dim3(nblk), dim3(kFusedRows), smem, s, w.V, w.ld, p, w.n, rows, coef, z, u, w.bpart,
                                                              w.part, w.counters, kFusedGroup, w.st);
     if (ngroups_out) *ngroups_out = ngroups;
     return cudaGetLastError();
@@ -1116,7 +1134,7 @@ cudaError_t launch_norms(const Workspace &w, const double *a, const double *b, c
 {
     const int grid = w.num_sms;
     const int nvec = !a ? 0 : !b ? 1 : !c ? 2 : 3;
-    k_norms<<<grid, kStreamThreads, 0, s>>>(w.n, a, b, c, w.part, nvec);
+    launch_k(false, k_norms, dim3(grid), dim3(kStreamThreads), 0, s, w.n, a, b, c, w.part, nvec);
     if (blocks_out) *blocks_out = grid;
     return cudaGetLastError();
 }
@@ -1124,37 +1142,37 @@ cudaError_t launch_norms(const Workspace &w, const double *a, const double *b, c
 cudaError_t launch_scale(const Workspace &w, const double *src, double *dst, int which,
                          bool check_halt, cudaStream_t s)
 {
-    k_scale<<<stream_grid(w), kStreamThreads, 0, s>>>(w.n, src, dst, which, w.st, check_halt ? 1 : 0);
+    launch_k(false, k_scale, dim3(stream_grid(w)), dim3(kStreamThreads), 0, s, w.n, src, dst, which, w.st, check_halt ? 1 : 0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init_state(const Workspace &w, double tol, double normA, cudaStream_t s)
 {
-    k_init_state<<<1, 32, 0, s>>>(w.st, tol, normA);
+    launch_k(w.pdl, k_init_state, dim3(1), dim3(32), 0, s, w.st, tol, normA);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bnorm(const Workspace &w, int nblk, cudaStream_t s)
 {
-    k_bnorm<<<1, kSmallThreads, 0, s>>>(w.part, nblk, w.st);
+    launch_k(w.pdl, k_bnorm, dim3(1), dim3(kSmallThreads), 0, s, w.part, nblk, w.st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_beta(const Workspace &w, int nblk, cudaStream_t s)
 {
-    k_beta<<<1, kSmallThreads, 0, s>>>(w.part, nblk, w.st);
+    launch_k(w.pdl, k_beta, dim3(1), dim3(kSmallThreads), 0, s, w.part, nblk, w.st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cycle_start(const Workspace &w, int, cudaStream_t s)
 {
-    k_cycle_start<<<1, kSmallThreads, 0, s>>>(small_args(w), w.mmax);
+    launch_k(w.pdl, k_cycle_start, dim3(1), dim3(kSmallThreads), 0, s, small_args(w), w.mmax);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prime(const Workspace &w, const DotsPlan &pl, cudaStream_t s)
 {
-    k_prime<<<1, kSmallThreads, 0, s>>>(small_args(w), pl.rblocks);
+    launch_k(w.pdl, k_prime, dim3(1), dim3(kSmallThreads), 0, s, small_args(w), pl.rblocks);
     return cudaGetLastError();
 }
 
@@ -1193,32 +1211,32 @@ cudaError_t configure_kernels(const Workspace &w)
 cudaError_t launch_step_a(const Workspace &w, int k, int gs, const DotsPlan &pl, cudaStream_t s)
 {
     const size_t smem = small_solve_smem(k - 1, 5);
-    k_step_a<<<1, kSmallThreads, smem, s>>>(small_args(w), k, gs, pl.rblocks);
+    launch_k(w.pdl, k_step_a, dim3(1), dim3(kSmallThreads), smem, s, small_args(w), k, gs, pl.rblocks);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_b(const Workspace &w, int k, const DotsPlan &pl, cudaStream_t s)
 {
     const size_t smem = small_solve_smem(k - 1, 3);
-    k_step_b<<<1, kSmallThreads, smem, s>>>(small_args(w), k, pl.rblocks);
+    launch_k(w.pdl, k_step_b, dim3(1), dim3(kSmallThreads), smem, s, small_args(w), k, pl.rblocks);
     return cudaGetLastError();
 }
 
 cudaError_t launch_flush(const Workspace &w, int m, const DotsPlan &pl, cudaStream_t s)
 {
-    k_flush<<<1, kSmallThreads, 0, s>>>(small_args(w), m, pl.rblocks);
+    launch_k(w.pdl, k_flush, dim3(1), dim3(kSmallThreads), 0, s, small_args(w), m, pl.rblocks);
     return cudaGetLastError();
 }
 
 cudaError_t launch_givens(const Workspace &w, int j, cudaStream_t s)
 {
-    k_givens<<<1, kGivensThreads, 0, s>>>(small_args(w), j);
+    launch_k(w.pdl, k_givens, dim3(1), dim3(kGivensThreads), 0, s, small_args(w), j);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lsq(const Workspace &w, int m, cudaStream_t s)
 {
-    k_lsq<<<1, kSmallThreads, 0, s>>>(small_args(w), m);
+    launch_k(w.pdl, k_lsq, dim3(1), dim3(kSmallThreads), 0, s, small_args(w), m);
     return cudaGetLastError();
 }
 
@@ -1229,7 +1247,7 @@ cudaError_t launch_transpose(const double *src, int ld_src, int rows, int cols, 
     int grid = (int)((total + 255) / 256);
     if (grid < 1) grid = 1;
     if (grid > 4096) grid = 4096;
-    k_transpose<<<grid, 256, 0, s>>>(src, ld_src, rows, cols, dst, ld_dst);
+    launch_k(false, k_transpose, dim3(grid), dim3(256), 0, s, src, ld_src, rows, cols, dst, ld_dst);
     return cudaGetLastError();
 }
 
@@ -1238,22 +1256,22 @@ cudaError_t estimate_norm2(const Workspace &w, const int *at_rowptr, const int *
 {
     // x: w.t, A x: w.z, A^T (A x): w.u; lambda in w.y[0]
     const int grid = stream_grid(w);
-    k_power_init<<<grid, kStreamThreads, 0, s>>>(w.n, w.t);
+    launch_k(false, k_power_init, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.t);
     for (int it = 0; it < iters; ++it) {
         if (w.spmv_warp_rows) {
-            k_spmv_warp<<<grid, kStreamThreads, 0, s>>>(w.n, w.rowptr, w.colind, w.val, w.t, w.z,
+            launch_k(false, k_spmv_warp, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.rowptr, w.colind, w.val, w.t, w.z,
                                                         nullptr, w.st, 0);
-            k_spmv_warp<<<grid, kStreamThreads, 0, s>>>(w.n, at_rowptr, at_colind, at_val, w.z, w.u,
+            launch_k(false, k_spmv_warp, dim3(grid), dim3(kStreamThreads), 0, s, w.n, at_rowptr, at_colind, at_val, w.z, w.u,
                                                         nullptr, w.st, 0);
         } else {
-            k_spmv_rows<<<grid, kStreamThreads, 0, s>>>(w.n, w.rowptr, w.colind, w.val, w.t, w.z,
+            launch_k(false, k_spmv_rows, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.rowptr, w.colind, w.val, w.t, w.z,
                                                         nullptr, w.st, 0);
-            k_spmv_rows<<<grid, kStreamThreads, 0, s>>>(w.n, at_rowptr, at_colind, at_val, w.z, w.u,
+            launch_k(false, k_spmv_rows, dim3(grid), dim3(kStreamThreads), 0, s, w.n, at_rowptr, at_colind, at_val, w.z, w.u,
                                                         nullptr, w.st, 0);
         }
-        k_norms<<<w.num_sms, kStreamThreads, 0, s>>>(w.n, w.u, nullptr, nullptr, w.part, 1);
-        k_power_norm<<<1, kSmallThreads, 0, s>>>(w.part, w.num_sms, w.y);
-        k_power_scale<<<grid, kStreamThreads, 0, s>>>(w.n, w.u, w.y);
+        launch_k(false, k_norms, dim3(w.num_sms), dim3(kStreamThreads), 0, s, w.n, w.u, nullptr, nullptr, w.part, 1);
+        launch_k(false, k_power_norm, dim3(1), dim3(kSmallThreads), 0, s, w.part, w.num_sms, w.y);
+        launch_k(false, k_power_scale, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.u, w.y);
         cudaMemcpyAsync(w.t, w.u, sizeof(double) * (size_t)w.n, cudaMemcpyDeviceToDevice, s);
     }
     double lam = 0.0;

@@ -131,6 +131,7 @@ k_update_dots_tma(double *V, int64_t ld, int p, int64_t n, int64_t rows_per_bloc
                   double *__restrict__ bpart, double *__restrict__ gpart, int *__restrict__ counters,
                   int group, DevState *st)
 {
+    IGS_PDL_ENTER();
     if (st->halt) return;
     constexpr int kColStride = kTR + 2;
     constexpr int TPR = kThreads / kTR;  // threads per row in the row phase (2, 4 or 8)
@@ -302,6 +303,7 @@ k_update_tma(double *V, int64_t ld, int p, int64_t n, int64_t rows_per_block,
              const double *__restrict__ coef, double alpha, const double *src, double *out,
              int norm_last, DevState *st)
 {
+    IGS_PDL_ENTER();
     if (st->halt) return;
     constexpr int kColStride = kTR + 2;
     constexpr int TPR = kThreads / kTR;  // threads per row (2, 4 or 8)
@@ -432,7 +434,7 @@ static cudaError_t launch_ud(const Workspace &w, int p, const double *coef, cons
     const int blocks = tma_blocks(w, (const void *)k_update_dots_tma<TR>, smem);
     const int64_t rows = tma_rows(w.n, blocks);
     const int nblk = (int)((w.n + rows - 1) / rows);
-    k_update_dots_tma<TR><<<nblk, kThreads, smem, s>>>(w.V, w.ld, p, w.n, rows, coef, z, u, w.bpart, w.part,
+    launch_k(false, k_update_dots_tma<TR>, dim3(nblk), dim3(kThreads), smem, s, w.V, w.ld, p, w.n, rows, coef, z, u, w.bpart, w.part,
                                                        w.counters, kFusedGroup, w.st);
     if (ngroups_out) *ngroups_out = (nblk + kFusedGroup - 1) / kFusedGroup;
     return cudaGetLastError();
@@ -446,7 +448,7 @@ static cudaError_t launch_u(const Workspace &w, int p, const double *coef, doubl
     const int blocks = tma_blocks(w, (const void *)k_update_tma<TR>, smem);
     const int64_t rows = tma_rows(w.n, blocks);
     const int nblk = (int)((w.n + rows - 1) / rows);
-    k_update_tma<TR><<<nblk, kThreads, smem, s>>>(w.V, w.ld, p, w.n, rows, coef, alpha, src, out,
+    launch_k(false, k_update_tma<TR>, dim3(nblk), dim3(kThreads), smem, s, w.V, w.ld, p, w.n, rows, coef, alpha, src, out,
                                                   norm_last ? 1 : 0, w.st);
     return cudaGetLastError();
 }

@@ -14,9 +14,9 @@ from typing import Any
 
 import numpy as np
 
-__all__ = ["Solver", "IGSError", "load_library", "library_path", "status_string",
+__all__ = ["Solver", "BatchSolver", "block_csr", "IGSError", "load_library", "library_path", "status_string",
            "OK", "NOT_CONVERGED", "BREAKDOWN", "EINVAL", "ENOMEM", "ECUDA", "ENUMERIC",
-           "KCLASS_NAMES", "EXPORTED_SYMBOLS"]
+           "KCLASS_NAMES", "EXPORTED_SYMBOLS", "EXPORTED_BATCH_SYMBOLS"]
 
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, ENOTIMPL = -1, -2, -3, -4, -5, -6
@@ -26,6 +26,10 @@ KCLASS_NAMES = ["spmv", "dots", "update", "small", "cycle"]
 EXPORTED_SYMBOLS = ["igs_create", "igs_destroy", "igs_solve", "igs_arnoldi", "igs_spmv",
                     "igs_get_info", "igs_profile_enable", "igs_profile_get", "igs_launch_count",
                     "igs_status_string", "igs_last_error", "igs_block_dots_static"]
+# Every function declared in include/igs_batch.h.
+EXPORTED_BATCH_SYMBOLS = ["igs_batch_create", "igs_batch_destroy", "igs_batch_solve",
+                          "igs_batch_set_config", "igs_batch_tune", "igs_batch_get_info",
+                          "igs_batch_get_norms", "igs_batch_last_error"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -68,6 +72,35 @@ class _Profile(C.Structure):
                 ("flops", C.c_double * 5)]
 
 
+class _BatchOpts(C.Structure):
+    _fields_ = [("stream", C.c_void_p), ("device", C.c_int), ("restart_m", C.c_int),
+                ("A_norm2", C.c_void_p), ("norm2_iters", C.c_int), ("block_threads", C.c_int),
+                ("blocks_per_sm", C.c_int)]
+
+
+class _BatchSolveOpts(C.Structure):
+    _fields_ = [("gs_iters", C.c_int), ("tol_beta", C.c_double), ("max_restarts", C.c_int),
+                ("inputs_on_device", C.c_int)]
+
+
+class _BatchResult(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("beta", C.c_void_p), ("status", C.c_void_p),
+                ("steps", C.c_void_p), ("cycles", C.c_void_p), ("total_steps", C.c_int64),
+                ("n_ok", C.c_int), ("n_not_converged", C.c_int), ("n_breakdown", C.c_int),
+                ("n_numeric", C.c_int), ("device_ms", C.c_double)]
+
+
+class _TuneEntry(C.Structure):
+    _fields_ = [("block_threads", C.c_int), ("blocks_per_sm", C.c_int), ("ms", C.c_double)]
+
+
+class _BatchInfo(C.Structure):
+    _fields_ = [("count", C.c_int), ("total_rows", C.c_int64), ("nnz", C.c_int64),
+                ("max_rows", C.c_int), ("restart_m", C.c_int), ("block_threads", C.c_int),
+                ("blocks_per_sm", C.c_int), ("num_sms", C.c_int), ("smem_bytes", C.c_int64),
+                ("basis_bytes", C.c_int64), ("n_tune", C.c_int), ("tune", _TuneEntry * 32)]
+
+
 _lib = None
 
 
@@ -105,6 +138,22 @@ def load_library(path: str | None = None):
     lib.igs_last_error.restype = C.c_char_p
     lib.igs_block_dots_static.argtypes = [vp, i64, i32, i64, vp, vp, vp, vp]
     lib.igs_block_dots_static.restype = i32
+    lib.igs_batch_create.argtypes = [C.POINTER(vp), i32, vp, vp, vp, vp, C.POINTER(_BatchOpts)]
+    lib.igs_batch_create.restype = i32
+    lib.igs_batch_destroy.argtypes = [vp]
+    lib.igs_batch_destroy.restype = None
+    lib.igs_batch_solve.argtypes = [vp, vp, vp, C.POINTER(_BatchSolveOpts), C.POINTER(_BatchResult)]
+    lib.igs_batch_solve.restype = i32
+    lib.igs_batch_set_config.argtypes = [vp, i32, i32]
+    lib.igs_batch_set_config.restype = i32
+    lib.igs_batch_tune.argtypes = [vp, i32, dbl, i32]
+    lib.igs_batch_tune.restype = i32
+    lib.igs_batch_get_info.argtypes = [vp, C.POINTER(_BatchInfo)]
+    lib.igs_batch_get_info.restype = i32
+    lib.igs_batch_get_norms.argtypes = [vp, vp]
+    lib.igs_batch_get_norms.restype = i32
+    lib.igs_batch_last_error.argtypes = [vp]
+    lib.igs_batch_last_error.restype = C.c_char_p
     if path is None:
         _lib = lib
     return lib
@@ -283,3 +332,156 @@ class Solver:
         self._lib.igs_profile_get(self._h, C.byref(p))
         return {name: {"ms": p.ms[i], "launches": int(p.launches[i]), "bytes": p.bytes[i],
                        "flops": p.flops[i]} for i, name in enumerate(KCLASS_NAMES)}
+
+
+# ----------------------------------------------------------------------------------------
+# Batched solver (include/igs_batch.h)
+# ----------------------------------------------------------------------------------------
+def block_csr(systems):
+    """Concatenate square CSR systems (objects with n, rowptr, colind, val) into the
+    block-diagonal CSR that ``igs_batch_create`` takes: ``(sys_ptr, rowptr, colind, val)``
+    with global column indices."""
+    ns = np.array([int(A.n) for A in systems], dtype=np.int64)
+    sys_ptr = np.zeros(len(systems) + 1, dtype=np.int64)
+    np.cumsum(ns, out=sys_ptr[1:])
+    nnzs = np.array([int(A.rowptr[-1]) for A in systems], dtype=np.int64)
+    nz_off = np.zeros(len(systems) + 1, dtype=np.int64)
+    np.cumsum(nnzs, out=nz_off[1:])
+    rowptr = np.empty(int(sys_ptr[-1]) + 1, dtype=np.int64)
+    rowptr[-1] = nz_off[-1]
+    colind = np.empty(int(nz_off[-1]), dtype=np.int32)
+    val = np.empty(int(nz_off[-1]), dtype=np.float64)
+    for s, A in enumerate(systems):
+        r0, r1 = int(sys_ptr[s]), int(sys_ptr[s + 1])
+        rowptr[r0:r1] = np.asarray(A.rowptr[:-1], dtype=np.int64) + nz_off[s]
+        colind[nz_off[s]:nz_off[s + 1]] = np.asarray(A.colind, dtype=np.int64) + r0
+        val[nz_off[s]:nz_off[s + 1]] = A.val
+    return sys_ptr, rowptr, colind, val
+
+
+class BatchSolver:
+    """Many independent systems solved by one persistent launch (``igs_batch_create``).
+
+    ``systems`` is a list of CSR objects (n, rowptr, colind, val) or a tuple
+    ``(sys_ptr, rowptr, colind, val)`` in block-diagonal form.  ``A_norm2``: per-system
+    ||A_s||_2 (sequence) or None to estimate them on the GPU.  ``block_threads`` and
+    ``blocks_per_sm`` both 0: tune the launch configuration at creation."""
+
+    def __init__(self, systems, m: int = 50, A_norm2=None, device: int = 0,
+                 stream: int | None = None, block_threads: int = 0, blocks_per_sm: int = 0,
+                 norm2_iters: int = 100):
+        self._lib = load_library()
+        if isinstance(systems, tuple):
+            sys_ptr, rowptr, colind, val = systems
+        else:
+            sys_ptr, rowptr, colind, val = block_csr(systems)
+        self.sys_ptr = np.ascontiguousarray(sys_ptr, dtype=np.int64)
+        self.count = len(self.sys_ptr) - 1
+        self.N = int(self.sys_ptr[-1])
+        rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(colind, dtype=np.int32)
+        va = np.ascontiguousarray(val, dtype=np.float64)
+        nrm = None
+        if A_norm2 is not None:
+            nrm = np.ascontiguousarray(A_norm2, dtype=np.float64)
+            if nrm.shape != (self.count,):
+                raise ValueError(f"A_norm2: need {self.count} values")
+        opts = _BatchOpts(C.c_void_p(stream) if stream else None, int(device), int(m),
+                          C.c_void_p(nrm.ctypes.data) if nrm is not None else None,
+                          int(norm2_iters), int(block_threads), int(blocks_per_sm))
+        h = C.c_void_p()
+        rc = self._lib.igs_batch_create(C.byref(h), self.count, C.c_void_p(self.sys_ptr.ctypes.data),
+                                        C.c_void_p(rp.ctypes.data), C.c_void_p(ci.ctypes.data),
+                                        C.c_void_p(va.ctypes.data), C.byref(opts))
+        if rc != OK:
+            raise IGSError(rc, "igs_batch_create")
+        self._h = h
+        self.m = int(m)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.igs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _err(self, rc: int, what: str):
+        raise IGSError(rc, f"{what}: {self._lib.igs_status_string(rc).decode()}: "
+                           f"{self._lib.igs_batch_last_error(self._h).decode()}")
+
+    @property
+    def info(self) -> dict:
+        inf = _BatchInfo()
+        self._lib.igs_batch_get_info(self._h, C.byref(inf))
+        out = {k: getattr(inf, k) for k, _ in _BatchInfo._fields_ if k != "tune"}
+        out["tune"] = [(inf.tune[i].block_threads, inf.tune[i].blocks_per_sm, inf.tune[i].ms)
+                       for i in range(inf.n_tune)]
+        return out
+
+    def norms(self) -> np.ndarray:
+        out = np.empty(self.count)
+        self._lib.igs_batch_get_norms(self._h, C.c_void_p(out.ctypes.data))
+        return out
+
+    def set_config(self, block_threads: int, blocks_per_sm: int):
+        rc = self._lib.igs_batch_set_config(self._h, int(block_threads), int(blocks_per_sm))
+        if rc != OK:
+            self._err(rc, "igs_batch_set_config")
+
+    def tune(self, gs: int = 2, tol: float = 1e-12, max_restarts: int = 20):
+        rc = self._lib.igs_batch_tune(self._h, int(gs), float(tol), int(max_restarts))
+        if rc != OK:
+            self._err(rc, "igs_batch_tune")
+
+    def solve(self, b, x0=None, gs: int = 2, tol: float = 1e-12, max_restarts: int = 20,
+              x_out=None, out=None) -> dict:
+        """Solve every system (``igs_batch_solve``).  Host numpy ``b`` gives numpy results;
+        a CUDA tensor ``b`` keeps everything on the device (``out`` may pass preallocated
+        device tensors x, beta, status, steps, cycles).  Returns ``dict(x, beta, status,
+        steps, cycles, rc, total_steps, n_ok, n_not_converged, n_breakdown, n_numeric,
+        device_ms)``."""
+        bp, dev, kb = _vec_arg(b, self.N, "b")
+        if x0 is not None:
+            xp, dev0, kx = _vec_arg(x0, self.N, "x0")
+            if dev0 != dev:
+                raise ValueError("b and x0 must both be host or both be device arrays")
+        else:
+            xp, kx = None, None
+        if dev:
+            import torch
+            o = dict(out or {})
+            dv = b.device
+            if x_out is not None:
+                o["x"] = x_out
+            o.setdefault("x", torch.empty(self.N, dtype=torch.float64, device=dv))
+            o.setdefault("beta", torch.empty(self.count, dtype=torch.float64, device=dv))
+            o.setdefault("status", torch.empty(self.count, dtype=torch.int32, device=dv))
+            o.setdefault("steps", torch.empty(self.count, dtype=torch.int64, device=dv))
+            o.setdefault("cycles", torch.empty(self.count, dtype=torch.int32, device=dv))
+            ptr = {k: C.c_void_p(v.data_ptr()) for k, v in o.items()}
+        else:
+            o = {"x": np.empty(self.N) if x_out is None else x_out,
+                 "beta": np.empty(self.count), "status": np.empty(self.count, dtype=np.int32),
+                 "steps": np.empty(self.count, dtype=np.int64),
+                 "cycles": np.empty(self.count, dtype=np.int32)}
+            ptr = {k: C.c_void_p(v.ctypes.data) for k, v in o.items()}
+        res = _BatchResult(ptr["x"], ptr["beta"], ptr["status"], ptr["steps"], ptr["cycles"],
+                           0, 0, 0, 0, 0, 0.0)
+        opts = _BatchSolveOpts(int(gs), float(tol), int(max_restarts), 1 if dev else 0)
+        rc = self._lib.igs_batch_solve(self._h, bp, xp, C.byref(opts), C.byref(res))
+        if rc < 0 and rc != ENUMERIC:
+            self._err(rc, "igs_batch_solve")
+        o.update(rc=rc, total_steps=int(res.total_steps), n_ok=res.n_ok,
+                 n_not_converged=res.n_not_converged, n_breakdown=res.n_breakdown,
+                 n_numeric=res.n_numeric, device_ms=res.device_ms)
+        return o

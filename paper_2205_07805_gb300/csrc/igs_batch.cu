@@ -15,8 +15,9 @@
 // Determinism: the arithmetic of a system depends only on that system (its n, its CSR rows
 // and the solve options), never on the CTA, the block size, the number of resident CTAs or
 // the other systems of the batch:
-//   - a dot product is summed over fixed row slices (slice_rows(n), a function of n only),
-//     each slice in row order with two interleaved chains, then over slices in order;
+//   - a dot product is summed over row slices whose number depends on n and the column count
+//     only (pick_slices), each slice in row order with two interleaved chains, then over
+//     the slices in order;
 //   - every row of an update or SpMV is one thread's fixed-order chain;
 //   - the triangular solves, the Givens scan and the back substitution run on warp 0 with
 //     fixed lane roles.
@@ -24,9 +25,9 @@
 // in a batch, and under every launch configuration the tuner may pick.
 //
 // Memory: each CTA (slot) owns a basis V of (m+1) columns with leading dimension
-// round_up(n, 4) in HBM (it is re-read from L2 when the working set fits); the Krylov
-// vector z/u, the slice partial sums, L (packed strictly-lower, column-major), R (packed
-// upper, column-major) and the small vectors are in shared memory.
+// round_up(n, 4) and the Givens factor R (packed upper, column-major) in HBM (re-read from
+// L2 when the working set fits); the Krylov vector z/u, the slice partial sums, L (packed
+// strictly-lower, column-major) and the small vectors are in shared memory.
 #include "../../include/igs.h"
 #include "../../include/igs_batch.h"
 #include "igs_internal.h"
@@ -45,16 +46,36 @@ namespace batch {
 constexpr int kMaxM = IGS_BATCH_MAX_M;  // largest restart length (two rows per lane in warp solves)
 constexpr int kMaxN = IGS_BATCH_MAX_N;  // largest system (the Krylov vector is kept in shared memory)
 constexpr int kMaxSlices = 16;      // dot products are split into at most this many row slices
-constexpr int kMinSlice = 64;       // rows per slice: a multiple of 64, at least 64
 constexpr int kMaxSlotsPerSM = 8;   // largest resident CTAs per SM any configuration uses
 
 __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-// Rows per dot-product slice of a system with n2 (= n rounded up to even) rows.
-__host__ __device__ inline int slice_rows(int n2)
+// Row slices of the dot products.  A system of n2 (even) rows is cut into nsl slices of
+// whole row pairs, slice s holding pairs [s*P/nsl, (s+1)*P/nsl) (P = n2/2).  For a product
+// over pc columns, nsl is chosen in [slices_lo(n2), slices_hi(n2)] so that the nsl*pc
+// (slice, column) items leave the fewest idle lanes in the last warp; the choice depends
+// on n and pc only.
+__host__ __device__ inline int slices_hi(int n2)
 {
-    const int sl = round_up((n2 + kMaxSlices - 1) / kMaxSlices, kMinSlice);
-    return sl < kMinSlice ? kMinSlice : sl;
+    const int s = (n2 >> 1) / 4;  // at least four row pairs per slice
+    return s < 1 ? 1 : (s > kMaxSlices ? kMaxSlices : s);
+}
+__host__ __device__ inline int slices_lo(int n2) { return slices_hi(n2) < 8 ? slices_hi(n2) : 8; }
+
+__host__ __device__ inline int pick_slices(int n2, int pc)
+{
+    int best = slices_lo(n2), best_idle = 0, best_tot = 1;
+    for (int s = slices_lo(n2); s <= slices_hi(n2); ++s) {
+        const int items = s * pc;
+        const int tot = (items + 31) / 32 * 32;
+        const int idle = tot - items;
+        if (s == slices_lo(n2) || idle * best_tot < best_idle * tot) {
+            best = s;
+            best_idle = idle;
+            best_tot = tot;
+        }
+    }
+    return best;
 }
 
 // Shared-memory index of row i of the Krylov vector: two doubles of padding every 128 rows
@@ -69,7 +90,7 @@ __host__ __device__ inline int upper_base(int j) { return j * (j + 1) / 2; }
 // Offsets (in doubles) of the dynamic shared-memory arrays for a batch with largest system
 // nmax and restart m.
 struct SmemLayout {
-    int zu, part, L, R, red, r0, r1, r3, hcol, cs, sn, g, y, total;
+    int zu, part, L, red, r0, r1, r3, hcol, cs, sn, g, y, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int nmax, int m)
@@ -80,7 +101,6 @@ __host__ __device__ inline SmemLayout smem_layout(int nmax, int m)
     s.zu = o;   o += round_up(pad_idx(n2) + 2, 2);
     s.part = o; o += round_up(kMaxSlices * (m + 1) * 2, 2);
     s.L = o;    o += round_up((m + 1) * m / 2 + 1, 2);
-    s.R = o;    o += round_up(m * (m + 1) / 2 + 1, 2);
     s.red = o;  o += round_up(2 * (m + 1), 2);
     s.r0 = o;   o += round_up(m + 1, 2);
     s.r1 = o;   o += round_up(m + 1, 2);
@@ -99,12 +119,17 @@ struct Args {
     int m;
     int nmax;
     const int64_t *sys_row0;  // count+1 row offsets into the concatenated vectors
-    const int64_t *rowptr;    // N+1, global nonzero offsets
-    const int *colind;        // column index local to the system
-    const double *val;
+    // A in sliced ELL (SELL-32): slice k (32 consecutive rows of one system) holds its
+    // entries at sell_off[k] .. sell_off[k+1]-1, entry j of lane r at sell_off[k] + 32 j + r,
+    // in the row's CSR order; padding has column -1.  sys_slice0[s] is system s's first slice.
+    const int64_t *sell_off;
+    const int *sys_slice0;
+    const int *sell_col;      // column index local to the system, or -1
+    const double *sell_val;
     const double *normA;      // per system ||A_s||_2
-    double *vslots;           // per-CTA basis storage
+    double *vslots;           // per-CTA basis storage: V, then R at r_offset
     int64_t slot_stride;      // doubles per slot
+    int64_t r_offset;         // doubles from a slot's start to its R
     unsigned int *queue;      // work counter (zeroed before each launch)
     unsigned long long *summary;  // [0] total steps, [1+k] systems with status code k+4
 };
@@ -130,11 +155,12 @@ struct Run {
 struct Shared {
     double nb, normA, rho, inv, stop_den, beta, rn, xn;
     int status, cst, done, stop, cycles;
+    int swarp;  // warp of this CTA that runs the single-warp steps
     long long steps;
 };
 
 struct Sys {
-    int n, n2, ldv, sl, nsl;
+    int n, n2, ldv, slice0;
     int64_t row0;
 };
 
@@ -142,15 +168,33 @@ __device__ __forceinline__ double2 ld2(const double *p) { return *reinterpret_ca
 __device__ __forceinline__ void st2(double *p, double2 v) { *reinterpret_cast<double2 *>(p) = v; }
 
 // y = A x, or y = b - A x when b != null (rows >= n of y are set to 0).  x, b: system-local.
+// Each row is summed in its CSR order; lanes of a warp read consecutive SELL entries.
 template <bool OUT_PAD>
 __device__ void b_spmv(const Args &a, const Sys &S, const double *x, const double *b, double *y)
 {
-    const int64_t *rp = a.rowptr + S.row0;
+    const int64_t *so = a.sell_off + S.slice0;
     for (int i = threadIdx.x; i < S.n2; i += blockDim.x) {
         double acc = 0.0;
         if (i < S.n) {
-            const int64_t k1 = rp[i + 1];
-            for (int64_t k = rp[i]; k < k1; ++k) acc = fma(a.val[k], x[a.colind[k]], acc);
+            const int k = i >> 5;
+            int64_t e = so[k] + (i & 31);
+            const int64_t e1 = so[k + 1];
+            // eight entries per batch (all loads of a batch in flight together)
+            for (; e < e1; e += 256) {
+                int c[8];
+                double v[8], xv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const bool in = e + 32 * u < e1;
+                    c[u] = in ? a.sell_col[e + 32 * u] : -1;
+                    v[u] = in ? a.sell_val[e + 32 * u] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) xv[u] = c[u] >= 0 ? x[c[u]] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+            }
             if (b) acc = b[i] - acc;
         }
         y[OUT_PAD ? pad_idx(i) : i] = acc;
@@ -163,11 +207,13 @@ template <int NQ, bool X0PAD>
 __device__ void b_dots(const Sys &S, const double *V, int pc, const double *x0, const double *x1,
                        double *part, double *red)
 {
-    const int nitems = pc * S.nsl;
+    const int nsl = pick_slices(S.n2, pc);
+    const int npairs = S.n2 >> 1;
+    const int nitems = pc * nsl;
     for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
         const int c = it % pc, s = it / pc;
-        const int i0 = s * S.sl;
-        const int i1 = min(S.n2, i0 + S.sl);
+        const int i0 = 2 * (s * npairs / nsl);
+        const int i1 = 2 * ((s + 1) * npairs / nsl);
         const double *vc = V + (int64_t)c * S.ldv;
         double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
         int i = i0;
@@ -206,7 +252,7 @@ __device__ void b_dots(const Sys &S, const double *V, int pc, const double *x0, 
     __syncthreads();
     for (int v = threadIdx.x; v < pc * NQ; v += blockDim.x) {
         double acc = 0.0;
-        for (int s = 0; s < S.nsl; ++s) acc += part[s * pc * NQ + v];
+        for (int s = 0; s < nsl; ++s) acc += part[s * pc * NQ + v];
         red[v] = acc;
     }
     __syncthreads();
@@ -216,12 +262,13 @@ __device__ void b_dots(const Sys &S, const double *V, int pc, const double *x0, 
 __device__ void b_sumsq(const Sys &S, const double *v0, const double *v1, int nv, double *part,
                         double *red)
 {
-    const int nitems = nv * S.nsl;
+    const int nsl = slices_hi(S.n2);
+    const int nitems = nv * nsl;
     for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
         const int q = it % nv, s = it / nv;
         const double *v = q == 0 ? v0 : v1;
-        const int i0 = s * S.sl;
-        const int i1 = min(S.n, i0 + S.sl);
+        const int i0 = s * S.n / nsl;
+        const int i1 = (s + 1) * S.n / nsl;
         double a0 = 0.0, a1 = 0.0;
         int i = i0;
         for (; i + 1 < i1; i += 2) {
@@ -234,50 +281,56 @@ __device__ void b_sumsq(const Sys &S, const double *v0, const double *v1, int nv
     __syncthreads();
     for (int q = threadIdx.x; q < nv; q += blockDim.x) {
         double acc = 0.0;
-        for (int s = 0; s < S.nsl; ++s) acc += part[s * nv + q];
+        for (int s = 0; s < nsl; ++s) acc += part[s * nv + q];
         red[q] = acc;
     }
     __syncthreads();
 }
 
 // out[i] = alpha * src[i] - sum_{c < pc} V[i, c] coef[c] for rows i < n2 (pairs of rows per
-// thread).  When nc >= 0, column nc of V is first scaled in place by scale_nc (the lagged
-// normalisation of step 7) and the scaled column enters the sum.
+// thread).  When nc >= 0 (then nc = pc - 1), column nc of V is first scaled in place by
+// scale_nc (the lagged normalisation of step 7) and the scaled column enters the sum.
 template <bool SRC_PAD, bool OUT_PAD>
 __device__ void b_update(const Sys &S, double *V, int pc, const double *coef, double alpha,
                          const double *src, double *out, int nc, double scale_nc)
 {
     const int npairs = S.n2 >> 1;
+    // the normalised column (always the last, nc = pc - 1) is scaled and stored before the
+    // other columns are streamed, so that no store sits between their loads; its term is
+    // still added last
+    const int ps = nc >= 0 ? nc : pc;
     for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
         const int i = 2 * pr;
+        double2 vn = make_double2(0.0, 0.0);
+        if (nc >= 0) {
+            vn = ld2(V + (int64_t)nc * S.ldv + i);
+            vn.x *= scale_nc;
+            vn.y *= scale_nc;
+            st2(V + (int64_t)nc * S.ldv + i, vn);
+        }
         double sx = 0.0, sy = 0.0;
         int c = 0;
-        for (; c + 4 <= pc; c += 4) {
+        for (; c + 4 <= ps; c += 4) {
             double2 v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) v[u] = ld2(V + (int64_t)(c + u) * S.ldv + i);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (c + u == nc) {
-                    v[u].x *= scale_nc;
-                    v[u].y *= scale_nc;
-                    st2(V + (int64_t)(c + u) * S.ldv + i, v[u]);
-                }
                 const double cf = coef[c + u];
                 sx = fma(v[u].x, cf, sx);
                 sy = fma(v[u].y, cf, sy);
             }
         }
-        for (; c < pc; ++c) {
-            double2 v = ld2(V + (int64_t)c * S.ldv + i);
-            if (c == nc) {
-                v.x *= scale_nc;
-                v.y *= scale_nc;
-                st2(V + (int64_t)c * S.ldv + i, v);
-            }
+        for (; c < ps; ++c) {
+            const double2 v = ld2(V + (int64_t)c * S.ldv + i);
             const double cf = coef[c];
             sx = fma(v.x, cf, sx);
             sy = fma(v.y, cf, sy);
+        }
+        if (nc >= 0) {
+            const double cf = coef[nc];
+            sx = fma(vn.x, cf, sx);
+            sy = fma(vn.y, cf, sy);
         }
         const double2 sv = ld2(src + (SRC_PAD ? pad_idx(i) : i));
         double2 o;
@@ -411,8 +464,8 @@ __device__ double w_sumsq(const double *h, int len)
 
 // Warp 0: complete Hessenberg column j (pending entries hcol[0..j]) with subdiagonal
 // gamma: numeric check, Givens, breakdown test, in-cycle stop test.  Returns 1 to stop.
-__device__ int w_complete_column(int j, double gamma, double *sm, const SmemLayout &L, Shared &sh,
-                                 double tol)
+__device__ int w_complete_column(int j, double gamma, double *sm, const SmemLayout &L, double *R,
+                                 Shared &sh, double tol)
 {
     const int lane = threadIdx.x & 31;
     int stop = 0;
@@ -421,7 +474,7 @@ __device__ int w_complete_column(int j, double gamma, double *sm, const SmemLayo
         return 1;
     }
     const double hn2 = w_sumsq(sm + L.hcol, j + 1);
-    const double res = w_givens(j, sm + L.hcol, gamma, sm + L.cs, sm + L.sn, sm + L.g, sm + L.R);
+    const double res = w_givens(j, sm + L.hcol, gamma, sm + L.cs, sm + L.sn, sm + L.g, R);
     if (gamma == 0.0 || gamma <= kBreakdownFactor * sqrt(hn2)) {
         if (lane == 0) sh.cst = IGS_BREAKDOWN;
         stop = 1;
@@ -439,7 +492,8 @@ __device__ void b_cycle(const Args &a, const Run &run, const Sys &S, double *V, 
                         const SmemLayout &L, Shared &sh)
 {
     const int m = a.m, gs = run.gs;
-    const bool w0 = threadIdx.x < 32;
+    const bool w0 = (int)(threadIdx.x >> 5) == sh.swarp;  // the warp doing the scalar work
+    double *R = V + a.r_offset;
     const int lane = threadIdx.x & 31;
     double *zu = sm + L.zu, *part = sm + L.part, *red = sm + L.red;
     if (threadIdx.x == 0) {
@@ -474,7 +528,7 @@ __device__ void b_cycle(const Args &a, const Run &run, const Sys &S, double *V, 
         if (w0) {
             // Step 6: gamma = ||w||, the subdiagonal of column p-2, which is now complete.
             const double gamma = sqrt(red[2 * (p - 1)]);
-            int stop = w_complete_column(p - 2, gamma, sm, L, sh, run.tol);
+            int stop = w_complete_column(p - 2, gamma, sm, L, R, sh, run.tol);
             if (!stop) {
                 const double inv = 1.0 / gamma;
                 // Steps 8-9: r^(0) / gamma, its last entry once more; step 10: L row / gamma.
@@ -523,7 +577,7 @@ __device__ void b_cycle(const Args &a, const Run &run, const Sys &S, double *V, 
     // Flush: gamma_{m+1} = ||w_{m+1}|| completes column m-1.
     if (!sh.stop && sh.cst == IGS_OK && sh.done == m - 1) {
         b_sumsq(S, V + (int64_t)m * S.ldv, nullptr, 1, part, red);
-        if (w0) w_complete_column(m - 1, sqrt(red[0]), sm, L, sh, run.tol);
+        if (w0) w_complete_column(m - 1, sqrt(red[0]), sm, L, R, sh, run.tol);
         __syncthreads();
     }
 }
@@ -537,8 +591,7 @@ __device__ void b_solve_system(const Args &a, const Run &run, int sid, double *V
     S.n = (int)(a.sys_row0[sid + 1] - S.row0);
     S.n2 = round_up(S.n, 2);
     S.ldv = round_up(S.n, 4);
-    S.sl = slice_rows(S.n2);
-    S.nsl = (S.n2 + S.sl - 1) / S.sl;
+    S.slice0 = a.sys_slice0[sid];
     const double *b = run.b + S.row0;
     double *x = run.x + S.row0;
     const double *x0 = run.x0_given ? run.x0 + S.row0 : nullptr;
@@ -595,7 +648,7 @@ __device__ void b_solve_system(const Args &a, const Run &run, int sid, double *V
         }
         // x_m = x_0 + V_m y_m (y by back substitution on the Givens factor).
         if (done > 0) {
-            if (threadIdx.x < 32) w_upper_solve(done, sm + L.R, sm + L.g, sm + L.y);
+            if ((int)(threadIdx.x >> 5) == sh.swarp) w_upper_solve(done, V + a.r_offset, sm + L.g, sm + L.y);
             __syncthreads();
             b_xupdate(S, V, done, sm + L.y, x);
         }
@@ -627,13 +680,22 @@ __device__ void b_solve_system(const Args &a, const Run &run, int sid, double *V
 }
 
 // The persistent batched solver: CTAs take systems from the queue until it is empty.
-__global__ void __launch_bounds__(512) k_batch_solve(Args a, const Run *__restrict__ runp)
+// Instantiated per block size T with the register budget of MINB resident CTAs per SM.
+template <int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) k_batch_solve(Args a, const Run *__restrict__ runp)
 {
     extern __shared__ __align__(16) double sm[];
     __shared__ Shared sh;
     __shared__ Run run;
     __shared__ int s_next;
-    if (threadIdx.x == 0) run = *runp;
+    if (threadIdx.x == 0) {
+        run = *runp;
+        // Single-warp steps go to warp (hardware warp slot / 4) mod warps: CTAs that share an
+        // SM then put them on different SM sub-partitions.  Any choice gives the same results.
+        unsigned wid;
+        asm volatile("mov.u32 %0, %%warpid;" : "=r"(wid));
+        sh.swarp = (int)((wid >> 2) % (blockDim.x >> 5));
+    }
     const SmemLayout L = smem_layout(a.nmax, a.m);
     double *V = a.vslots + (int64_t)blockIdx.x * a.slot_stride;
     for (;;) {
@@ -647,9 +709,9 @@ __global__ void __launch_bounds__(512) k_batch_solve(Args a, const Run *__restri
 }
 
 // ||A_s||_2 by power iteration on A_s^T A_s (one CTA per system; At = A^T in the same
-// block-diagonal CSR form).  Start vector: a fixed hash of the row index.
-__global__ void __launch_bounds__(256) k_batch_norm2(Args a, const int64_t *__restrict__ at_rowptr,
-                                                     const int *__restrict__ at_colind,
+// sliced form).  Start vector: a fixed hash of the row index.
+__global__ void __launch_bounds__(256) k_batch_norm2(Args a, const int64_t *__restrict__ at_off,
+                                                     const int *__restrict__ at_col,
                                                      const double *__restrict__ at_val, int count,
                                                      int iters, double *__restrict__ out)
 {
@@ -657,18 +719,17 @@ __global__ void __launch_bounds__(256) k_batch_norm2(Args a, const int64_t *__re
     __shared__ double s_lam;
     const SmemLayout L = smem_layout(a.nmax, a.m);
     double *V = a.vslots + (int64_t)blockIdx.x * a.slot_stride;
-    Args at = a;
-    at.rowptr = at_rowptr;
-    at.colind = at_colind;
-    at.val = at_val;
+    Args at = a;  // A^T in the same SELL form and slicing
+    at.sell_off = at_off;
+    at.sell_col = at_col;
+    at.sell_val = at_val;
     for (int sid = blockIdx.x; sid < count; sid += gridDim.x) {
         Sys S;
         S.row0 = a.sys_row0[sid];
         S.n = (int)(a.sys_row0[sid + 1] - S.row0);
         S.n2 = round_up(S.n, 2);
         S.ldv = round_up(S.n, 4);
-        S.sl = slice_rows(S.n2);
-        S.nsl = (S.n2 + S.sl - 1) / S.sl;
+        S.slice0 = a.sys_slice0[sid];
         double *xv = V, *yv = V + S.ldv, *uv = V + 2 * (int64_t)S.ldv;
         const double sc = 1.0 / sqrt((double)S.n);
         for (int i = threadIdx.x; i < S.n; i += blockDim.x) {
@@ -696,6 +757,19 @@ __global__ void __launch_bounds__(256) k_batch_norm2(Args a, const int64_t *__re
     }
 }
 
+using BatchKernel = void (*)(Args, const Run *);
+
+// Kernel instance for a block size (128, 256 or 512 threads), else null.
+inline BatchKernel batch_kernel(int threads)
+{
+    switch (threads) {
+    case 128: return k_batch_solve<128, 5>;
+    case 256: return k_batch_solve<256, 2>;
+    case 512: return k_batch_solve<512, 1>;
+    default: return nullptr;
+    }
+}
+
 }  // namespace batch
 }  // namespace igs
 
@@ -714,10 +788,10 @@ struct igs_batch {
     size_t smem = 0;
     int max_smem_optin = 0;
     // device data
-    int64_t *sys_row0 = nullptr, *rowptr = nullptr;
-    int *colind = nullptr, *order = nullptr, *order_sample = nullptr;
-    double *val = nullptr, *normA = nullptr, *vslots = nullptr;
-    int64_t slot_stride = 0;
+    int64_t *sys_row0 = nullptr, *sell_off = nullptr;
+    int *sys_slice0 = nullptr, *sell_col = nullptr, *order = nullptr, *order_sample = nullptr;
+    double *sell_val = nullptr, *normA = nullptr, *vslots = nullptr;
+    int64_t slot_stride = 0, r_offset = 0;
     int slots_alloc = 0;
     unsigned int *queue = nullptr;
     unsigned long long *summary = nullptr;
@@ -775,12 +849,14 @@ Args make_args(const igs_batch *bt)
     a.m = bt->m;
     a.nmax = bt->nmax;
     a.sys_row0 = bt->sys_row0;
-    a.rowptr = bt->rowptr;
-    a.colind = bt->colind;
-    a.val = bt->val;
+    a.sell_off = bt->sell_off;
+    a.sys_slice0 = bt->sys_slice0;
+    a.sell_col = bt->sell_col;
+    a.sell_val = bt->sell_val;
     a.normA = bt->normA;
     a.vslots = bt->vslots;
     a.slot_stride = bt->slot_stride;
+    a.r_offset = bt->r_offset;
     a.queue = bt->queue;
     a.summary = bt->summary;
     return a;
@@ -789,7 +865,7 @@ Args make_args(const igs_batch *bt)
 int max_blocks_per_sm(igs_batch *bt, int threads, int *out)
 {
     int nb = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, igs::batch::k_batch_solve,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, igs::batch::batch_kernel(threads),
                                                                   threads, bt->smem);
     if (e != cudaSuccess) return fail(bt, IGS_ECUDA, "occupancy query", e);
     *out = nb < igs::batch::kMaxSlotsPerSM ? nb : igs::batch::kMaxSlotsPerSM;
@@ -814,7 +890,7 @@ int get_graph(igs_batch *bt, int threads, int bpsm, cudaGraphExec_t *out)
         cudaMemcpyAsync(bt->run_dev, bt->run_host, sizeof(Run), cudaMemcpyHostToDevice, cs);
         cudaMemsetAsync(bt->queue, 0, sizeof(unsigned int), cs);
         cudaMemsetAsync(bt->summary, 0, 10 * sizeof(unsigned long long), cs);
-        igs::batch::k_batch_solve<<<grid, threads, bt->smem, cs>>>(make_args(bt), bt->run_dev);
+        igs::batch::batch_kernel(threads)<<<grid, threads, bt->smem, cs>>>(make_args(bt), bt->run_dev);
         cudaError_t le = cudaGetLastError();
         cudaMemcpyAsync(bt->summary_host, bt->summary, 10 * sizeof(unsigned long long),
                         cudaMemcpyDeviceToHost, cs);
@@ -897,6 +973,68 @@ int autotune(igs_batch *bt, int gs, double tol, int max_restarts)
 
 }  // namespace
 
+namespace {
+
+// Sliced ELL (32-row slices, each as wide as its longest row) of a block-diagonal CSR with
+// system-local column indices; entries keep each row's CSR order.
+struct SellHost {
+    std::vector<int> slice0;     // count+1
+    std::vector<int64_t> off;    // slices+1
+    std::vector<int> col;
+    std::vector<double> val;
+};
+
+void build_sell(int count, const int64_t *sys_ptr, const int64_t *rp, const int *ci, const double *va,
+                SellHost &out)
+{
+    out.slice0.assign((size_t)count + 1, 0);
+    int64_t nsl = 0;
+    for (int s = 0; s < count; ++s) {
+        out.slice0[(size_t)s] = (int)nsl;
+        nsl += (sys_ptr[s + 1] - sys_ptr[s] + 31) / 32;
+    }
+    out.slice0[(size_t)count] = (int)nsl;
+    out.off.assign((size_t)nsl + 1, 0);
+    int64_t k = 0;
+    for (int s = 0; s < count; ++s)
+        for (int64_t r0 = sys_ptr[s]; r0 < sys_ptr[s + 1]; r0 += 32, ++k) {
+            const int64_t r1 = std::min(r0 + 32, sys_ptr[s + 1]);
+            int64_t w = 0;
+            for (int64_t i = r0; i < r1; ++i) w = std::max(w, rp[i + 1] - rp[i]);
+            out.off[(size_t)k + 1] = out.off[(size_t)k] + 32 * w;
+        }
+    out.col.assign((size_t)std::max<int64_t>(out.off[(size_t)nsl], 1), -1);
+    out.val.assign((size_t)std::max<int64_t>(out.off[(size_t)nsl], 1), 0.0);
+    k = 0;
+    for (int s = 0; s < count; ++s)
+        for (int64_t r0 = sys_ptr[s]; r0 < sys_ptr[s + 1]; r0 += 32, ++k) {
+            const int64_t r1 = std::min(r0 + 32, sys_ptr[s + 1]);
+            for (int64_t i = r0; i < r1; ++i)
+                for (int64_t j = 0; j < rp[i + 1] - rp[i]; ++j) {
+                    const size_t e = (size_t)(out.off[(size_t)k] + 32 * j + (i - r0));
+                    out.col[e] = ci[rp[i] + j];
+                    out.val[e] = va[rp[i] + j];
+                }
+        }
+}
+
+int upload_sell(const SellHost &h, int64_t **off, int **slice0, int **col, double **val, cudaStream_t s)
+{
+    const size_t ne = h.col.size();
+    if (dalloc(off, h.off.size()) || dalloc(col, ne) || dalloc(val, ne) ||
+        (slice0 && dalloc(slice0, h.slice0.size())))
+        return IGS_ENOMEM;
+    if (cudaMemcpyAsync(*off, h.off.data(), sizeof(int64_t) * h.off.size(), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(*col, h.col.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(*val, h.val.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, s) ||
+        (slice0 && cudaMemcpyAsync(*slice0, h.slice0.data(), sizeof(int) * h.slice0.size(),
+                                   cudaMemcpyHostToDevice, s)))
+        return IGS_ECUDA;
+    return IGS_OK;
+}
+
+}  // namespace
+
 extern "C" int igs_batch_create(igs_batch **out, int count, const int64_t *sys_ptr,
                                 const int64_t *rowptr, const int32_t *colind, const double *vals,
                                 const igs_batch_opts *opts)
@@ -966,13 +1104,16 @@ extern "C" int igs_batch_create(igs_batch **out, int count, const int64_t *sys_p
         return bail(IGS_ECUDA);
     const SmemLayout L = smem_layout(nmax, m);
     bt->smem = sizeof(double) * (size_t)L.total;
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_batch_solve) != cudaSuccess) return bail(IGS_ECUDA);
-    if (bt->smem + fa.sharedSizeBytes > (size_t)bt->max_smem_optin) return bail(IGS_EINVAL);
-    if (cudaFuncSetAttribute(k_batch_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_batch_norm2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem) !=
+    for (int t : {128, 256, 512}) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, batch_kernel(t)) != cudaSuccess) return bail(IGS_ECUDA);
+        if (bt->smem + fa.sharedSizeBytes > (size_t)bt->max_smem_optin) return bail(IGS_EINVAL);
+        if (cudaFuncSetAttribute(batch_kernel(t), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem) !=
             cudaSuccess)
+            return bail(IGS_ECUDA);
+    }
+    if (cudaFuncSetAttribute(k_batch_norm2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem) !=
+        cudaSuccess)
         return bail(IGS_ECUDA);
 
     // slots: one per CTA of the largest configuration the GPU can hold (any block size)
@@ -985,8 +1126,9 @@ extern "C" int igs_batch_create(igs_batch **out, int count, const int64_t *sys_p
     }
     if (slots_per_sm < 1) return bail(IGS_EINVAL);
     bt->slots_alloc = bt->num_sms * slots_per_sm;
-    // (m+1) basis columns; at least three for the power iteration's vectors
-    bt->slot_stride = (int64_t)std::max(m + 1, 3) * round_up(nmax, 4);
+    // (m+1) basis columns (at least three for the power iteration's vectors), then R
+    bt->r_offset = (int64_t)std::max(m + 1, 3) * round_up(nmax, 4);
+    bt->slot_stride = bt->r_offset + (int64_t)m * (m + 1) / 2;
     bt->slot_stride = (bt->slot_stride + 31) / 32 * 32;
 
     // solve order: largest system first (ties by index); the tuning sample is every 4th
@@ -1007,9 +1149,7 @@ extern "C" int igs_batch_create(igs_batch **out, int count, const int64_t *sys_p
         btune[(size_t)i] = s;
     }
 
-    if (dalloc(&bt->sys_row0, (size_t)count + 1) || dalloc(&bt->rowptr, (size_t)N + 1) ||
-        dalloc(&bt->colind, (size_t)nnz) || dalloc(&bt->val, (size_t)nnz) ||
-        dalloc(&bt->order, (size_t)count) || dalloc(&bt->order_sample, sample.size()) ||
+    if (dalloc(&bt->sys_row0, (size_t)count + 1) || dalloc(&bt->order, (size_t)count) || dalloc(&bt->order_sample, sample.size()) ||
         dalloc(&bt->normA, (size_t)count) ||
         dalloc(&bt->vslots, (size_t)bt->slots_alloc * (size_t)bt->slot_stride) ||
         dalloc(&bt->queue, 1) || dalloc(&bt->summary, 10) || dalloc(&bt->run_dev, 1) ||
@@ -1026,10 +1166,14 @@ extern "C" int igs_batch_create(igs_batch **out, int count, const int64_t *sys_p
     if (cudaEventCreate(&bt->ev0) != cudaSuccess || cudaEventCreate(&bt->ev1) != cudaSuccess)
         return bail(IGS_ECUDA);
     cudaStream_t s = bt->stream;
+    {
+        SellHost sh;
+        build_sell(count, sys_ptr, rowptr, loc.data(), vals, sh);
+        rc = upload_sell(sh, &bt->sell_off, &bt->sys_slice0, &bt->sell_col, &bt->sell_val, s);
+        if (rc != IGS_OK) return bail(rc);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return bail(IGS_ECUDA);
+    }
     if (cudaMemcpyAsync(bt->sys_row0, sys_ptr, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s) ||
-        cudaMemcpyAsync(bt->rowptr, rowptr, sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, s) ||
-        (nnz && cudaMemcpyAsync(bt->colind, loc.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s)) ||
-        (nnz && cudaMemcpyAsync(bt->val, vals, sizeof(double) * nnz, cudaMemcpyHostToDevice, s)) ||
         cudaMemcpyAsync(bt->order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s) ||
         cudaMemcpyAsync(bt->order_sample, sample.data(), sizeof(int) * sample.size(), cudaMemcpyHostToDevice, s) ||
         cudaMemcpyAsync(bt->b_tune, btune.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s) ||
@@ -1057,19 +1201,14 @@ extern "C" int igs_batch_create(igs_batch **out, int count, const int64_t *sys_p
                     tci[(size_t)dst] = (int)(i - sys_ptr[sidx]);
                     tva[(size_t)dst] = vals[k];
                 }
+        SellHost th;
+        build_sell(count, sys_ptr, trp.data(), tci.data(), tva.data(), th);
         int64_t *at_rp = nullptr;
         int *at_ci = nullptr;
         double *at_va = nullptr;
-        if (dalloc(&at_rp, (size_t)N + 1) || dalloc(&at_ci, (size_t)nnz) || dalloc(&at_va, (size_t)nnz)) {
-            cudaFree(at_rp);
-            cudaFree(at_ci);
-            cudaFree(at_va);
-            return bail(IGS_ENOMEM);
-        }
+        int urc = upload_sell(th, &at_rp, nullptr, &at_ci, &at_va, s);
         const int iters = opts->norm2_iters > 0 ? opts->norm2_iters : 100;
-        cudaError_t e = cudaMemcpyAsync(at_rp, trp.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(at_ci, tci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(at_va, tva.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s);
+        cudaError_t e = urc == IGS_OK ? cudaSuccess : cudaErrorMemoryAllocation;
         if (e == cudaSuccess) {
             const int grid = std::min(count, bt->slots_alloc);
             k_batch_norm2<<<grid, 256, bt->smem, s>>>(make_args(bt), at_rp, at_ci, at_va, count, iters, bt->normA);
@@ -1108,9 +1247,10 @@ extern "C" void igs_batch_destroy(igs_batch *bt)
     if (bt->stream) cudaStreamSynchronize(bt->stream);
     for (auto &g : bt->graphs) cudaGraphExecDestroy(g.exec);
     cudaFree(bt->sys_row0);
-    cudaFree(bt->rowptr);
-    cudaFree(bt->colind);
-    cudaFree(bt->val);
+    cudaFree(bt->sell_off);
+    cudaFree(bt->sys_slice0);
+    cudaFree(bt->sell_col);
+    cudaFree(bt->sell_val);
     cudaFree(bt->order);
     cudaFree(bt->order_sample);
     cudaFree(bt->normA);

@@ -7,6 +7,7 @@ Arnoldi columns, Givens least squares, x update and the true backward error), i.
 Arnoldi steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--gs 1|2] [--impl reference]
+                  [--workload cd2d|batched] [--no-batched]
 
 Prints one JSON line (rank 0).  `value` is device-timed throughput with b already in HBM
 (CUDA events on the library's stream); `e2e` is the same metric through the C interface
@@ -15,6 +16,11 @@ dominant kernel (the block multi-dot) against the FP64 FMA pipe (it is FP64-issu
 GB300) with its HBM throughput alongside; `cpu_baseline` times the CPU oracle on one full
 cycle of the same workload.  With --gpus N > 1 (torchrun) every rank runs an independent
 replica (the method has no data-parallel exchange on one system): weak scaling.
+
+The line also carries `batched`: the batched form (include/igs_batch.h) on 4096 banded
+systems (n ~ U{64..2048}, 7 diagonals, m = 50, every system to beta <= 1e-12) in solves/s,
+its FP64 roofline, and the same systems solved one at a time by igs_solve (a sample) for
+comparison.  `--workload batched` prints that measurement as the main line instead.
 """
 from __future__ import annotations
 
@@ -46,6 +52,40 @@ def workload_config(gs):
             "n": GRID_N * GRID_N, "nnz": 5 * GRID_N * GRID_N - 4 * GRID_N, "restart_m": M,
             "gs_iters": gs, "step": f"one restart cycle = {M} Arnoldi steps",
             "l2": "inputs larger than L2 (Krylov basis 212 MB > 126 MB L2)"}
+
+
+BATCH_COUNT, BATCH_M, BATCH_TOL, BATCH_MAX_RESTARTS = 4096, 50, 1e-12, 20
+BATCH_METRIC, BATCH_UNIT = "solves/s", "solves/s"
+FP64_PEAK_TFLOPS = 152 * FP64_FMA_PER_CLK_PER_SM * 2 * 2070.0e6 / 1e12
+
+
+def batch_config(gs, count=BATCH_COUNT):
+    return {"workload": f"batched: {count} independent banded systems, n ~ U{{64..2048}}, "
+                        "7 diagonals, N(0,1) off-diagonals, diagonal 1.1 x off-diagonal row sum",
+            "count": count, "restart_m": BATCH_M, "gs_iters": gs, "tol_beta": BATCH_TOL,
+            "step": "one batch solve: every system to beta <= 1e-12 (one persistent launch)",
+            "l2": "inputs larger than L2 (matrices 366 MB, bases 0.6 GB)"}
+
+
+def batch_fma(ns, nnzs, steps, cycles, m, gs):
+    """Algorithmic FP64 multiply-adds of a batch solve (model of Alg. 4.1 per system): per
+    cycle r = b - A x and two norms (nnz + 2n), the prime step (nnz + 2n), per loop column p
+    the SpMV and (2 + 2(gs-1) + 1) p n for the reductions and updates (5pn with two
+    iterations, 3pn with one), the flush norm (n), and x += V y (columns x n)."""
+    per_p = 5 if gs == 2 else 3
+    total = 0.0
+    for n, nnz, st, cy in zip(ns, nnzs, steps, cycles):
+        n, nnz, st, cy = float(n), float(nnz), int(st), int(cy)
+        cols = [m] * (cy - 1) + [st - m * (cy - 1)] if cy > 0 else []
+        for c in cols:
+            total += nnz + 2 * n + nnz + 2 * n + c * n
+            total += (c - 1) * nnz + per_p * n * (c * (c + 1) / 2 - 1)
+            if c == m:
+                total += n
+            else:  # an in-cycle stop after the SpMV and first reduction of column c + 1
+                total += nnz + 2 * (c + 1) * n
+        total += nnz + 2 * n  # the final residual check
+    return total
 
 
 def dist_env():
@@ -130,6 +170,36 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    if args.workload == "batched":
+        import oracle
+        oracle.build()
+        out = gen.banded_batch(count=args.batch_count, seed=SEED)
+        stride = max(1, args.batch_count // 16)
+        sample = [(out[i][0], out[i][1], gen.norm2_power(out[i][0], iters=100))
+                  for i in range(0, args.batch_count, stride)]
+
+        def ostep():
+            for A, b, nA in sample:
+                oracle.gmres(A, b, m=BATCH_M, gs=args.gs, tol=BATCH_TOL, max_cycles=BATCH_MAX_RESTARTS,
+                             normA=nA)
+
+        for _ in range(args.warmup):
+            ostep()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ostep()
+        dt = time.perf_counter() - t0
+        value = args.steps * len(sample) / dt
+        line = {"impl": "reference", "metric": BATCH_METRIC, "value": value, "unit": BATCH_UNIT,
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": batch_config(args.gs, args.batch_count),
+                "cpu_baseline": {"value": value, "unit": BATCH_UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{len(sample)} of the {args.batch_count} systems per step"},
+                "e2e": {"value": value, "unit": BATCH_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     A, b, _, _ = gen.cd2d(GRID_N, PECLET, SEED)
     import oracle
     oracle.build()
@@ -160,6 +230,128 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, pkg, torch, local, dist, with_one_at_a_time=True):
+    """The batched form: `steps` timed batch solves (CUDA events on the launch stream), the
+    FP64 roofline of the persistent kernel, an end-to-end figure with host buffers, and a
+    sample of the same systems solved one at a time by igs_solve."""
+    ws, rank, _ = dist_env()
+    count = args.batch_count
+    out = gen.banded_batch(count=count, seed=SEED + rank)
+    As = [o[0] for o in out]
+    b = np.concatenate([o[1] for o in out])
+    stream = torch.cuda.current_stream()
+    t_create = time.perf_counter()
+    tb = [int(v) for v in args.batch_launch.split(":")] if args.batch_launch else [0, 0]
+    bs = pkg.BatchSolver(As, m=BATCH_M, device=local, stream=stream.cuda_stream, block_threads=tb[0],
+                         blocks_per_sm=tb[1])
+    t_create = time.perf_counter() - t_create
+    info = bs.info
+    b_dev = torch.from_numpy(b).cuda()
+    res = {"x": torch.empty_like(b_dev),
+           "beta": torch.empty(count, dtype=torch.float64, device=b_dev.device),
+           "status": torch.empty(count, dtype=torch.int32, device=b_dev.device),
+           "steps": torch.empty(count, dtype=torch.int64, device=b_dev.device),
+           "cycles": torch.empty(count, dtype=torch.int32, device=b_dev.device)}
+
+    def step():
+        return bs.solve(b_dev, gs=args.gs, tol=BATCH_TOL, max_restarts=BATCH_MAX_RESTARTS, out=res)
+
+    for _ in range(args.warmup):
+        r = step()
+    assert r["n_ok"] == count, r
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        r = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    dev_ms = [r["device_ms"]]  # kernel-only time of the last solve (graph launch events)
+    steps_b = res["steps"].cpu().numpy()
+    cycles_b = res["cycles"].cpu().numpy()
+    total_steps = int(steps_b.sum())
+
+    # end to end: host b in, host x / beta / status / steps / cycles out
+    b_host = np.ascontiguousarray(b)
+    bs.solve(b_host, gs=args.gs, tol=BATCH_TOL, max_restarts=BATCH_MAX_RESTARTS)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        bs.solve(b_host, gs=args.gs, tol=BATCH_TOL, max_restarts=BATCH_MAX_RESTARTS)
+    e2e_s = time.perf_counter() - t0
+    ms, e2e_s, solves_total = reduce_replicas(ms, e2e_s, args.steps * count, dist, "cuda")
+
+    ns = [A.n for A in As]
+    nnzs = [A.nnz for A in As]
+    fma = batch_fma(ns, nnzs, steps_b, cycles_b, BATCH_M, args.gs)
+    avg_s = ms / 1e3 / args.steps
+    achieved = 2 * fma / avg_s / 1e12
+    line = {"metric": BATCH_METRIC, "value": solves_total / (ms / 1e3), "unit": BATCH_UNIT,
+            "ms_per_step": ms / args.steps, "arnoldi_steps_per_s": total_steps * ws / avg_s,
+            "arnoldi_steps_per_batch": total_steps, "kernel_ms_last": dev_ms[0],
+            "config": {**batch_config(args.gs, count), "parallelism": f"replicas x{ws}"},
+            "launch": {"block_threads": info["block_threads"], "blocks_per_sm": info["blocks_per_sm"],
+                       "tuned": not args.batch_launch, "tune_table_ms": info["tune"], "create_s": t_create},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "k_batch_solve (persistent; all steps of Alg. 4.1 per system)",
+                         "flops_per_launch": 2 * fma,
+                         "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2070 MHz"},
+            "e2e": {"value": solves_total / e2e_s, "unit": BATCH_UNIT, "h2d_bytes_per_step": 8 * len(b),
+                    "d2h_bytes_per_step": 8 * len(b) + count * (8 + 4 + 8 + 4)},
+            "gpu_launches": args.steps}
+    if with_one_at_a_time and not args.no_one_at_a_time:
+        # the same systems, one igs_solve each (sample of 32 spread over the batch); solve
+        # time only (contexts created and their graphs captured beforehand)
+        norms = bs.norms()
+        idx = list(range(0, count, max(1, count // 32)))
+        t_solve = 0.0
+        steps_one = 0
+        for i in idx:
+            with pkg.Solver(As[i], max_restart_m=BATCH_M, A_norm2=float(norms[i]), device=local,
+                            stream=stream.cuda_stream) as sv:
+                bi = torch.from_numpy(out[i][1]).cuda()
+                xi = torch.empty_like(bi)
+                sv.solve(bi, m=BATCH_M, gs=args.gs, tol=BATCH_TOL, max_restarts=BATCH_MAX_RESTARTS,
+                         x_out=xi, hist_cap=0)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                o = sv.solve(bi, m=BATCH_M, gs=args.gs, tol=BATCH_TOL, max_restarts=BATCH_MAX_RESTARTS,
+                             x_out=xi, hist_cap=0)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t_solve += e0.elapsed_time(e1) / 1e3
+                steps_one += o["steps"]
+        one = len(idx) / t_solve
+        line["one_at_a_time"] = {"value": one, "unit": BATCH_UNIT, "path": "igs_solve per system (FP64)",
+                                 "sample": f"{len(idx)} systems spread over the batch ({steps_one} Arnoldi steps)"}
+        line["speedup_vs_one_at_a_time"] = line["value"] / (one * ws)
+    bs.close()
+    return line
+
+
+def oracle_batch_rate(stride=128):
+    """Solves/s of the CPU oracle (one thread) on every stride-th system of the batch."""
+    import oracle
+    out = gen.banded_batch(count=BATCH_COUNT, seed=SEED)
+    t = 0.0
+    k = 0
+    for i in range(0, BATCH_COUNT, stride):
+        A, b, _, _ = out[i]
+        nA = gen.norm2_power(A, iters=100)
+        t0 = time.perf_counter()
+        oracle.gmres(A, b, m=BATCH_M, gs=2, tol=BATCH_TOL, max_cycles=BATCH_MAX_RESTARTS, normA=nA)
+        t += time.perf_counter() - t0
+        k += 1
+    return k / t, k, t
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -168,6 +360,13 @@ def main():
     ap.add_argument("--gs", type=int, default=2)
     ap.add_argument("--impl", default="igs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cd2d", choices=["cd2d", "batched"])
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched sub-measurement")
+    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
+                    help="systems in the batched workload (smaller counts: profiling cases)")
+    ap.add_argument("--batch-launch", default="",
+                    help="T:B = block threads and CTAs per SM for the batched kernel (default: tuned)")
+    ap.add_argument("--no-one-at-a-time", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -188,6 +387,30 @@ def main():
     if dist:
         dist.barrier()
     import paper_2205_07805_gb300 as pkg
+
+    if args.workload == "batched":
+        clocks = Clocks(local)
+        clocks.start()
+        bl = run_batched(args, pkg, torch, local, dist)
+        clk = clocks.stop()
+        line = {"metric": BATCH_METRIC, "value": bl["value"], "unit": BATCH_UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": bl["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": bl["config"], "roofline": bl["roofline"], "e2e": bl["e2e"],
+                "gpu_launches": bl["gpu_launches"], "clocks": clk,
+                **{k: bl[k] for k in ("arnoldi_steps_per_s", "launch", "one_at_a_time",
+                                      "speedup_vs_one_at_a_time") if k in bl}}
+        if rank == 0 and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            rate, k, dt = oracle_batch_rate()
+            line["cpu_baseline"] = {"value": rate, "unit": BATCH_UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"{k} of the {BATCH_COUNT} systems (every 128th), {dt:.1f} s"}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
 
     A, b, x0, _ = gen.cd2d(GRID_N, PECLET, SEED + rank)
     normA = gen.norm2_power(A, iters=50)
@@ -250,7 +473,7 @@ def main():
     bytes_per_launch = d["bytes"] / max(1, d["launches"])
     achieved_tflops = flops_per_launch / avg_s / 1e12
     sm_clock = (clk or {}).get("sm_max_mhz") or 2070.0
-    peak_tflops = 152 * FP64_FMA_PER_CLK_PER_SM * 2 * 2070.0e6 / 1e12
+    peak_tflops = FP64_PEAK_TFLOPS
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -281,6 +504,11 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"one full cycle ({M} Arnoldi columns) of the same workload, {dt:.1f} s"}
     solver.close()
+    if not args.no_batched:
+        bl = run_batched(args, pkg, torch, local, dist)
+        line["batched"] = {k: bl[k] for k in ("metric", "value", "unit", "ms_per_step", "arnoldi_steps_per_s",
+                                              "config", "launch", "roofline", "e2e", "one_at_a_time",
+                                              "speedup_vs_one_at_a_time") if k in bl}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

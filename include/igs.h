@@ -59,7 +59,22 @@ typedef struct {
     double A_norm2;     /* ||A||_2 used by the backward error beta (eq. "nrbe", Sec. 1); <= 0:
                            estimated on the GPU by power iteration on A^T A                 */
     int norm2_iters;    /* power iterations for that estimate; <= 0: 100                     */
+    int fp32_basis;     /* nonzero: also allocate an FP32 Krylov basis and FP32 copy of A's
+                           values (4 (n+32)(m+2) + 4 nnz bytes more), which solves with
+                           precision = IGS_PREC_FP32_IR require                             */
 } igs_create_opts;
+
+/* Arithmetic of igs_solve's Arnoldi cycles. */
+enum {
+    IGS_PREC_FP64 = 0,     /* everything in FP64 (Alg. 4.1 as stated)                          */
+    IGS_PREC_FP32_IR = 1   /* FP32 SpMV, basis and basis updates; FP64 Gram accumulation (FP32
+                              sums over 32 rows promoted to FP64), (I+L) solves, Givens least
+                              squares, x and r = b - A x.  Each restart is one step of FP64
+                              iterative refinement: r = b - A x, an FP32 cycle on A d = r
+                              stopped when its residual estimate falls by inner_tol (or meets
+                              tol_beta), x = x + d.  The paper names mixed precision only as
+                              future work (Sec. 6); this form is this library's extension.   */
+};
 
 /* Options of igs_solve. */
 typedef struct {
@@ -69,6 +84,10 @@ typedef struct {
     double tol_beta;      /* stop when beta(x) <= tol_beta; 0 runs max_restarts full cycles  */
     int max_restarts;     /* at most this many cycles (>= 1)                                 */
     int inputs_on_device; /* 1: b, x0 and res->x are device pointers; 0: host pointers        */
+    int precision;        /* IGS_PREC_FP64 (0, default) or IGS_PREC_FP32_IR (needs a context
+                             created with fp32_basis); anything else: IGS_EINVAL            */
+    double inner_tol;     /* IGS_PREC_FP32_IR: relative residual reduction per FP32 cycle;
+                             <= 0: 1e-6.  Ignored for FP64                                   */
 } igs_solve_opts;
 
 /* Results of igs_solve.  Input fields are marked "in". */

@@ -46,12 +46,16 @@ class IGSError(RuntimeError):
 
 class _CreateOpts(C.Structure):
     _fields_ = [("stream", C.c_void_p), ("device", C.c_int), ("max_restart_m", C.c_int),
-                ("A_norm2", C.c_double), ("norm2_iters", C.c_int)]
+                ("A_norm2", C.c_double), ("norm2_iters", C.c_int), ("fp32_basis", C.c_int)]
 
 
 class _SolveOpts(C.Structure):
     _fields_ = [("restart_m", C.c_int), ("gs_iters", C.c_int), ("tol_beta", C.c_double),
-                ("max_restarts", C.c_int), ("inputs_on_device", C.c_int)]
+                ("max_restarts", C.c_int), ("inputs_on_device", C.c_int), ("precision", C.c_int),
+                ("inner_tol", C.c_double)]
+
+
+PRECISIONS = {"fp64": 0, "fp32_ir": 1}
 
 
 class _Result(C.Structure):
@@ -187,7 +191,8 @@ class Solver:
     (float64) attributes, or a tuple ``(n, rowptr, colind, val)``."""
 
     def __init__(self, A, max_restart_m: int = 100, A_norm2: float | None = None,
-                 device: int = 0, stream: int | None = None, norm2_iters: int = 100):
+                 device: int = 0, stream: int | None = None, norm2_iters: int = 100,
+                 fp32_basis: bool = False):
         self._lib = load_library()
         if isinstance(A, tuple):
             n, rowptr, colind, val = A
@@ -198,7 +203,7 @@ class Solver:
         ci = np.ascontiguousarray(colind, dtype=np.int32)
         va = np.ascontiguousarray(val, dtype=np.float64)
         opts = _CreateOpts(C.c_void_p(stream) if stream else None, int(device), int(max_restart_m),
-                           float(A_norm2) if A_norm2 else 0.0, int(norm2_iters))
+                           float(A_norm2) if A_norm2 else 0.0, int(norm2_iters), 1 if fp32_basis else 0)
         h = C.c_void_p()
         rc = self._lib.igs_create(C.byref(h), self.n, int(rp[-1]), C.c_void_p(rp.ctypes.data),
                                   C.c_void_p(ci.ctypes.data), C.c_void_p(va.ctypes.data), C.byref(opts))
@@ -242,10 +247,11 @@ class Solver:
     # ------------------------------------------------------------------------------
     def solve(self, b, x0=None, m: int = 30, gs: int = 2, tol: float = 1e-13,
               max_restarts: int = 10, x_out=None, hist_cap: int | None = None,
-              want_H: bool = False) -> dict:
+              want_H: bool = False, precision: str = "fp64", inner_tol: float = 0.0) -> dict:
         """Restarted IGS-GMRES(m) (``igs_solve``).  Returns ``dict(x, status, beta, rho0,
         steps, cycles, hist_res, hist_lfro[, H])``.  With a CUDA tensor ``b`` the inputs and
-        ``x`` stay on the device."""
+        ``x`` stay on the device.  ``precision="fp32_ir"`` runs the cycles on the FP32 basis
+        inside FP64 iterative refinement (context created with ``fp32_basis=True``)."""
         bp, dev, kb = _vec_arg(b, self.n, "b")
         if x0 is not None:
             xp, dev0, kx = _vec_arg(x0, self.n, "x0")
@@ -268,7 +274,10 @@ class Solver:
         H = np.zeros((m + 1, m), order="F") if want_H else None
         res = _Result(op, C.c_void_p(hres.ctypes.data), C.c_void_p(hlf.ctypes.data), cap, 0,
                       C.c_void_p(H.ctypes.data) if want_H else None, m + 1, 0.0, 0.0, 0, 0)
-        opts = _SolveOpts(int(m), int(gs), float(tol), int(max_restarts), 1 if dev else 0)
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+        opts = _SolveOpts(int(m), int(gs), float(tol), int(max_restarts), 1 if dev else 0,
+                          PRECISIONS[precision], float(inner_tol))
         rc = self._lib.igs_solve(self._h, bp, xp, C.byref(opts), C.byref(res))
         if rc < 0:
             self._err(rc, "igs_solve")

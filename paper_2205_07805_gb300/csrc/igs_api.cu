@@ -148,8 +148,11 @@ double upd_bytes(const igs::Workspace &w, int p) { return 8.0 * w.n * (p + 2); }
 
 // Enqueue one restart cycle (see the file comment).  Precondition: ctx->w.r = b - A x,
 // st->rnorm/xnorm/bnorm set (by the solve set-up or the previous cycle's end).
-cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs)
+cudaError_t enqueue_cycle32(igs_ctx *ctx, Issuer &is, int m, int gs);
+
+cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
 {
+    if (prec == IGS_PREC_FP32_IR) return enqueue_cycle32(ctx, is, m, gs);
     const igs::Workspace &w = ctx->w;
     cudaStream_t s = is.s;
     const int64_t ld = w.ld;
@@ -278,13 +281,115 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs)
     return cudaSuccess;
 }
 
+// One cycle of the precision form (IGS_PREC_FP32_IR): the same steps and single-block
+// kernels as the FP64 cycle, with the SpMV, the basis, z and u in FP32 (igs_fp32.cu); the
+// cycle's residual r = b - A x (FP64, from the previous cycle) enters as v_1 = r / rho and the
+// cycle ends with x = x + V y and r = b - A x in FP64: one step of iterative refinement.
+cudaError_t enqueue_cycle32(igs_ctx *ctx, Issuer &is, int m, int gs)
+{
+    const igs::Workspace &w = ctx->w;
+    cudaStream_t s = is.s;
+    const int64_t ld = w.ld;
+    float *V = w.V32;
+    auto col = [&](int c) { return V + (int64_t)c * ld; };
+    cudaError_t e;
+    const double spmv32b = 8.0 * w.nnz + 4.0 * (w.n + 1) + 8.0 * w.n;
+    auto dots32b = [&](int p, int nq) { return 4.0 * w.n * (p + nq); };
+    auto upd32b = [&](int p) { return 4.0 * w.n * (p + 2); };
+#define RUN(cls, bytes, flops, on, expr)                                          \
+    do {                                                                          \
+        e = is.run((cls), (bytes), (flops), [&](cudaStream_t st_) { (void)st_; return (expr); }, (on)); \
+        if (e != cudaSuccess) return e;                                           \
+    } while (0)
+
+    // Step 1: rho = ||r0|| (FP64), v1 = r0 / rho (to FP32).
+    RUN(igs::KC_CYCLE, 0, 0, s, igs::launch_cycle_start(w, 0, st_));
+    RUN(igs::KC_CYCLE, 12.0 * w.n, w.n, s, igs::launch_scale_to32(w, w.r, col(0), st_));
+    // Step 2: w2 = A v1, H11 = v1^T w2, w2 -= H11 v1.
+    igs::DotsPlan pl{};
+    RUN(igs::KC_SPMV, spmv32b, 2.0 * w.nnz, s, igs::launch_spmv32(w, col(0), col(1), st_));
+    RUN(igs::KC_DOTS, dots32b(1, 1), 2.0 * w.n, s, igs::launch_dots32(w, 1, col(1), nullptr, st_, &pl));
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_prime(w, pl, st_));
+    RUN(igs::KC_UPDATE, upd32b(1), 2.0 * w.n, s, igs::launch_update32(w, 1, w.r1v, 1.0, col(1), col(1), false, st_));
+
+    bool pending_join = false;
+    auto join_side = [&]() -> cudaError_t {
+        if (pending_join && is.capture) {
+            cudaError_t ee = cudaStreamWaitEvent(s, ctx->ev_join, 0);
+            if (ee != cudaSuccess) return ee;
+        }
+        pending_join = false;
+        return cudaSuccess;
+    };
+    auto fork_givens = [&](int j) -> cudaError_t {
+        cudaStream_t on = s;
+        if (is.capture) {
+            cudaError_t ee = cudaEventRecord(ctx->ev_fork, s);
+            if (ee == cudaSuccess) ee = cudaStreamWaitEvent(is.side, ctx->ev_fork, 0);
+            if (ee != cudaSuccess) return ee;
+            on = is.side;
+        }
+        cudaError_t ee = is.run(igs::KC_SMALL, 0, 0, [&](cudaStream_t st_) { return igs::launch_givens(w, j, st_); }, on);
+        if (ee != cudaSuccess) return ee;
+        if (is.capture) {
+            ee = cudaEventRecord(ctx->ev_join, is.side);
+            if (ee != cudaSuccess) return ee;
+            pending_join = true;
+        }
+        return cudaSuccess;
+    };
+
+    for (int k = 3; k <= m + 1; ++k) {
+        const int p = k - 1;
+        float *wv = col(p - 1);
+        // Step 4: z = A w_{k-1} (FP32).
+        RUN(igs::KC_SPMV, spmv32b, 2.0 * w.nnz, s, igs::launch_spmv32(w, wv, w.z32, st_));
+        // Step 5: [V_{k-2}, w_{k-1}]^T [w_{k-1}, z] (FP32 chunks, FP64 partial sums).
+        RUN(igs::KC_DOTS, dots32b(p, 2), 4.0 * w.n * p, s, igs::launch_dots32(w, p, wv, w.z32, st_, &pl));
+        if ((e = join_side()) != cudaSuccess) return e;
+        // Steps 6-12 (+ step 17 for one iteration), FP64.
+        RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_a(w, k, gs, pl, st_));
+        if ((e = fork_givens(k - 3)) != cudaSuccess) return e;
+        // Steps 7, 11, 13: v_{k-1} = w/gamma in place, u = z/gamma - V_{k-1} r^(1) (FP32).
+        float *uout = gs == 1 ? col(p) : w.u32;
+        RUN(igs::KC_UPDATE, upd32b(p) + 4.0 * w.n, 2.0 * w.n * p, s,
+            igs::launch_update32(w, p, w.r1v, 0.0, w.z32, uout, true, st_));
+        if (gs == 2) {
+            // Step 14: r^(2) = V_{k-1}^T u.
+            RUN(igs::KC_DOTS, dots32b(p, 1), 2.0 * w.n * p, s, igs::launch_dots32(w, p, w.u32, nullptr, st_, &pl));
+            // Steps 15, 17.
+            RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_b(w, k, pl, st_));
+            // Step 16: w_k = u - V_{k-1} r^(3).
+            RUN(igs::KC_UPDATE, upd32b(p), 2.0 * w.n * p, s,
+                igs::launch_update32(w, p, w.r3v, 1.0, w.u32, col(p), false, st_));
+        }
+    }
+    // Flush: gamma_{m+1} = ||w_{m+1}||, H_{m+1,m}, last L row, v_{m+1} = w_{m+1}/gamma.
+    RUN(igs::KC_DOTS, dots32b(m + 1, 1), 2.0 * w.n * (m + 1), s,
+        igs::launch_dots32(w, m + 1, col(m), nullptr, st_, &pl));
+    if ((e = join_side()) != cudaSuccess) return e;
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_flush(w, m, pl, st_));
+    RUN(igs::KC_CYCLE, 8.0 * w.n, w.n, s, igs::launch_scale32(w, col(m), st_));
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));
+    // y = argmin ||rho e1 - H y||; x = x + V y in FP64 (the refinement step).
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_lsq(w, m, st_));
+    RUN(igs::KC_CYCLE, 4.0 * w.n * m + 16.0 * w.n, 2.0 * w.n * m, s, igs::launch_xupdate32(w, st_));
+    // r = b - A x, ||r||, ||x||, beta(x) in FP64.
+    RUN(igs::KC_CYCLE, spmv_bytes(w) + 8.0 * w.n, 2.0 * w.nnz, s, igs::launch_spmv(w, w.x, w.r, w.b, false, st_));
+    int nblk = 0;
+    RUN(igs::KC_CYCLE, 16.0 * w.n, 4.0 * w.n, s, igs::launch_norms(w, w.r, w.x, nullptr, &nblk, st_));
+    RUN(igs::KC_CYCLE, 0, 0, s, igs::launch_beta(w, nblk, st_));
+#undef RUN
+    return cudaSuccess;
+}
+
 // Solve-level set-up: state, ||b||, r = b - A x, beta(x).  b and x are already in w.b, w.x.
-cudaError_t enqueue_setup(igs_ctx *ctx, Issuer &is, double tol)
+cudaError_t enqueue_setup(igs_ctx *ctx, Issuer &is, double tol, double inner_tol)
 {
     const igs::Workspace &w = ctx->w;
     cudaError_t e;
     int nblk = 0;
-    e = is.run(igs::KC_CYCLE, 0, 0, [&](cudaStream_t s) { return igs::launch_init_state(w, tol, ctx->normA, s); }, is.s);
+    e = is.run(igs::KC_CYCLE, 0, 0, [&](cudaStream_t s) { return igs::launch_init_state(w, tol, ctx->normA, inner_tol, s); }, is.s);
     if (e != cudaSuccess) return e;
     e = is.run(igs::KC_CYCLE, 8.0 * w.n, 2.0 * w.n, [&](cudaStream_t s) { return igs::launch_norms(w, w.b, nullptr, nullptr, &nblk, s); }, is.s);
     if (e != cudaSuccess) return e;
@@ -297,9 +402,9 @@ cudaError_t enqueue_setup(igs_ctx *ctx, Issuer &is, double tol)
     return is.run(igs::KC_CYCLE, 0, 0, [&](cudaStream_t s) { return igs::launch_beta(w, nblk, s); }, is.s);
 }
 
-int get_graph(igs_ctx *ctx, int m, int gs, igs_ctx::Graph **out)
+int get_graph(igs_ctx *ctx, int m, int gs, int prec, igs_ctx::Graph **out)
 {
-    auto key = std::make_pair(m, gs);
+    auto key = std::make_pair(m, gs + 4 * prec);
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
         *out = &it->second;
@@ -307,7 +412,7 @@ int get_graph(igs_ctx *ctx, int m, int gs, igs_ctx::Graph **out)
     }
     Issuer is{ctx, ctx->cap, ctx->side, true};
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_cycle(ctx, is, m, gs);
+    cudaError_t e = enqueue_cycle(ctx, is, m, gs, prec);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &g);
     if (e != cudaSuccess) {
@@ -326,11 +431,11 @@ int get_graph(igs_ctx *ctx, int m, int gs, igs_ctx::Graph **out)
 }
 
 // Run one cycle: replay the graph, or issue eagerly with events when profiling.
-int run_cycle(igs_ctx *ctx, int m, int gs)
+int run_cycle(igs_ctx *ctx, int m, int gs, int prec)
 {
     if (ctx->profiling) {
         Issuer is{ctx, ctx->stream, ctx->stream, false};
-        cudaError_t e = enqueue_cycle(ctx, is, m, gs);
+        cudaError_t e = enqueue_cycle(ctx, is, m, gs, prec);
         ctx->launches += is.kernels;
         CK(e);
         CK(cudaStreamSynchronize(ctx->stream));
@@ -338,17 +443,17 @@ int run_cycle(igs_ctx *ctx, int m, int gs)
         return IGS_OK;
     }
     igs_ctx::Graph *g = nullptr;
-    int rc = get_graph(ctx, m, gs, &g);
+    int rc = get_graph(ctx, m, gs, prec, &g);
     if (rc != IGS_OK) return rc;
     CK(cudaGraphLaunch(g->exec, ctx->stream));
     ctx->launches += g->kernels;
     return IGS_OK;
 }
 
-int run_setup(igs_ctx *ctx, double tol)
+int run_setup(igs_ctx *ctx, double tol, double inner_tol)
 {
     Issuer is{ctx, ctx->stream, ctx->stream, false};
-    cudaError_t e = enqueue_setup(ctx, is, tol);
+    cudaError_t e = enqueue_setup(ctx, is, tol, inner_tol);
     ctx->launches += is.kernels;
     CK(e);
     if (ctx->profiling) {
@@ -560,6 +665,20 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
     w.rowptr = rp;
     w.colind = ci;
     w.val = va;
+    if (o.fp32_basis) {
+        // precision form: FP32 basis, Krylov vectors and A's values (rounded to nearest)
+        if ((rc = dalloc(ctx, &w.V32, (size_t)w.ld * (M + 1))) || (rc = dalloc(ctx, &w.z32, (size_t)w.ld)) ||
+            (rc = dalloc(ctx, &w.u32, (size_t)w.ld)) || (rc = dalloc(ctx, &w.val32, (size_t)nnz)))
+            return bail(rc);
+        std::vector<float> v32((size_t)(nnz > 0 ? nnz : 1));
+        for (int64_t q = 0; q < nnz; ++q) v32[(size_t)q] = (float)vals[q];
+        cudaError_t e = nnz > 0 ? cudaMemcpy(w.val32, v32.data(), sizeof(float) * (size_t)nnz, cudaMemcpyHostToDevice)
+                                : cudaSuccess;
+        if (e != cudaSuccess) {
+            fail(ctx, IGS_ECUDA, "copying A (FP32): %s", cudaGetErrorString(e));
+            return bail(IGS_ECUDA);
+        }
+    }
     {
         cudaError_t e = igs::configure_kernels(w);
         if (e == cudaSuccess) e = igs::configure_tma_kernels();
@@ -670,13 +789,18 @@ int igs_solve(igs_ctx *ctx, const double *b, const double *x0, const igs_solve_o
     if (opts->max_restarts < 1) return fail(ctx, IGS_EINVAL, "max_restarts must be >= 1");
     if (!(opts->tol_beta >= 0.0)) return fail(ctx, IGS_EINVAL, "tol_beta must be >= 0");
     if (res->H && res->H_ld < m + 1) return fail(ctx, IGS_EINVAL, "H_ld < m+1");
+    const int prec = opts->precision;
+    if (prec != IGS_PREC_FP64 && prec != IGS_PREC_FP32_IR) return fail(ctx, IGS_EINVAL, "unknown precision %d", prec);
+    if (prec == IGS_PREC_FP32_IR && !ctx->w.V32)
+        return fail(ctx, IGS_EINVAL, "precision FP32_IR needs a context created with fp32_basis");
+    const double inner_tol = prec == IGS_PREC_FP32_IR ? (opts->inner_tol > 0.0 ? opts->inner_tol : 1e-6) : 0.0;
     CK(cudaSetDevice(ctx->device));
     igs::Workspace &w = ctx->w;
     const bool dev = opts->inputs_on_device != 0;
     int rc;
     if ((rc = copy_vec_in(ctx, w.b, b, dev)) != IGS_OK) return rc;
     if ((rc = copy_vec_in(ctx, w.x, x0, dev)) != IGS_OK) return rc;
-    if ((rc = run_setup(ctx, opts->tol_beta)) != IGS_OK) return rc;
+    if ((rc = run_setup(ctx, opts->tol_beta, inner_tol)) != IGS_OK) return rc;
     igs::DevState hs{};
     if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
     res->hist_len = 0;
@@ -691,7 +815,7 @@ int igs_solve(igs_ctx *ctx, const double *b, const double *x0, const igs_solve_o
         status = IGS_OK;
     } else {
         for (int cyc = 0; cyc < opts->max_restarts; ++cyc) {
-            if ((rc = run_cycle(ctx, m, gs)) != IGS_OK) return rc;
+            if ((rc = run_cycle(ctx, m, gs, prec)) != IGS_OK) return rc;
             if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
             res->cycles += 1;
             const int nc = hs.ncols;
@@ -746,8 +870,8 @@ int igs_arnoldi(igs_ctx *ctx, const double *r0, int m, int gs, int on_device, do
     int rc;
     if ((rc = copy_vec_in(ctx, w.b, r0, on_device != 0)) != IGS_OK) return rc;
     if ((rc = copy_vec_in(ctx, w.x, nullptr, false)) != IGS_OK) return rc;
-    if ((rc = run_setup(ctx, 0.0)) != IGS_OK) return rc;
-    if ((rc = run_cycle(ctx, m, gs)) != IGS_OK) return rc;
+    if ((rc = run_setup(ctx, 0.0, 0.0)) != IGS_OK) return rc;
+    if ((rc = run_cycle(ctx, m, gs, IGS_PREC_FP64)) != IGS_OK) return rc;
     igs::DevState hs{};
     if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

@@ -69,6 +69,8 @@ struct DevState {
     double normA;      // ||A||_2
     double bnorm;      // ||b||
     double rnorm, xnorm, beta;  // end-of-cycle residual norm, ||x||, backward error
+    double inner_tol;  // FP32 cycles of the precision form: stop when |g| <= inner_tol * rho
+    double stop_floor; // inner_tol * rho of the current cycle (0 for FP64 solves)
     int halt;          // nonzero: the remaining step kernels of this cycle do nothing
     int stop_cols;     // > 0: columns the cycle ends with (early stop or breakdown)
     int stop_reason;   // 0 running, 1 converged, 2 breakdown, -4 numeric error
@@ -101,6 +103,10 @@ struct Workspace {
     int *counters = nullptr;       // group arrival counters of the fused update
     double *hist_res = nullptr, *hist_lfro = nullptr;  // per-cycle history (mmax entries)
     DevState *st = nullptr;
+    // precision form (allocated when the context is created with an FP32 basis)
+    float *V32 = nullptr;          // ld x (mmax+1), column-major, zero padding rows
+    float *z32 = nullptr, *u32 = nullptr;
+    float *val32 = nullptr;        // A's values rounded to FP32 (same rowptr / colind)
     int ldh() const { return mmax + 1; }
     int ldl() const { return mmax + 1; }
 };
@@ -161,13 +167,25 @@ cudaError_t launch_flush(const Workspace &w, int m, const DotsPlan &pl, cudaStre
 cudaError_t launch_givens(const Workspace &w, int j, cudaStream_t s);
 cudaError_t launch_lsq(const Workspace &w, int m, cudaStream_t s);
 cudaError_t launch_beta(const Workspace &w, int nblk, cudaStream_t s);
-cudaError_t launch_init_state(const Workspace &w, double tol, double normA, cudaStream_t s);
+cudaError_t launch_init_state(const Workspace &w, double tol, double normA, double inner_tol,
+                              cudaStream_t s);
 cudaError_t launch_bnorm(const Workspace &w, int nblk, cudaStream_t s);
 
 // dst(i, c) = src(i, c) for i < rows, c < cols: src column-major (ld_src), dst row-major
 // (ld_dst).
 cudaError_t launch_transpose(const double *src, int ld_src, int rows, int cols, double *dst,
                              int ld_dst, cudaStream_t s);
+
+// FP32-basis kernels of the precision form (igs_fp32.cu).  Same grids and FP64 partial-sum
+// layout as the FP64 kernels; all return cudaGetLastError().
+cudaError_t launch_spmv32(const Workspace &w, const float *x, float *y, cudaStream_t s);
+cudaError_t launch_dots32(const Workspace &w, int p, const float *x0, const float *x1, cudaStream_t s,
+                          DotsPlan *plan_out);
+cudaError_t launch_update32(const Workspace &w, int p, const double *coef, double alpha, const float *src,
+                            float *out, bool norm_last, cudaStream_t s);
+cudaError_t launch_scale_to32(const Workspace &w, const double *src, float *dst, cudaStream_t s);
+cudaError_t launch_scale32(const Workspace &w, float *v, cudaStream_t s);
+cudaError_t launch_xupdate32(const Workspace &w, cudaStream_t s);
 
 // Per-context kernel configuration (dynamic shared-memory limits); call before any capture.
 cudaError_t configure_kernels(const Workspace &w);

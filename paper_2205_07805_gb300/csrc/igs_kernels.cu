@@ -600,13 +600,14 @@ static SmallArgs small_args(const Workspace &w)
 }
 
 // Solve-level initialisation of the device state.
-__global__ void k_init_state(DevState *st, double tol, double normA)
+__global__ void k_init_state(DevState *st, double tol, double normA, double inner_tol)
 {
     IGS_PDL_ENTER();
     if (threadIdx.x == 0) {
         DevState s = {};
         s.tol = tol;
         s.normA = normA;
+        s.inner_tol = inner_tol;
         *st = s;
     }
 }
@@ -649,6 +650,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_cycle_start(SmallArgs a, int 
         a.g[0] = rho;
         a.lfro2[0] = 0.0;
         st->stop_den = st->bnorm + st->normA * st->xnorm;
+        st->stop_floor = st->inner_tol * rho;
         st->halt = 0;
         st->stop_cols = 0;
         st->stop_reason = 0;
@@ -929,7 +931,10 @@ __global__ void __launch_bounds__(kGivensThreads) k_givens(SmallArgs a, int j)
         const double res = fabs(s * gj);
         a.hist_res[j] = res;
         a.hist_lfro[j] = sqrt(a.lfro2[j]);
-        if (st->stop_reason == 0 && st->stop_den > 0.0 && res <= st->tol * st->stop_den) {
+        // in-cycle stop: the estimated backward error meets tol, or (FP32 cycles of the
+        // precision form) the cycle reduced its residual by inner_tol
+        if (st->stop_reason == 0 &&
+            ((st->stop_den > 0.0 && res <= st->tol * st->stop_den) || res <= st->stop_floor)) {
             st->stop_reason = 1;
             st->stop_cols = j + 1;
         }
@@ -1146,9 +1151,10 @@ cudaError_t launch_scale(const Workspace &w, const double *src, double *dst, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_state(const Workspace &w, double tol, double normA, cudaStream_t s)
+cudaError_t launch_init_state(const Workspace &w, double tol, double normA, double inner_tol,
+                              cudaStream_t s)
 {
-    launch_k(w.pdl, k_init_state, dim3(1), dim3(32), 0, s, w.st, tol, normA);
+    launch_k(w.pdl, k_init_state, dim3(1), dim3(32), 0, s, w.st, tol, normA, inner_tol);
     return cudaGetLastError();
 }
 

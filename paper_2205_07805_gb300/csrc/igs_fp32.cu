@@ -63,79 +63,92 @@ k_spmv32_warp(int64_t n, const int *__restrict__ rowptr, const int *__restrict__
 
 // Block multi-dot of the FP32 basis (Alg. 4.1 steps 5 and 14), same grid and partial layout
 // as the FP64 k_dots: part[rb*(NQ*p) + q*p + c] = sum over row block rb of V[:,c] X_q.
-// Thread t owns column c_lo + t % cw and a contiguous slice of its rows; products are summed
-// in FP32 over chunks of 32 rows, each chunk sum is added to an FP64 accumulator, and the
-// slices are combined in FP64 by a fixed tree.
+// The block's cw columns are split over its warps: warp w takes column c_lo + w % cw and
+// the (w / cw)-th of S = warps / cw contiguous sub-ranges of the block's rows, and streams it
+// with coalesced 16-byte loads (a warp reads 512 contiguous bytes per load), so every column
+// is read in long runs.  Each lane sums its products in FP32 over chunks of 32 of its rows
+// and adds each chunk sum to an FP64 accumulator; the lanes are combined by a fixed FP64
+// shuffle tree and the sub-ranges in order.
 template <int NQ>
-__global__ void __launch_bounds__(kStreamThreads, kDotsBlocksPerSM)
+__global__ void __launch_bounds__(kStreamThreads, 2)
 k_dots32(const float *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t rows,
          const float *__restrict__ x0, const float *__restrict__ x1, double *__restrict__ part,
          const DevState *st, int check_halt)
 {
     IGS_PDL_ENTER();
     if (check_halt && halted32(st)) return;
-    __shared__ double red[NQ][kStreamThreads];
+    constexpr int W = kStreamThreads / 32;
+    __shared__ double red[NQ][W];
     const int rb = blockIdx.x, G = gridDim.y, cg = blockIdx.y;
     const int c_lo = (int)((int64_t)cg * p / G), c_hi = (int)((int64_t)(cg + 1) * p / G);
     const int cw = c_hi - c_lo;
-    const int S = blockDim.x / cw;
-    const int t = threadIdx.x, cl = t % cw, s = t / cw;
+    const int S = W / cw;  // sub-ranges per column (cw <= 4 <= W)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int cl = wid % cw, sr = wid / cw;
     const int64_t r_lo = (int64_t)rb * rows;
     const int64_t r_hi = r_lo + rows < n4 ? r_lo + rows : n4;
     double d0 = 0.0, d1 = 0.0;
-    if (s < S && r_lo < r_hi) {
+    if (sr < S && r_lo < r_hi) {
         const int64_t nquad = (r_hi - r_lo) >> 2;
-        const int64_t q0 = nquad * s / S, q1 = nquad * (s + 1) / S;
+        const int64_t q0 = nquad * sr / S, q1 = nquad * (sr + 1) / S;
         const float4 *vc = reinterpret_cast<const float4 *>(V + (int64_t)(c_lo + cl) * ld + r_lo);
         const float4 *xa = reinterpret_cast<const float4 *>(x0 + r_lo);
         const float4 *xb = reinterpret_cast<const float4 *>((NQ == 2 ? x1 : x0) + r_lo);
-        int64_t q = q0;
-        while (q < q1) {
-            const int64_t qe = q + kChunk4 < q1 ? q + kChunk4 : q1;
+        constexpr int U = NQ == 2 ? 4 : 8;  // loads per lane per batch; a chunk is 8 quads
+        for (int64_t base = q0; base < q1; base += 32 * kChunk4) {
             float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
-            for (; q < qe; ++q) {
-                const float4 v = vc[q];
-                const float4 x = xa[q];
-                a0 = fmaf(v.x, x.x, a0);
-                a1 = fmaf(v.y, x.y, a1);
-                a0 = fmaf(v.z, x.z, a0);
-                a1 = fmaf(v.w, x.w, a1);
-                if (NQ == 2) {
-                    const float4 y = xb[q];
-                    b0 = fmaf(v.x, y.x, b0);
-                    b1 = fmaf(v.y, y.y, b1);
-                    b0 = fmaf(v.z, y.z, b0);
-                    b1 = fmaf(v.w, y.w, b1);
+#pragma unroll
+            for (int h = 0; h < kChunk4; h += U) {
+                float4 v[U], x[U], y[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t q = base + (int64_t)(h + u) * 32 + lane;
+                    const bool in = q < q1;
+                    v[u] = in ? vc[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    x[u] = in ? xa[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (NQ == 2) y[u] = in ? xb[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    a0 = fmaf(v[u].x, x[u].x, a0);
+                    a1 = fmaf(v[u].y, x[u].y, a1);
+                    a0 = fmaf(v[u].z, x[u].z, a0);
+                    a1 = fmaf(v[u].w, x[u].w, a1);
+                    if (NQ == 2) {
+                        b0 = fmaf(v[u].x, y[u].x, b0);
+                        b1 = fmaf(v[u].y, y[u].y, b1);
+                        b0 = fmaf(v[u].z, y[u].z, b0);
+                        b1 = fmaf(v[u].w, y[u].w, b1);
+                    }
                 }
             }
             d0 += (double)(a0 + a1);
             if (NQ == 2) d1 += (double)(b0 + b1);
         }
     }
-    red[0][t] = d0;
-    if (NQ == 2) red[1][t] = d1;
-    int Sp = S;
-    while (Sp > 1) {
-        const int h = (Sp + 1) >> 1;
-        __syncthreads();
-        if (s < Sp - h) {
-#pragma unroll
-            for (int qq = 0; qq < NQ; ++qq) red[qq][t] += red[qq][t + h * cw];
-        }
-        Sp = h;
+    for (int o = 16; o > 0; o >>= 1) {
+        d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+        if (NQ == 2) d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+    }
+    if (lane == 0) {
+        red[0][wid] = d0;
+        if (NQ == 2) red[NQ - 1][wid] = d1;
     }
     __syncthreads();
-    if (s == 0) {
-#pragma unroll
-        for (int qq = 0; qq < NQ; ++qq) part[(int64_t)rb * NQ * p + (int64_t)qq * p + c_lo + cl] = red[qq][t];
+    if (threadIdx.x < cw * NQ) {
+        const int c = threadIdx.x % cw, qq = threadIdx.x / cw;
+        double acc = 0.0;
+        for (int j = 0; j < S; ++j) acc += red[qq][j * cw + c];
+        part[(int64_t)rb * NQ * p + (int64_t)qq * p + c_lo + c] = acc;
     }
 }
 
 // FP32 basis update (steps 7, 11, 13, 16): out[i] = a src[i] - sum_{c<p} V[i,c] coef[c],
 // coef (FP64, from the single-block steps) rounded to FP32.  With norm_last, column p-1 is
-// first scaled in place by 1/gamma and a = 1/gamma.
+// first scaled in place by 1/gamma and a = 1/gamma.  Four consecutive rows per thread
+// (16-byte loads; a block reads 4 KB of each column), padding rows included (they stay 0).
 __global__ void __launch_bounds__(kStreamThreads)
-k_update32(float *V, int64_t ld, int p, int64_t n, const double *__restrict__ coef, double alpha,
+k_update32(float *V, int64_t ld, int p, int64_t n4, const double *__restrict__ coef, double alpha,
            const float *src, float *out, int norm_last, const DevState *st)
 {
     IGS_PDL_ENTER();
@@ -145,34 +158,59 @@ k_update32(float *V, int64_t ld, int p, int64_t n, const double *__restrict__ co
     for (int c = threadIdx.x; c < p; c += blockDim.x) scf[c] = (float)coef[c];
     __syncthreads();
     const int pc = norm_last ? p - 1 : p;
+    const int64_t nq = n4 >> 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float *vi = V + i;
-        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
+        const float4 *vq = reinterpret_cast<const float4 *>(V) + q;
+        const int64_t ldq = ld >> 2;
+        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
         int c = 0;
         for (; c + 7 < pc; c += 8) {
-            float v[8];
+            float4 v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = vi[(int64_t)(c + q) * ld];
-            acc0 = fmaf(v[0], scf[c], acc0);
-            acc1 = fmaf(v[1], scf[c + 1], acc1);
-            acc2 = fmaf(v[2], scf[c + 2], acc2);
-            acc3 = fmaf(v[3], scf[c + 3], acc3);
-            acc0 = fmaf(v[4], scf[c + 4], acc0);
-            acc1 = fmaf(v[5], scf[c + 5], acc1);
-            acc2 = fmaf(v[6], scf[c + 6], acc2);
-            acc3 = fmaf(v[7], scf[c + 7], acc3);
+            for (int u = 0; u < 8; ++u) v[u] = vq[(int64_t)(c + u) * ldq];
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                const float c0 = scf[c + u], c1 = scf[c + u + 1];
+                acc0.x = fmaf(v[u].x, c0, acc0.x);
+                acc0.y = fmaf(v[u].y, c0, acc0.y);
+                acc0.z = fmaf(v[u].z, c0, acc0.z);
+                acc0.w = fmaf(v[u].w, c0, acc0.w);
+                acc1.x = fmaf(v[u + 1].x, c1, acc1.x);
+                acc1.y = fmaf(v[u + 1].y, c1, acc1.y);
+                acc1.z = fmaf(v[u + 1].z, c1, acc1.z);
+                acc1.w = fmaf(v[u + 1].w, c1, acc1.w);
+            }
         }
-        for (; c < pc; ++c) acc0 = fmaf(vi[(int64_t)c * ld], scf[c], acc0);
-        acc0 += acc2;
-        acc1 += acc3;
+        for (; c < pc; ++c) {
+            const float4 v = vq[(int64_t)c * ldq];
+            const float cf = scf[c];
+            acc0.x = fmaf(v.x, cf, acc0.x);
+            acc0.y = fmaf(v.y, cf, acc0.y);
+            acc0.z = fmaf(v.z, cf, acc0.z);
+            acc0.w = fmaf(v.w, cf, acc0.w);
+        }
         if (norm_last) {
-            float *vl = V + (int64_t)(p - 1) * ld + i;
-            const float v = *vl * a;
+            float4 *vl = reinterpret_cast<float4 *>(V) + (int64_t)(p - 1) * ldq + q;
+            float4 v = *vl;
+            v.x *= a;
+            v.y *= a;
+            v.z *= a;
+            v.w *= a;
             *vl = v;
-            acc1 = fmaf(v, scf[p - 1], acc1);
+            const float cf = scf[p - 1];
+            acc1.x = fmaf(v.x, cf, acc1.x);
+            acc1.y = fmaf(v.y, cf, acc1.y);
+            acc1.z = fmaf(v.z, cf, acc1.z);
+            acc1.w = fmaf(v.w, cf, acc1.w);
         }
-        out[i] = fmaf(a, src[i], -(acc0 + acc1));
+        const float4 sv = reinterpret_cast<const float4 *>(src)[q];
+        float4 o;
+        o.x = fmaf(a, sv.x, -(acc0.x + acc1.x));
+        o.y = fmaf(a, sv.y, -(acc0.y + acc1.y));
+        o.z = fmaf(a, sv.z, -(acc0.z + acc1.z));
+        o.w = fmaf(a, sv.w, -(acc0.w + acc1.w));
+        reinterpret_cast<float4 *>(out)[q] = o;
     }
 }
 
@@ -227,7 +265,10 @@ k_xupdate32(const float *__restrict__ V, int64_t ld, int64_t n, const double *__
 // ---- launchers ----
 cudaError_t launch_spmv32(const Workspace &w, const float *x, float *y, cudaStream_t s)
 {
-    const int grid = w.num_sms * kBlocksPerSM;
+    // one thread (short rows) or one warp (long rows) per row, all rows in flight at once
+    const int64_t per_block = w.spmv_warp_rows ? kStreamThreads / 32 : kStreamThreads;
+    const int64_t want = (w.n + per_block - 1) / per_block;
+    const int grid = (int)(want < (int64_t)1 << 30 ? want : (int64_t)1 << 30);
     if (w.spmv_warp_rows)
         launch_k(false, k_spmv32_warp, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.rowptr, w.colind, w.val32,
                  x, y, (const DevState *)w.st);
@@ -257,8 +298,9 @@ cudaError_t launch_update32(const Workspace &w, int p, const double *coef, doubl
                             float *out, bool norm_last, cudaStream_t s)
 {
     const size_t smem = sizeof(float) * (size_t)(p > 0 ? p : 1);
-    const int grid = (int)((w.n + kStreamThreads - 1) / kStreamThreads);
-    launch_k(false, k_update32, dim3(grid), dim3(kStreamThreads), smem, s, w.V32, w.ld, p, w.n, coef, alpha, src,
+    const int64_t n4 = (w.n + 3) & ~int64_t(3);
+    const int grid = (int)((n4 / 4 + kStreamThreads - 1) / kStreamThreads);
+    launch_k(false, k_update32, dim3(grid), dim3(kStreamThreads), smem, s, w.V32, w.ld, p, n4, coef, alpha, src,
              out, norm_last ? 1 : 0, (const DevState *)w.st);
     return cudaGetLastError();
 }

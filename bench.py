@@ -17,7 +17,9 @@ GB300) with its HBM throughput alongside; `cpu_baseline` times the CPU oracle on
 cycle of the same workload.  With --gpus N > 1 (torchrun) every rank runs an independent
 replica (the method has no data-parallel exchange on one system): weak scaling.
 
-The line also carries `batched`: the batched form (include/igs_batch.h) on 4096 banded
+The line also carries `precision`: the FP32-basis form inside FP64 iterative refinement
+against the FP64 form on the 160^3 convection-diffusion system (n = 4.1M, m = 200) to
+beta <= 1e-14, with the FP32 multi-dot's HBM roofline; and `batched`: the batched form (include/igs_batch.h) on 4096 banded
 systems (n ~ U{64..2048}, 7 diagonals, m = 50, every system to beta <= 1e-12) in solves/s,
 its FP64 roofline, and the same systems solved one at a time by igs_solve (a sample) for
 comparison.  `--workload batched` prints that measurement as the main line instead.
@@ -336,6 +338,75 @@ def run_batched(args, pkg, torch, local, dist, with_one_at_a_time=True):
     return line
 
 
+PREC_N, PREC_PECLET, PREC_M, PREC_TOL = 160, 20.0, 200, 1e-14
+
+
+def prec_config(N=PREC_N):
+    return {"workload": f"precision form: cd3d {N}^3 upwind convection-diffusion, Pe {PREC_PECLET:g}",
+            "n": N ** 3, "nnz": 7 * N ** 3 - 6 * N ** 2, "restart_m": PREC_M, "gs_iters": 2,
+            "tol_beta": PREC_TOL,
+            "step": "one solve to beta <= 1e-14: FP32 basis inside FP64 iterative refinement vs all-FP64",
+            "l2": "inputs larger than L2 (FP32 basis 3.3 GB, FP64 basis 6.6 GB)"}
+
+
+def run_precision(args, pkg, torch, local, dist):
+    """The precision form (igs_solve, precision = fp32_ir) against the FP64 form on the same
+    3-D system to beta <= 1e-14: device time of each solve, the FP32 multi-dot's HBM roofline
+    (eager re-run of one cycle with CUDA events per launch), and the difference between the
+    two solutions (the FP64 form is the reference at this size: the CPU oracle would need
+    hours; both forms are parity-tested against it on smaller grids)."""
+    ws, rank, _ = dist_env()
+    N = args.prec_grid
+    A, b, _, _ = gen.cd3d(N, PREC_PECLET, SEED + rank)
+    stream = torch.cuda.current_stream()
+    t_create = time.perf_counter()
+    sv = pkg.Solver(A, max_restart_m=PREC_M, device=local, stream=stream.cuda_stream, fp32_basis=True)
+    t_create = time.perf_counter() - t_create
+    bd = torch.from_numpy(b).cuda()
+    x32, x64 = torch.empty_like(bd), torch.empty_like(bd)
+    for prec in ("fp32_ir", "fp64"):  # capture each form's cycle graph
+        sv.solve(bd, m=PREC_M, gs=2, tol=0.0, max_restarts=1, x_out=x32, precision=prec, hist_cap=0)
+    out = {}
+    for prec, xo in (("fp32_ir", x32), ("fp64", x64)):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = sv.solve(bd, m=PREC_M, gs=2, tol=PREC_TOL, max_restarts=100, x_out=xo, precision=prec, hist_cap=0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ms, _, _ = reduce_replicas(ms, 0.0, 1, dist, "cuda")
+        out[prec] = {"ms": ms, "solves_per_s": ws / (ms / 1e3), "status": r["status"], "beta": r["beta"],
+                     "steps": r["steps"], "cycles": r["cycles"], "arnoldi_steps_per_s": r["steps"] / (ms / 1e3)}
+    diff = float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64))
+    # roofline of the FP32 multi-dot (the form's largest kernel), one eager cycle
+    sv.profile_enable(True)
+    sv.solve(bd, m=PREC_M, gs=2, tol=0.0, max_restarts=1, x_out=x32, precision="fp32_ir", hist_cap=0)
+    prof = sv.profile()
+    sv.profile_enable(False)
+    sv.close()
+    d = prof["dots"]
+    hbm_peak = 6681.5
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", hbm_peak)
+    except Exception:
+        pass
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    total_ms = sum(v["ms"] for v in prof.values())
+    return {"metric": "solves/s", "value": out["fp32_ir"]["solves_per_s"], "unit": "solves/s",
+            "config": prec_config(N), "fp32_ir": out["fp32_ir"], "fp64": out["fp64"],
+            "speedup_vs_fp64": out["fp64"]["ms"] / out["fp32_ir"]["ms"],
+            "x_rel_diff_vs_fp64": diff, "create_s": t_create,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "kernel": "k_dots32 (FP32-basis multi-dot, Alg. 4.1 steps 5 and 14)",
+                         "bytes_per_launch": d["bytes"] / max(1, d["launches"]),
+                         "share_of_cycle": d["ms"] / total_ms if total_ms else None,
+                         "kernel_ms_per_cycle": {k: v["ms"] for k, v in prof.items()}}}
+
+
 def oracle_batch_rate(stride=128):
     """Solves/s of the CPU oracle (one thread) on every stride-th system of the batch."""
     import oracle
@@ -360,13 +431,16 @@ def main():
     ap.add_argument("--gs", type=int, default=2)
     ap.add_argument("--impl", default="igs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cd2d", choices=["cd2d", "batched"])
+    ap.add_argument("--workload", default="cd2d", choices=["cd2d", "batched", "precision"])
+    ap.add_argument("--prec-grid", type=int, default=PREC_N,
+                    help="grid side of the precision-form workload (smaller sides: profiling cases)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched sub-measurement")
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
                     help="systems in the batched workload (smaller counts: profiling cases)")
     ap.add_argument("--batch-launch", default="",
                     help="T:B = block threads and CTAs per SM for the batched kernel (default: tuned)")
     ap.add_argument("--no-one-at-a-time", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the precision-form sub-measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -387,6 +461,22 @@ def main():
     if dist:
         dist.barrier()
     import paper_2205_07805_gb300 as pkg
+
+    if args.workload == "precision":
+        clocks = Clocks(local)
+        clocks.start()
+        pl = run_precision(args, pkg, torch, local, dist)
+        clk = clocks.stop()
+        line = {"metric": "solves/s", "value": pl["value"], "unit": "solves/s", "n_gpus": ws, "steps": 1,
+                "warmup": 1, "ms_per_step": pl["fp32_ir"]["ms"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 basis / f64 refinement", "data": "synthetic",
+                "config": pl["config"], "roofline": pl["roofline"], "clocks": clk,
+                **{k: pl[k] for k in ("fp32_ir", "fp64", "speedup_vs_fp64", "x_rel_diff_vs_fp64")}}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
 
     if args.workload == "batched":
         clocks = Clocks(local)
@@ -504,6 +594,8 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"one full cycle ({M} Arnoldi columns) of the same workload, {dt:.1f} s"}
     solver.close()
+    if not args.no_precision:
+        line["precision"] = run_precision(args, pkg, torch, local, dist)
     if not args.no_batched:
         bl = run_batched(args, pkg, torch, local, dist)
         line["batched"] = {k: bl[k] for k in ("metric", "value", "unit", "ms_per_step", "arnoldi_steps_per_s",

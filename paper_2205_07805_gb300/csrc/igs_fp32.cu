@@ -281,7 +281,9 @@ cudaError_t launch_spmv32(const Workspace &w, const float *x, float *y, cudaStre
 cudaError_t launch_dots32(const Workspace &w, int p, const float *x0, const float *x1, cudaStream_t s,
                           DotsPlan *plan_out)
 {
-    const DotsPlan pl = plan_dots(w, p);
+    // one wave: two resident blocks per SM (register budget of k_dots32), never more row
+    // blocks than the FP64 plan (whose partial-sum capacity the workspace holds)
+    const DotsPlan pl = plan_dots_slots(w, p, 2 * w.num_sms);
     if (plan_out) *plan_out = pl;
     const int64_t n4 = (w.n + 3) / 4 * 4;
     dim3 grid(pl.rblocks, pl.groups);

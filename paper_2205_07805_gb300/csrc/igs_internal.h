@@ -118,6 +118,8 @@ struct DotsPlan {
     int64_t rows;    // rows per row block (multiple of 4)
 };
 DotsPlan plan_dots(const Workspace &w, int p);
+// The same plan for a grid of at most `slots` blocks (groups x row blocks).
+DotsPlan plan_dots_slots(const Workspace &w, int p, int slots);
 
 // Kernel classes (match IGS_KCLASS_* in igs.h).
 enum KClass { KC_SPMV = 0, KC_DOTS = 1, KC_UPDATE = 2, KC_SMALL = 3, KC_CYCLE = 4 };

@@ -1033,10 +1033,11 @@ static int dots_slots(const Workspace &w)
     return w.num_sms * kDotsBlocksPerSM;
 }
 
-DotsPlan plan_dots(const Workspace &w, int p)
+DotsPlan plan_dots(const Workspace &w, int p) { return plan_dots_slots(w, p, dots_slots(w)); }
+
+DotsPlan plan_dots_slots(const Workspace &w, int p, int slots)
 {
     DotsPlan pl;
-    const int slots = dots_slots(w);
     int groups = (p + kDotsColsPerBlock - 1) / kDotsColsPerBlock;
     if (groups > slots) groups = slots;
     if (groups < 1) groups = 1;

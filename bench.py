@@ -19,7 +19,10 @@ replica (the method has no data-parallel exchange on one system): weak scaling.
 
 The line also carries `precision`: the FP32-basis form inside FP64 iterative refinement
 against the FP64 form on the 160^3 convection-diffusion system (n = 4.1M, m = 200) to
-beta <= 1e-14, with the FP32 multi-dot's HBM roofline; and `batched`: the batched form (include/igs_batch.h) on 4096 banded
+beta <= 1e-14, with the FP32 multi-dot's HBM roofline; `served`: a Poisson stream of
+2-D convection-diffusion requests (2000/s, sides 64..1024) replayed against the request
+server (include/igs_serve.h) for a 20 s window (60 s with --workload served), with served
+solves/s, p50/p99 latency and the refused backlog; and `batched`: the batched form (include/igs_batch.h) on 4096 banded
 systems (n ~ U{64..2048}, 7 diagonals, m = 50, every system to beta <= 1e-12) in solves/s,
 its FP64 roofline, and the same systems solved one at a time by igs_solve (a sample) for
 comparison.  `--workload batched` prints that measurement as the main line instead.
@@ -407,6 +410,116 @@ def run_precision(args, pkg, torch, local, dist):
                          "kernel_ms_per_cycle": {k: v["ms"] for k, v in prof.items()}}}
 
 
+SERVE_LAMBDA, SERVE_SIDES, SERVE_PE, SERVE_TOLS, SERVE_M = 2000.0, (64, 1024), (1.0, 100.0), (1e-10, 1e-14), 100
+SERVE_ARENA = 150 * (1 << 30)
+
+
+def serve_config(duration):
+    return {"workload": "served: Poisson arrivals of 2-D upwind convection-diffusion solves",
+            "lambda_per_s": SERVE_LAMBDA, "window_s": duration, "grid_side": list(SERVE_SIDES),
+            "peclet": list(SERVE_PE), "tol_beta": list(SERVE_TOLS), "restart_m": SERVE_M, "gs_iters": 2,
+            "precision_mix": "FP64 / FP32 basis in FP64 refinement, 50/50",
+            "basis_budget_bytes": SERVE_ARENA,
+            "step": "the whole stream: arrivals for window_s, then the admitted backlog drains"}
+
+
+def serve_stream(seed, duration):
+    """Seeded arrival stream: (arrival time, grid side, Peclet, tol, precision, rhs seed)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / SERVE_LAMBDA)
+        if t >= duration:
+            return out
+        out.append((t, int(rng.integers(SERVE_SIDES[0], SERVE_SIDES[1] + 1)),
+                    float(rng.uniform(*SERVE_PE)), SERVE_TOLS[int(rng.integers(0, 2))],
+                    "fp32_ir" if rng.integers(0, 2) else "fp64", int(rng.integers(1 << 30))))
+
+
+def run_served(args, pkg, torch, local, dist, duration, drain_s, one_at_a_time=4):
+    """Replay the arrival stream against the request server: a request is materialised (its
+    matrix generated) and submitted at its arrival time when the server's backlog has room,
+    else it is refused (counted).  Latency = completion - arrival.  Then solves one at a time
+    through igs_solve (FP64) on a sample of the same distribution."""
+    ws, rank, _ = dist_env()
+    stream = serve_stream(SEED + rank, duration)
+    max_queue = 16
+    sv = pkg.Server(max_restart_m=SERVE_M, arena_bytes=SERVE_ARENA, slots=8, rows_per_cta=4096,
+                    max_queue=max_queue, device=local)
+    arrivals, done, refused = {}, [], 0
+    t_start = sv.clock()
+    k = 0
+    while True:
+        now = sv.clock() - t_start
+        while k < len(stream) and stream[k][0] <= now:
+            t_arr, side, pe, tol, prec, rs = stream[k]
+            k += 1
+            if sv.stats()["queued"] >= max_queue:
+                refused += 1
+                continue
+            A, b, _, _ = gen.cd2d(side, pe, rs)
+            rid = sv.submit(A, b, m=SERVE_M, gs=2, tol=tol, max_restarts=2000, precision=prec)
+            if rid is None:
+                refused += 1
+                continue
+            arrivals[rid] = (t_start + t_arr, side, prec, tol)
+            sv.pump()
+        sv.pump()
+        for c in sv.poll():
+            done.append(c)
+            sv.take(c["id"])
+        st = sv.stats()
+        if now >= duration and (st["queued"] + st["running"] == 0 or now >= duration + drain_s):
+            break
+        time.sleep(0.001)
+    t_end = sv.clock()
+    st = sv.stats()
+    sv.close()
+    lat = np.array([c["t_done"] - arrivals[c["id"]][0] for c in done]) if done else np.array([np.nan])
+    svc = np.array([c["t_done"] - c["t_admit"] for c in done]) if done else np.array([np.nan])
+    ok = sum(1 for c in done if c["status"] == 0)
+    line = {"metric": "served solves/s", "value": len(done) / (t_end - t_start), "unit": "solves/s",
+            "config": serve_config(duration), "offered": len(stream), "submitted": st["submitted"],
+            "refused_backlog_full": refused, "completed": len(done), "completed_ok": ok,
+            "unfinished_at_end": st["queued"] + st["running"], "wall_s": t_end - t_start,
+            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+            "service_p50_s": float(np.percentile(svc, 50)),
+            "arena_peak_bytes": st["arena_peak"], "gpu_launches": st["launches"],
+            "by_precision": {p: sum(1 for c in done if arrivals[c["id"]][2] == p) for p in ("fp64", "fp32_ir")},
+            "max_backlog": max_queue}
+    if one_at_a_time and done:
+        # the same requests (a sample of those the server completed, spread over the run),
+        # one at a time through igs_solve in FP64 with graph-captured cycles
+        sample = [done[i] for i in np.linspace(0, len(done) - 1, min(one_at_a_time, len(done))).astype(int)]
+        by_id = {i: s_ for i, s_ in zip(range(len(stream)), stream)}
+        t_tot, n_ok, served_s = 0.0, 0, 0.0
+        for c in sample:
+            t_arr, side, prec, tol = arrivals[c["id"]]
+            rs = next(x[5] for x in stream if abs(x[0] + t_start - t_arr) < 1e-9)
+            pe = next(x[2] for x in stream if abs(x[0] + t_start - t_arr) < 1e-9)
+            A, b, _, _ = gen.cd2d(side, pe, rs)
+            st_ = torch.cuda.current_stream()
+            with pkg.Solver(A, max_restart_m=SERVE_M, device=local, stream=st_.cuda_stream) as so:
+                bd = torch.from_numpy(b).cuda()
+                xd = torch.empty_like(bd)
+                so.solve(bd, m=SERVE_M, gs=2, tol=tol, max_restarts=1, x_out=xd, hist_cap=0)  # capture
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = so.solve(bd, m=SERVE_M, gs=2, tol=tol, max_restarts=2000, x_out=xd, hist_cap=0)
+                torch.cuda.synchronize()
+                t_tot += time.perf_counter() - t0
+                n_ok += r["status"] == 0
+            served_s += c["t_done"] - c["t_admit"]
+        del by_id
+        line["one_at_a_time"] = {"value": len(sample) / t_tot, "unit": "solves/s", "converged": n_ok,
+                                 "path": "igs_solve per request (FP64, whole GPU, context set-up and "
+                                         "graph capture outside the timing)",
+                                 "sample": f"{len(sample)} of the completed requests, solved again one at a time",
+                                 "sample_served_service_s": served_s, "sample_one_at_a_time_s": t_tot}
+        line["speedup_vs_one_at_a_time"] = line["value"] / line["one_at_a_time"]["value"]
+    return line
+
+
 def oracle_batch_rate(stride=128):
     """Solves/s of the CPU oracle (one thread) on every stride-th system of the batch."""
     import oracle
@@ -431,7 +544,7 @@ def main():
     ap.add_argument("--gs", type=int, default=2)
     ap.add_argument("--impl", default="igs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cd2d", choices=["cd2d", "batched", "precision"])
+    ap.add_argument("--workload", default="cd2d", choices=["cd2d", "batched", "precision", "served"])
     ap.add_argument("--prec-grid", type=int, default=PREC_N,
                     help="grid side of the precision-form workload (smaller sides: profiling cases)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched sub-measurement")
@@ -441,6 +554,9 @@ def main():
                     help="T:B = block threads and CTAs per SM for the batched kernel (default: tuned)")
     ap.add_argument("--no-one-at-a-time", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision-form sub-measurement")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-stream sub-measurement")
+    ap.add_argument("--serve-window", type=float, default=0.0,
+                    help="arrival window in seconds (default: 60 for --workload served, 20 in the main line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -461,6 +577,23 @@ def main():
     if dist:
         dist.barrier()
     import paper_2205_07805_gb300 as pkg
+
+    if args.workload == "served":
+        clocks = Clocks(local)
+        clocks.start()
+        window = args.serve_window or 60.0
+        sl = run_served(args, pkg, torch, local, dist, window, drain_s=120.0, one_at_a_time=8)
+        clk = clocks.stop()
+        line = {"metric": sl["metric"], "value": sl["value"], "unit": sl["unit"], "n_gpus": ws, "steps": 1,
+                "warmup": 0, "ms_per_step": 1e3 * sl["wall_s"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64 / f32 basis in f64 refinement", "data": "synthetic",
+                "config": sl["config"], "clocks": clk,
+                **{k: v for k, v in sl.items() if k not in ("metric", "value", "unit", "config")}}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
 
     if args.workload == "precision":
         clocks = Clocks(local)
@@ -596,6 +729,9 @@ def main():
     solver.close()
     if not args.no_precision:
         line["precision"] = run_precision(args, pkg, torch, local, dist)
+    if not args.no_served:
+        line["served"] = run_served(args, pkg, torch, local, dist, args.serve_window or 20.0, drain_s=30.0,
+                                    one_at_a_time=4)
     if not args.no_batched:
         bl = run_batched(args, pkg, torch, local, dist)
         line["batched"] = {k: bl[k] for k in ("metric", "value", "unit", "ms_per_step", "arnoldi_steps_per_s",

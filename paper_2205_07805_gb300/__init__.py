@@ -14,9 +14,10 @@ from typing import Any
 
 import numpy as np
 
-__all__ = ["Solver", "BatchSolver", "block_csr", "IGSError", "load_library", "library_path", "status_string",
+__all__ = ["Solver", "BatchSolver", "Server", "block_csr", "IGSError", "load_library", "library_path", "status_string",
            "OK", "NOT_CONVERGED", "BREAKDOWN", "EINVAL", "ENOMEM", "ECUDA", "ENUMERIC",
-           "KCLASS_NAMES", "EXPORTED_SYMBOLS", "EXPORTED_BATCH_SYMBOLS"]
+           "KCLASS_NAMES", "EXPORTED_SYMBOLS", "EXPORTED_BATCH_SYMBOLS",
+           "EXPORTED_SERVE_SYMBOLS"]
 
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, ENOTIMPL = -1, -2, -3, -4, -5, -6
@@ -30,6 +31,10 @@ EXPORTED_SYMBOLS = ["igs_create", "igs_destroy", "igs_solve", "igs_arnoldi", "ig
 EXPORTED_BATCH_SYMBOLS = ["igs_batch_create", "igs_batch_destroy", "igs_batch_solve",
                           "igs_batch_set_config", "igs_batch_tune", "igs_batch_get_info",
                           "igs_batch_get_norms", "igs_batch_last_error"]
+# Every function declared in include/igs_serve.h.
+EXPORTED_SERVE_SYMBOLS = ["igs_server_create", "igs_server_destroy", "igs_server_submit",
+                          "igs_server_pump", "igs_server_poll", "igs_server_take_result",
+                          "igs_server_get_stats", "igs_server_clock", "igs_server_last_error"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -105,6 +110,30 @@ class _BatchInfo(C.Structure):
                 ("basis_bytes", C.c_int64), ("n_tune", C.c_int), ("tune", _TuneEntry * 32)]
 
 
+class _ServerOpts(C.Structure):
+    _fields_ = [("device", C.c_int), ("max_restart_m", C.c_int), ("arena_bytes", C.c_int64),
+                ("slots", C.c_int), ("rows_per_cta", C.c_int), ("max_queue", C.c_int)]
+
+
+class _Request(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("colind", C.c_void_p),
+                ("vals", C.c_void_p), ("b", C.c_void_p), ("x0", C.c_void_p), ("A_norm2", C.c_double),
+                ("restart_m", C.c_int), ("gs_iters", C.c_int), ("tol_beta", C.c_double),
+                ("max_restarts", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double)]
+
+
+class _Completion(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int), ("beta", C.c_double), ("steps", C.c_int64),
+                ("cycles", C.c_int), ("gang_ctas", C.c_int), ("device_bytes", C.c_int64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("queued", C.c_int64), ("running", C.c_int64),
+                ("completed", C.c_int64), ("arena_bytes", C.c_int64), ("arena_used", C.c_int64),
+                ("arena_peak", C.c_int64), ("launches", C.c_int64)]
+
+
 _lib = None
 
 
@@ -158,6 +187,24 @@ def load_library(path: str | None = None):
     lib.igs_batch_get_norms.restype = i32
     lib.igs_batch_last_error.argtypes = [vp]
     lib.igs_batch_last_error.restype = C.c_char_p
+    lib.igs_server_create.argtypes = [C.POINTER(vp), C.POINTER(_ServerOpts)]
+    lib.igs_server_create.restype = i32
+    lib.igs_server_destroy.argtypes = [vp]
+    lib.igs_server_destroy.restype = None
+    lib.igs_server_submit.argtypes = [vp, C.POINTER(_Request), C.POINTER(i64)]
+    lib.igs_server_submit.restype = i32
+    lib.igs_server_pump.argtypes = [vp, C.POINTER(i32)]
+    lib.igs_server_pump.restype = i32
+    lib.igs_server_poll.argtypes = [vp, C.POINTER(_Completion), i32, C.POINTER(i32)]
+    lib.igs_server_poll.restype = i32
+    lib.igs_server_take_result.argtypes = [vp, i64, vp]
+    lib.igs_server_take_result.restype = i32
+    lib.igs_server_get_stats.argtypes = [vp, C.POINTER(_ServerStats)]
+    lib.igs_server_get_stats.restype = i32
+    lib.igs_server_clock.argtypes = [vp]
+    lib.igs_server_clock.restype = dbl
+    lib.igs_server_last_error.argtypes = [vp]
+    lib.igs_server_last_error.restype = C.c_char_p
     if path is None:
         _lib = lib
     return lib
@@ -494,3 +541,112 @@ class BatchSolver:
                  n_not_converged=res.n_not_converged, n_breakdown=res.n_breakdown,
                  n_numeric=res.n_numeric, device_ms=res.device_ms)
         return o
+
+
+# ----------------------------------------------------------------------------------------
+# Request server (include/igs_serve.h)
+# ----------------------------------------------------------------------------------------
+class Server:
+    """Continuous-batching request server (``igs_server_create``).  ``submit`` queues a
+    request (host arrays), ``pump`` admits what fits and collects finished requests,
+    ``poll`` returns completion records, ``take`` the solution of a completed request."""
+
+    def __init__(self, max_restart_m: int = 100, arena_bytes: int = 1 << 30, slots: int = 8,
+                 rows_per_cta: int = 4096, max_queue: int = 0, device: int = 0):
+        self._lib = load_library()
+        opts = _ServerOpts(int(device), int(max_restart_m), int(arena_bytes), int(slots),
+                           int(rows_per_cta), int(max_queue))
+        h = C.c_void_p()
+        rc = self._lib.igs_server_create(C.byref(h), C.byref(opts))
+        if rc != OK:
+            raise IGSError(rc, "igs_server_create")
+        self._h = h
+        self._n = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.igs_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _err(self, rc: int, what: str):
+        raise IGSError(rc, f"{what}: {self._lib.igs_status_string(rc).decode()}: "
+                           f"{self._lib.igs_server_last_error(self._h).decode()}")
+
+    def submit(self, A, b, x0=None, A_norm2: float = 0.0, m: int = 100, gs: int = 2,
+               tol: float = 1e-12, max_restarts: int = 100, precision: str = "fp64",
+               inner_tol: float = 0.0):
+        """Queue one request; returns its id, or None when the queue is full."""
+        rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(A.colind, dtype=np.int32)
+        va = np.ascontiguousarray(A.val, dtype=np.float64)
+        bb = np.ascontiguousarray(b, dtype=np.float64)
+        xx = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+        req = _Request(int(A.n), int(rp[-1]), C.c_void_p(rp.ctypes.data), C.c_void_p(ci.ctypes.data),
+                       C.c_void_p(va.ctypes.data), C.c_void_p(bb.ctypes.data),
+                       C.c_void_p(xx.ctypes.data) if xx is not None else None, float(A_norm2),
+                       int(m), int(gs), float(tol), int(max_restarts), PRECISIONS[precision],
+                       float(inner_tol))
+        rid = C.c_int64(0)
+        rc = self._lib.igs_server_submit(self._h, C.byref(req), C.byref(rid))
+        if rc == ENOMEM:
+            return None
+        if rc != OK:
+            self._err(rc, "igs_server_submit")
+        self._n[rid.value] = int(A.n)
+        return rid.value
+
+    def pump(self) -> int:
+        running = C.c_int(0)
+        rc = self._lib.igs_server_pump(self._h, C.byref(running))
+        if rc != OK:
+            self._err(rc, "igs_server_pump")
+        return running.value
+
+    def poll(self, max_out: int = 256) -> list:
+        buf = (_Completion * max_out)()
+        k = C.c_int(0)
+        self._lib.igs_server_poll(self._h, buf, int(max_out), C.byref(k))
+        return [{f: getattr(buf[i], f) for f, _ in _Completion._fields_} for i in range(k.value)]
+
+    def take(self, rid: int) -> np.ndarray:
+        x = np.empty(self._n[rid])
+        rc = self._lib.igs_server_take_result(self._h, int(rid), C.c_void_p(x.ctypes.data))
+        if rc != OK:
+            self._err(rc, "igs_server_take_result")
+        del self._n[rid]
+        return x
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        self._lib.igs_server_get_stats(self._h, C.byref(st))
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
+
+    def clock(self) -> float:
+        return float(self._lib.igs_server_clock(self._h))
+
+    def run_all(self, sleep_s: float = 0.0005) -> list:
+        """Pump until nothing is queued or running; returns all completion records."""
+        import time
+        out = []
+        while True:
+            running = self.pump()
+            out += self.poll()
+            st = self.stats()
+            if running == 0 and st["queued"] == 0:
+                out += self.poll()
+                return out
+            time.sleep(sleep_s)

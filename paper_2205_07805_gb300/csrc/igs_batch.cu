@@ -2,35 +2,28 @@
 // persistent kernel launch.
 //
 // Each CTA takes systems from a device work queue (largest first) and runs the whole
-// restarted IGS-GMRES(m) of Alg. 4.1 on one system at a time: cycle start r = b - A x and
-// the backward error of eq. "nrbe", step 1 (v_1 = r / rho), step 2 (the single-projection
-// prime), the k = 3..m+1 loop (steps 4-18: SpMV, the fused reduction of step 5, the lagged
-// normalisation of steps 6-11, one or two Gauss-Seidel corrections with the unit lower
-// triangular (I + L), the Hessenberg column of step 17), the Givens least squares beside
-// it with the in-cycle stop test, the flush that sets H_{m+1,m}, and x_m = x_0 + V_m y_m.
-// The control flow (stop, breakdown and restart rules) is the same as the single-system
-// path's.  Every per-step scalar lives in shared memory, so a step costs no kernel launch
-// and no host round trip.
+// restarted IGS-GMRES(m) of Alg. 4.1 on one system at a time: the device solver of
+// igs_sysdev.cuh with a gang of one CTA (cycle start and the backward error of eq. "nrbe",
+// steps 1-18, the Givens least squares with the in-cycle stop test, the flush, x_m = x_0 +
+// V_m y_m, breakdown and restarts, with the single-system path's control flow).  Every
+// per-step scalar lives in shared memory, so a step costs no kernel launch and no host round
+// trip.
 //
 // Determinism: the arithmetic of a system depends only on that system (its n, its CSR rows
 // and the solve options), never on the CTA, the block size, the number of resident CTAs or
-// the other systems of the batch:
-//   - a dot product is summed over row slices whose number depends on n and the column count
-//     only (pick_slices), each slice in row order with two interleaved chains, then over
-//     the slices in order;
-//   - every row of an update or SpMV is one thread's fixed-order chain;
-//   - the triangular solves, the Givens scan and the back substitution run on warp 0 with
-//     fixed lane roles.
+// the other systems of the batch (igs_sysdev.cuh: fixed slices and orders, fixed lane roles).
 // So a system's x, beta and step count are bitwise the same whether it is solved alone or
 // in a batch, and under every launch configuration the tuner may pick.
 //
 // Memory: each CTA (slot) owns a basis V of (m+1) columns with leading dimension
 // round_up(n, 4) and the Givens factor R (packed upper, column-major) in HBM (re-read from
 // L2 when the working set fits); the Krylov vector z/u, the slice partial sums, L (packed
-// strictly-lower, column-major) and the small vectors are in shared memory.
+// strictly-lower, column-major) and the small vectors are in shared memory.  A is kept in
+// SELL-32 (32-row slices, each as wide as its longest row, entries in CSR order).
 #include "../../include/igs.h"
 #include "../../include/igs_batch.h"
 #include "igs_internal.h"
+#include "igs_sysdev.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -43,75 +36,17 @@
 namespace igs {
 namespace batch {
 
-constexpr int kMaxM = IGS_BATCH_MAX_M;  // largest restart length (two rows per lane in warp solves)
+using sysdev::round_up;
+using sysdev::SmemLayout;
+
+constexpr int kMaxM = IGS_BATCH_MAX_M;  // largest restart length of the batched solver
 constexpr int kMaxN = IGS_BATCH_MAX_N;  // largest system (the Krylov vector is kept in shared memory)
-constexpr int kMaxSlices = 16;      // dot products are split into at most this many row slices
-constexpr int kMaxSlotsPerSM = 8;   // largest resident CTAs per SM any configuration uses
-
-__host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
-
-// Row slices of the dot products.  A system of n2 (even) rows is cut into nsl slices of
-// whole row pairs, slice s holding pairs [s*P/nsl, (s+1)*P/nsl) (P = n2/2).  For a product
-// over pc columns, nsl is chosen in [slices_lo(n2), slices_hi(n2)] so that the nsl*pc
-// (slice, column) items leave the fewest idle lanes in the last warp; the choice depends
-// on n and pc only.
-__host__ __device__ inline int slices_hi(int n2)
-{
-    const int s = (n2 >> 1) / 4;  // at least four row pairs per slice
-    return s < 1 ? 1 : (s > kMaxSlices ? kMaxSlices : s);
-}
-__host__ __device__ inline int slices_lo(int n2) { return slices_hi(n2) < 8 ? slices_hi(n2) : 8; }
-
-__host__ __device__ inline int pick_slices(int n2, int pc)
-{
-    int best = slices_lo(n2), best_idle = 0, best_tot = 1;
-    for (int s = slices_lo(n2); s <= slices_hi(n2); ++s) {
-        const int items = s * pc;
-        const int tot = (items + 31) / 32 * 32;
-        const int idle = tot - items;
-        if (s == slices_lo(n2) || idle * best_tot < best_idle * tot) {
-            best = s;
-            best_idle = idle;
-            best_tot = tot;
-        }
-    }
-    return best;
-}
-
-// Shared-memory index of row i of the Krylov vector: two doubles of padding every 128 rows
-// put the starts of different slices in different banks.
-__host__ __device__ inline int pad_idx(int i) { return i + 2 * (i >> 7); }
-
-// Packed strictly-lower L of order m+1, column-major: column c holds rows c+1..m.
-__host__ __device__ inline int lower_base(int c, int m) { return c * m - c * (c - 1) / 2 - c - 1; }
-// Packed upper R (order m), column-major: column j holds rows 0..j.
-__host__ __device__ inline int upper_base(int j) { return j * (j + 1) / 2; }
-
-// Offsets (in doubles) of the dynamic shared-memory arrays for a batch with largest system
-// nmax and restart m.
-struct SmemLayout {
-    int zu, part, L, red, r0, r1, r3, hcol, cs, sn, g, y, total;
-};
+constexpr int kMaxSlotsPerSM = 8;       // largest resident CTAs per SM any configuration uses
+static_assert(kMaxM <= sysdev::kMaxM, "restart length beyond the device solver's limit");
 
 __host__ __device__ inline SmemLayout smem_layout(int nmax, int m)
 {
-    SmemLayout s;
-    int o = 0;
-    const int n2 = round_up(nmax, 2);
-    s.zu = o;   o += round_up(pad_idx(n2) + 2, 2);
-    s.part = o; o += round_up(kMaxSlices * (m + 1) * 2, 2);
-    s.L = o;    o += round_up((m + 1) * m / 2 + 1, 2);
-    s.red = o;  o += round_up(2 * (m + 1), 2);
-    s.r0 = o;   o += round_up(m + 1, 2);
-    s.r1 = o;   o += round_up(m + 1, 2);
-    s.r3 = o;   o += round_up(m + 1, 2);
-    s.hcol = o; o += round_up(m + 2, 2);
-    s.cs = o;   o += round_up(m + 1, 2);
-    s.sn = o;   o += round_up(m + 1, 2);
-    s.g = o;    o += round_up(m + 2, 2);
-    s.y = o;    o += round_up(m + 1, 2);
-    s.total = o;
-    return s;
+    return sysdev::smem_layout<double>(round_up(nmax, 2), m);
 }
 
 // Matrix and workspace of a batch (kernel argument, by value).
@@ -131,7 +66,7 @@ struct Args {
     int64_t slot_stride;      // doubles per slot
     int64_t r_offset;         // doubles from a slot's start to its R
     unsigned int *queue;      // work counter (zeroed before each launch)
-    unsigned long long *summary;  // [0] total steps, [1+k] systems with status code k+4
+    unsigned long long *summary;  // [0] total steps, [1+k] systems with status code k-6
 };
 
 // Per-call parameters, copied to the device before each launch.
@@ -151,532 +86,33 @@ struct Run {
     int *cycles;        // nullable
 };
 
-// Block-uniform state of the system being solved.
-struct Shared {
-    double nb, normA, rho, inv, stop_den, beta, rn, xn;
-    int status, cst, done, stop, cycles;
-    int swarp;  // warp of this CTA that runs the single-warp steps
-    long long steps;
-};
-
-struct Sys {
-    int n, n2, ldv, slice0;
-    int64_t row0;
-};
-
-__device__ __forceinline__ double2 ld2(const double *p) { return *reinterpret_cast<const double2 *>(p); }
-__device__ __forceinline__ void st2(double *p, double2 v) { *reinterpret_cast<double2 *>(p) = v; }
-
-// y = A x, or y = b - A x when b != null (rows >= n of y are set to 0).  x, b: system-local.
-// Each row is summed in its CSR order; lanes of a warp read consecutive SELL entries.
-template <bool OUT_PAD>
-__device__ void b_spmv(const Args &a, const Sys &S, const double *x, const double *b, double *y)
+// The solve arguments of system sid in CTA slot V / R.
+__device__ sysdev::SysArgs<double> sys_args(const Args &a, const Run &run, int sid, double *V)
 {
-    const int64_t *so = a.sell_off + S.slice0;
-    for (int i = threadIdx.x; i < S.n2; i += blockDim.x) {
-        double acc = 0.0;
-        if (i < S.n) {
-            const int k = i >> 5;
-            int64_t e = so[k] + (i & 31);
-            const int64_t e1 = so[k + 1];
-            // eight entries per batch (all loads of a batch in flight together)
-            for (; e < e1; e += 256) {
-                int c[8];
-                double v[8], xv[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const bool in = e + 32 * u < e1;
-                    c[u] = in ? a.sell_col[e + 32 * u] : -1;
-                    v[u] = in ? a.sell_val[e + 32 * u] : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) xv[u] = c[u] >= 0 ? x[c[u]] : 0.0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
-            }
-            if (b) acc = b[i] - acc;
-        }
-        y[OUT_PAD ? pad_idx(i) : i] = acc;
-    }
-}
-
-// red[c*NQ + q] = V[:, c]^T X_q for c < pc (X_0 = x0, X_1 = x1; x1 is the padded shared
-// vector).  Fixed slices, fixed order (see the file comment).
-template <int NQ, bool X0PAD>
-__device__ void b_dots(const Sys &S, const double *V, int pc, const double *x0, const double *x1,
-                       double *part, double *red)
-{
-    const int nsl = pick_slices(S.n2, pc);
-    const int npairs = S.n2 >> 1;
-    const int nitems = pc * nsl;
-    for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
-        const int c = it % pc, s = it / pc;
-        const int i0 = 2 * (s * npairs / nsl);
-        const int i1 = 2 * ((s + 1) * npairs / nsl);
-        const double *vc = V + (int64_t)c * S.ldv;
-        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
-        int i = i0;
-        for (; i + 8 <= i1; i += 8) {
-            double2 v[4], xa[4], xb[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                v[u] = ld2(vc + i + 2 * u);
-                xa[u] = ld2(x0 + (X0PAD ? pad_idx(i + 2 * u) : i + 2 * u));
-                if (NQ == 2) xb[u] = ld2(x1 + pad_idx(i + 2 * u));
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                a0 = fma(v[u].x, xa[u].x, a0);
-                a1 = fma(v[u].y, xa[u].y, a1);
-                if (NQ == 2) {
-                    b0 = fma(v[u].x, xb[u].x, b0);
-                    b1 = fma(v[u].y, xb[u].y, b1);
-                }
-            }
-        }
-        for (; i < i1; i += 2) {
-            const double2 v = ld2(vc + i);
-            const double2 xa = ld2(x0 + (X0PAD ? pad_idx(i) : i));
-            a0 = fma(v.x, xa.x, a0);
-            a1 = fma(v.y, xa.y, a1);
-            if (NQ == 2) {
-                const double2 xb = ld2(x1 + pad_idx(i));
-                b0 = fma(v.x, xb.x, b0);
-                b1 = fma(v.y, xb.y, b1);
-            }
-        }
-        part[(s * pc + c) * NQ] = a0 + a1;
-        if (NQ == 2) part[(s * pc + c) * NQ + 1] = b0 + b1;
-    }
-    __syncthreads();
-    for (int v = threadIdx.x; v < pc * NQ; v += blockDim.x) {
-        double acc = 0.0;
-        for (int s = 0; s < nsl; ++s) acc += part[s * pc * NQ + v];
-        red[v] = acc;
-    }
-    __syncthreads();
-}
-
-// red[q] = ||v_q||^2 for up to two system-local vectors (any alignment), fixed slices.
-__device__ void b_sumsq(const Sys &S, const double *v0, const double *v1, int nv, double *part,
-                        double *red)
-{
-    const int nsl = slices_hi(S.n2);
-    const int nitems = nv * nsl;
-    for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
-        const int q = it % nv, s = it / nv;
-        const double *v = q == 0 ? v0 : v1;
-        const int i0 = s * S.n / nsl;
-        const int i1 = (s + 1) * S.n / nsl;
-        double a0 = 0.0, a1 = 0.0;
-        int i = i0;
-        for (; i + 1 < i1; i += 2) {
-            a0 = fma(v[i], v[i], a0);
-            a1 = fma(v[i + 1], v[i + 1], a1);
-        }
-        if (i < i1) a0 = fma(v[i], v[i], a0);
-        part[s * nv + q] = a0 + a1;
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
-        double acc = 0.0;
-        for (int s = 0; s < nsl; ++s) acc += part[s * nv + q];
-        red[q] = acc;
-    }
-    __syncthreads();
-}
-
-// out[i] = alpha * src[i] - sum_{c < pc} V[i, c] coef[c] for rows i < n2 (pairs of rows per
-// thread).  When nc >= 0 (then nc = pc - 1), column nc of V is first scaled in place by
-// scale_nc (the lagged normalisation of step 7) and the scaled column enters the sum.
-template <bool SRC_PAD, bool OUT_PAD>
-__device__ void b_update(const Sys &S, double *V, int pc, const double *coef, double alpha,
-                         const double *src, double *out, int nc, double scale_nc)
-{
-    const int npairs = S.n2 >> 1;
-    // the normalised column (always the last, nc = pc - 1) is scaled and stored before the
-    // other columns are streamed, so that no store sits between their loads; its term is
-    // still added last
-    const int ps = nc >= 0 ? nc : pc;
-    for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
-        const int i = 2 * pr;
-        double2 vn = make_double2(0.0, 0.0);
-        if (nc >= 0) {
-            vn = ld2(V + (int64_t)nc * S.ldv + i);
-            vn.x *= scale_nc;
-            vn.y *= scale_nc;
-            st2(V + (int64_t)nc * S.ldv + i, vn);
-        }
-        double sx = 0.0, sy = 0.0;
-        int c = 0;
-        for (; c + 4 <= ps; c += 4) {
-            double2 v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = ld2(V + (int64_t)(c + u) * S.ldv + i);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const double cf = coef[c + u];
-                sx = fma(v[u].x, cf, sx);
-                sy = fma(v[u].y, cf, sy);
-            }
-        }
-        for (; c < ps; ++c) {
-            const double2 v = ld2(V + (int64_t)c * S.ldv + i);
-            const double cf = coef[c];
-            sx = fma(v.x, cf, sx);
-            sy = fma(v.y, cf, sy);
-        }
-        if (nc >= 0) {
-            const double cf = coef[nc];
-            sx = fma(vn.x, cf, sx);
-            sy = fma(vn.y, cf, sy);
-        }
-        const double2 sv = ld2(src + (SRC_PAD ? pad_idx(i) : i));
-        double2 o;
-        o.x = alpha * sv.x - sx;
-        o.y = alpha * sv.y - sy;
-        st2(out + (OUT_PAD ? pad_idx(i) : i), o);
-    }
-}
-
-// x[i] = x[i] + sum_{c < p} V[i, c] y[c] for i < n (x system-local, any alignment).
-__device__ void b_xupdate(const Sys &S, const double *V, int p, const double *y, double *x)
-{
-    for (int i = threadIdx.x; i < S.n; i += blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < p; ++c) s = fma(V[(int64_t)c * S.ldv + i], y[c], s);
-        x[i] = x[i] + s;
-    }
-}
-
-// Warp 0: out = (I + L_p)^{-1} rhs by forward substitution (Alg. 4.1 steps 12 and 15),
-// p <= 64, lane l owns rows l and l + 32.
-__device__ void w_lower_solve(int p, const double *L, int m, const double *rhs, double *out)
-{
-    const int lane = threadIdx.x & 31;
-    double x0 = lane < p ? rhs[lane] : 0.0;
-    double x1 = lane + 32 < p ? rhs[lane + 32] : 0.0;
-    for (int c = 0; c + 1 < p; ++c) {
-        const double xc = __shfl_sync(0xffffffffu, c < 32 ? x0 : x1, c & 31);
-        const int base = lower_base(c, m);
-        if (c < 31 && lane > c && lane < p) x0 = fma(-L[base + lane], xc, x0);
-        if (p > 32) {
-            const int i = lane + 32;
-            if (i > c && i < p) x1 = fma(-L[base + i], xc, x1);
-        }
-    }
-    if (lane < p) out[lane] = x0;
-    if (lane + 32 < p) out[lane + 32] = x1;
-}
-
-// Warp 0: y = R_p^{-1} g by back substitution (R packed upper), p <= 64.
-__device__ void w_upper_solve(int p, const double *R, const double *g, double *y)
-{
-    const int lane = threadIdx.x & 31;
-    double a0 = lane < p ? g[lane] : 0.0;
-    double a1 = lane + 32 < p ? g[lane + 32] : 0.0;
-    for (int c = p - 1; c >= 0; --c) {
-        const int ol = c & 31;
-        const int base = upper_base(c);
-        double yc = 0.0;
-        if (lane == ol) yc = (c >= 32 ? a1 : a0) / R[base + c];
-        yc = __shfl_sync(0xffffffffu, yc, ol);
-        if (lane == 0) y[c] = yc;
-        if (lane < c) a0 = fma(-R[base + lane], yc, a0);
-        if (lane + 32 < c) a1 = fma(-R[base + lane + 32], yc, a1);
-    }
-}
-
-// Warp 0: bring Hessenberg column j (entries h[0..j], subdiagonal hsub) into the Givens QR
-// (eq. "llse").  The j earlier rotations are applied as a warp scan of the affine maps
-// a -> -s_i a + c_i h_{i+1} (lane l owns maps 2l and 2l+1), then the new rotation.  Writes
-// R column j, cs[j], sn[j], g[j], g[j+1]; returns |g_{j+1}| on every lane.
-__device__ double w_givens(int j, const double *h, double hsub, double *cs, double *sn, double *g,
-                           double *R)
-{
-    const int lane = threadIdx.x & 31;
-    const int m0 = 2 * lane;
-    double cA = 1.0, cB = 0.0;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int i = m0 + q;
-        if (i < j) {
-            const double al = -sn[i], be = cs[i] * h[i + 1];
-            cB = fma(al, cB, be);
-            cA = al * cA;
-        }
-    }
-    for (int o = 1; o < 32; o <<= 1) {
-        const double pA = __shfl_up_sync(0xffffffffu, cA, o);
-        const double pB = __shfl_up_sync(0xffffffffu, cB, o);
-        if (lane >= o) {
-            cB = fma(cA, pB, cB);
-            cA = cA * pA;
-        }
-    }
-    double eA = __shfl_up_sync(0xffffffffu, cA, 1);
-    double eB = __shfl_up_sync(0xffffffffu, cB, 1);
-    if (lane == 0) {
-        eA = 1.0;
-        eB = 0.0;
-    }
-    double av = fma(eA, h[0], eB);
-    const int rb = upper_base(j);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int i = m0 + q;
-        if (i < j) {
-            const double hi1 = h[i + 1];
-            R[rb + i] = fma(cs[i], av, sn[i] * hi1);
-            av = fma(-sn[i], av, cs[i] * hi1);
-        }
-    }
-    const double aj = j == 0 ? h[0] : __shfl_sync(0xffffffffu, av, (j - 1) >> 1);
-    const double r = hypot(aj, hsub);
-    double c = 1.0, s = 0.0;
-    if (r != 0.0) {
-        c = aj / r;
-        s = hsub / r;
-    }
-    const double gj = g[j];
-    __syncwarp();
-    if (lane == 0) {
-        cs[j] = c;
-        sn[j] = s;
-        R[rb + j] = r;
-        g[j + 1] = -s * gj;
-        g[j] = c * gj;
-    }
-    __syncwarp();
-    return fabs(s * gj);
-}
-
-// Warp 0: sum of squares of h[0..len) (lane-strided, then a fixed shuffle tree).
-__device__ double w_sumsq(const double *h, int len)
-{
-    const int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int i = lane; i < len; i += 32) s = fma(h[i], h[i], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    sysdev::SysArgs<double> s;
+    const int64_t row0 = a.sys_row0[sid];
+    s.n = (int)(a.sys_row0[sid + 1] - row0);
+    s.m = a.m;
+    s.gs = run.gs;
+    s.max_cycles = run.max_cycles;
+    s.ldv = round_up(s.n, 4);
+    s.tol = run.tol;
+    s.inner_tol = 0.0;
+    s.normA = a.normA[sid];
+    s.sell_off = a.sell_off + a.sys_slice0[sid];
+    s.sell_col = a.sell_col;
+    s.sell_val = a.sell_val;
+    s.sell_val32 = nullptr;
+    s.b = run.b + row0;
+    s.x0 = run.x0_given ? run.x0 + row0 : nullptr;
+    s.x = run.x + row0;
+    s.V = V;
+    s.r64 = nullptr;
+    s.beta_out = run.beta ? run.beta + sid : nullptr;
+    s.status_out = run.status ? run.status + sid : nullptr;
+    s.steps_out = run.steps ? run.steps + sid : nullptr;
+    s.cycles_out = run.cycles ? run.cycles + sid : nullptr;
     return s;
-}
-
-// Warp 0: complete Hessenberg column j (pending entries hcol[0..j]) with subdiagonal
-// gamma: numeric check, Givens, breakdown test, in-cycle stop test.  Returns 1 to stop.
-__device__ int w_complete_column(int j, double gamma, double *sm, const SmemLayout &L, double *R,
-                                 Shared &sh, double tol)
-{
-    const int lane = threadIdx.x & 31;
-    int stop = 0;
-    if (!isfinite(gamma)) {
-        if (lane == 0) sh.cst = IGS_ENUMERIC;
-        return 1;
-    }
-    const double hn2 = w_sumsq(sm + L.hcol, j + 1);
-    const double res = w_givens(j, sm + L.hcol, gamma, sm + L.cs, sm + L.sn, sm + L.g, R);
-    if (gamma == 0.0 || gamma <= kBreakdownFactor * sqrt(hn2)) {
-        if (lane == 0) sh.cst = IGS_BREAKDOWN;
-        stop = 1;
-    } else if (sh.stop_den > 0.0 && res / sh.stop_den <= tol) {
-        stop = 1;
-    }
-    if (lane == 0) sh.done = j + 1;
-    return stop;
-}
-
-// One Arnoldi cycle of Alg. 4.1 on the residual held in V[:, 0] (norm sh.rho).  Sets
-// sh.done (completed columns), sh.cst (IGS_OK, IGS_BREAKDOWN or IGS_ENUMERIC); the Givens
-// factorisation of the completed columns is left in R, g.
-__device__ void b_cycle(const Args &a, const Run &run, const Sys &S, double *V, double *sm,
-                        const SmemLayout &L, Shared &sh)
-{
-    const int m = a.m, gs = run.gs;
-    const bool w0 = (int)(threadIdx.x >> 5) == sh.swarp;  // the warp doing the scalar work
-    double *R = V + a.r_offset;
-    const int lane = threadIdx.x & 31;
-    double *zu = sm + L.zu, *part = sm + L.part, *red = sm + L.red;
-    if (threadIdx.x == 0) {
-        sh.cst = IGS_OK;
-        sh.done = 0;
-        sh.stop = 0;
-        sm[L.g] = sh.rho;
-    }
-    // Step 1: v_1 = r_0 / rho (in place).
-    b_update<false, false>(S, V, 0, nullptr, 1.0 / sh.rho, V, V, -1, 0.0);
-    __syncthreads();
-    // Step 2: w_2 = A v_1, H_11 = v_1^T w_2, w_2 = w_2 - H_11 v_1.
-    b_spmv<false>(a, S, V, nullptr, V + S.ldv);
-    __syncthreads();
-    b_dots<1, false>(S, V, 1, V + S.ldv, nullptr, part, red);
-    if (threadIdx.x == 0) {
-        sm[L.hcol] = red[0];
-        sm[L.r1] = red[0];
-    }
-    __syncthreads();
-    b_update<false, false>(S, V, 1, sm + L.r1, 1.0, V + S.ldv, V + S.ldv, -1, 0.0);
-    __syncthreads();
-
-    for (int k = 3; k <= m + 1; ++k) {
-        const int p = k - 1;
-        double *w = V + (int64_t)(p - 1) * S.ldv;
-        // Step 4: z = A w_{k-1}.
-        b_spmv<true>(a, S, w, nullptr, zu);
-        __syncthreads();
-        // Step 5: L row = V_{k-2}^T w, r^(0) = V_{k-1}^T z, ||w||^2, in one pass over V.
-        b_dots<2, false>(S, V, p, w, zu, part, red);
-        if (w0) {
-            // Step 6: gamma = ||w||, the subdiagonal of column p-2, which is now complete.
-            const double gamma = sqrt(red[2 * (p - 1)]);
-            int stop = w_complete_column(p - 2, gamma, sm, L, R, sh, run.tol);
-            if (!stop) {
-                const double inv = 1.0 / gamma;
-                // Steps 8-9: r^(0) / gamma, its last entry once more; step 10: L row / gamma.
-                for (int c = lane; c < p; c += 32) {
-                    double v = red[2 * c + 1] * inv;
-                    if (c == p - 1) v *= inv;
-                    sm[L.r0 + c] = v;
-                }
-                for (int c = lane; c < p - 1; c += 32) sm[L.L + lower_base(c, m) + (p - 1)] = red[2 * c] * inv;
-                __syncwarp();
-                // Step 12: r^(1) = (I + L)^{-1} r^(0).
-                w_lower_solve(p, sm + L.L, m, sm + L.r0, sm + L.r1);
-                if (gs == 1) {
-                    __syncwarp();
-                    for (int c = lane; c < p; c += 32) sm[L.hcol + c] = sm[L.r1 + c];
-                }
-                if (lane == 0) sh.inv = inv;
-            }
-            if (lane == 0) sh.stop = stop;
-        }
-        __syncthreads();
-        if (sh.stop) break;
-        const double inv = sh.inv;
-        double *wk = V + (int64_t)p * S.ldv;
-        if (gs == 2) {
-            // Steps 7, 11, 13: v_{k-1} = w / gamma in place; u = z / gamma - V_{k-1} r^(1).
-            b_update<true, true>(S, V, p, sm + L.r1, inv, zu, zu, p - 1, inv);
-            __syncthreads();
-            // Step 14: r^(2) = V_{k-1}^T u.
-            b_dots<1, true>(S, V, p, zu, nullptr, part, red);
-            if (w0) {
-                // Step 15: r^(3) = (I + L)^{-1} r^(2); step 17: H column = r^(1) + r^(3).
-                w_lower_solve(p, sm + L.L, m, red, sm + L.r3);
-                __syncwarp();
-                for (int c = lane; c < p; c += 32) sm[L.hcol + c] = sm[L.r1 + c] + sm[L.r3 + c];
-            }
-            __syncthreads();
-            // Step 16: w_k = u - V_{k-1} r^(3).
-            b_update<true, false>(S, V, p, sm + L.r3, 1.0, zu, wk, -1, 0.0);
-        } else {
-            // One Gauss-Seidel iteration: w_k = u.
-            b_update<true, false>(S, V, p, sm + L.r1, inv, zu, wk, p - 1, inv);
-        }
-        __syncthreads();
-    }
-    // Flush: gamma_{m+1} = ||w_{m+1}|| completes column m-1.
-    if (!sh.stop && sh.cst == IGS_OK && sh.done == m - 1) {
-        b_sumsq(S, V + (int64_t)m * S.ldv, nullptr, 1, part, red);
-        if (w0) w_complete_column(m - 1, sqrt(red[0]), sm, L, R, sh, run.tol);
-        __syncthreads();
-    }
-}
-
-// Restarted IGS-GMRES(m) on system `sid`, the same control flow as the single-system solver.
-__device__ void b_solve_system(const Args &a, const Run &run, int sid, double *V, double *sm,
-                               const SmemLayout &L, Shared &sh)
-{
-    Sys S;
-    S.row0 = a.sys_row0[sid];
-    S.n = (int)(a.sys_row0[sid + 1] - S.row0);
-    S.n2 = round_up(S.n, 2);
-    S.ldv = round_up(S.n, 4);
-    S.slice0 = a.sys_slice0[sid];
-    const double *b = run.b + S.row0;
-    double *x = run.x + S.row0;
-    const double *x0 = run.x0_given ? run.x0 + S.row0 : nullptr;
-    double *part = sm + L.part, *red = sm + L.red;
-
-    for (int i = threadIdx.x; i < S.n; i += blockDim.x) x[i] = x0 ? x0[i] : 0.0;
-    b_sumsq(S, b, nullptr, 1, part, red);
-    if (threadIdx.x == 0) {
-        sh.nb = sqrt(red[0]);
-        sh.normA = a.normA[sid];
-        sh.cycles = 0;
-        sh.steps = 0;
-        sh.status = IGS_NOT_CONVERGED;
-        sh.beta = nan("");
-    }
-    __syncthreads();
-    for (;;) {
-        // r_0 = b - A x_0 into V[:, 0]; beta(x) per eq. "nrbe" (zero residual: beta = 0).
-        b_spmv<false>(a, S, x, b, V);
-        __syncthreads();
-        b_sumsq(S, V, x, 2, part, red);
-        int brk = 0;
-        if (threadIdx.x == 0) {
-            const double rn = sqrt(red[0]), xn = sqrt(red[1]);
-            const double beta = rn == 0.0 ? 0.0 : rn / (sh.nb + sh.normA * xn);
-            sh.beta = beta;
-            if (!isfinite(beta)) {
-                sh.status = IGS_ENUMERIC;
-                brk = 1;
-            } else if (beta <= run.tol || rn == 0.0) {
-                sh.status = IGS_OK;
-                brk = 1;
-            } else if (sh.cycles >= run.max_cycles) {
-                sh.status = IGS_NOT_CONVERGED;
-                brk = 1;
-            }
-            sh.rho = rn;
-            sh.stop_den = sh.nb + sh.normA * xn;
-            sh.stop = brk;
-        }
-        __syncthreads();
-        if (sh.stop) break;
-        b_cycle(a, run, S, V, sm, L, sh);
-        const int done = sh.done, cst = sh.cst;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            sh.steps += done;
-            sh.cycles += 1;
-        }
-        if (cst == IGS_ENUMERIC) {
-            if (threadIdx.x == 0) sh.status = IGS_ENUMERIC;
-            __syncthreads();
-            break;
-        }
-        // x_m = x_0 + V_m y_m (y by back substitution on the Givens factor).
-        if (done > 0) {
-            if ((int)(threadIdx.x >> 5) == sh.swarp) w_upper_solve(done, V + a.r_offset, sm + L.g, sm + L.y);
-            __syncthreads();
-            b_xupdate(S, V, done, sm + L.y, x);
-        }
-        __syncthreads();
-        if (cst == IGS_BREAKDOWN) {
-            b_spmv<false>(a, S, x, b, V);
-            __syncthreads();
-            b_sumsq(S, V, x, 2, part, red);
-            if (threadIdx.x == 0) {
-                const double rn = sqrt(red[0]), xn = sqrt(red[1]);
-                const double beta = rn == 0.0 ? 0.0 : rn / (sh.nb + sh.normA * xn);
-                sh.beta = beta;
-                sh.status = (isfinite(beta) && beta <= run.tol) ? IGS_OK : IGS_BREAKDOWN;
-            }
-            __syncthreads();
-            break;
-        }
-    }
-    if (threadIdx.x == 0) {
-        if (run.beta) run.beta[sid] = sh.beta;
-        if (run.status) run.status[sid] = sh.status;
-        if (run.steps) run.steps[sid] = sh.steps;
-        if (run.cycles) run.cycles[sid] = sh.cycles;
-        atomicAdd(&a.summary[0], (unsigned long long)sh.steps);
-        const int k = sh.status + 6;  // status codes -6..2 -> 0..8
-        if (k >= 0 && k < 9) atomicAdd(&a.summary[1 + k], 1ull);
-    }
-    __syncthreads();
 }
 
 // The persistent batched solver: CTAs take systems from the queue until it is empty.
@@ -685,16 +121,12 @@ template <int T, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_batch_solve(Args a, const Run *__restrict__ runp)
 {
     extern __shared__ __align__(16) double sm[];
-    __shared__ Shared sh;
+    __shared__ sysdev::Shared sh;
     __shared__ Run run;
     __shared__ int s_next;
     if (threadIdx.x == 0) {
         run = *runp;
-        // Single-warp steps go to warp (hardware warp slot / 4) mod warps: CTAs that share an
-        // SM then put them on different SM sub-partitions.  Any choice gives the same results.
-        unsigned wid;
-        asm volatile("mov.u32 %0, %%warpid;" : "=r"(wid));
-        sh.swarp = (int)((wid >> 2) % (blockDim.x >> 5));
+        sysdev::init_shared(sh);
     }
     const SmemLayout L = smem_layout(a.nmax, a.m);
     double *V = a.vslots + (int64_t)blockIdx.x * a.slot_stride;
@@ -704,7 +136,24 @@ __global__ void __launch_bounds__(T, MINB) k_batch_solve(Args a, const Run *__re
         const int q = s_next;
         __syncthreads();
         if (q >= run.count) break;
-        b_solve_system(a, run, run.order[q], V, sm, L, sh);
+        const int sid = run.order[q];
+        const sysdev::SysArgs<double> sa = sys_args(a, run, sid, V);
+        sysdev::Gang gg;
+        gg.G = 1;
+        gg.g = 0;
+        gg.lo = 0;
+        gg.hi = round_up(sa.n, 2);
+        gg.sync = nullptr;
+        gg.gpart = nullptr;
+        gg.gld = 0;
+        gg.R = V + a.r_offset;
+        sysdev::d_solve<double>(sa, gg, sm, L, sh);
+        if (threadIdx.x == 0) {
+            atomicAdd(&a.summary[0], (unsigned long long)sh.steps);
+            const int k = sh.status + 6;  // status codes -6..2 -> 0..8
+            if (k >= 0 && k < 9) atomicAdd(&a.summary[1 + k], 1ull);
+        }
+        __syncthreads();
     }
 }
 
@@ -716,23 +165,30 @@ __global__ void __launch_bounds__(256) k_batch_norm2(Args a, const int64_t *__re
                                                      int iters, double *__restrict__ out)
 {
     extern __shared__ __align__(16) double sm[];
+    __shared__ sysdev::Shared sh;
     __shared__ double s_lam;
+    if (threadIdx.x == 0) sysdev::init_shared(sh);
+    __syncthreads();
     const SmemLayout L = smem_layout(a.nmax, a.m);
     double *V = a.vslots + (int64_t)blockIdx.x * a.slot_stride;
-    Args at = a;  // A^T in the same SELL form and slicing
-    at.sell_off = at_off;
-    at.sell_col = at_col;
-    at.sell_val = at_val;
     for (int sid = blockIdx.x; sid < count; sid += gridDim.x) {
-        Sys S;
-        S.row0 = a.sys_row0[sid];
-        S.n = (int)(a.sys_row0[sid + 1] - S.row0);
-        S.n2 = round_up(S.n, 2);
-        S.ldv = round_up(S.n, 4);
-        S.slice0 = a.sys_slice0[sid];
-        double *xv = V, *yv = V + S.ldv, *uv = V + 2 * (int64_t)S.ldv;
-        const double sc = 1.0 / sqrt((double)S.n);
-        for (int i = threadIdx.x; i < S.n; i += blockDim.x) {
+        const int64_t row0 = a.sys_row0[sid];
+        const int n = (int)(a.sys_row0[sid + 1] - row0);
+        const int ldv = round_up(n, 4);
+        sysdev::SysArgs<double> sa{}, st{};
+        sa.n = st.n = n;
+        sa.sell_off = a.sell_off + a.sys_slice0[sid];
+        sa.sell_col = a.sell_col;
+        sa.sell_val = a.sell_val;
+        st.sell_off = at_off + a.sys_slice0[sid];
+        st.sell_col = at_col;
+        st.sell_val = at_val;
+        sysdev::Gang gg{};
+        gg.G = 1;
+        gg.hi = round_up(n, 2);
+        double *xv = V, *yv = V + ldv, *uv = V + 2 * (int64_t)ldv;
+        const double sc = 1.0 / sqrt((double)n);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
             uint64_t hsh = (uint64_t)i * 0x9E3779B97F4A7C15ull;
             hsh ^= hsh >> 29;
             xv[i] = sc * (0.5 + (double)(hsh >> 11) * 0x1p-53);
@@ -740,16 +196,16 @@ __global__ void __launch_bounds__(256) k_batch_norm2(Args a, const int64_t *__re
         __syncthreads();
         double lam = 0.0;
         for (int it = 0; it < iters; ++it) {
-            b_spmv<false>(a, S, xv, nullptr, yv);
+            sysdev::d_spmv<double, double, double, double, false>(sa, gg, sa.sell_val, xv, nullptr, yv);
             __syncthreads();
-            b_spmv<false>(at, S, yv, nullptr, uv);
+            sysdev::d_spmv<double, double, double, double, false>(st, gg, st.sell_val, yv, nullptr, uv);
             __syncthreads();
-            b_sumsq(S, uv, nullptr, 1, sm + L.part, sm + L.red);
+            sysdev::d_sumsq<double, double>(gg, sh, n, uv, (const double *)nullptr, 1, sm + L.part, sm + L.red);
             if (threadIdx.x == 0) s_lam = sqrt(sm[L.red]);
             __syncthreads();
             lam = s_lam;
             const double f = lam > 0.0 ? 1.0 / lam : 0.0;
-            for (int i = threadIdx.x; i < S.n; i += blockDim.x) xv[i] = uv[i] * f;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) xv[i] = uv[i] * f;
             __syncthreads();
         }
         if (threadIdx.x == 0) out[sid] = sqrt(lam);

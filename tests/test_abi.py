@@ -38,6 +38,31 @@ def test_exports_every_declared_batch_function(lib):
         assert hasattr(lib, name), name
 
 
+def test_exports_every_declared_serve_function(lib):
+    hdr = open(os.path.join(ROOT, "include", "igs_serve.h")).read()
+    declared = set(re.findall(r"\b(igs_server_[a-z0-9_]+)\s*\(", hdr))
+    assert declared, "no declarations parsed"
+    import paper_2205_07805_gb300 as pkg
+    assert declared == set(pkg.EXPORTED_SERVE_SYMBOLS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_server_rejects_bad_options_before_touching_the_device(lib):
+    import paper_2205_07805_gb300 as pkg
+    h = C.c_void_p()
+    for opts in [(0, 0, 1 << 20, 0, 0, 0), (0, 200, 1 << 20, 0, 0, 0), (0, 50, 0, 0, 0, 0),
+                 (0, 50, 1 << 20, 65, 0, 0), (0, 50, 1 << 20, 0, 100, 0)]:
+        o = pkg._ServerOpts(*opts)
+        assert lib.igs_server_create(C.byref(h), C.byref(o)) == -1 and not h.value
+    assert lib.igs_server_create(None, None) == -1
+    lib.igs_server_destroy(None)
+    assert lib.igs_server_submit(None, None, None) == -1
+    assert lib.igs_server_pump(None, None) == -1
+    assert lib.igs_server_get_stats(None, None) == -1
+    assert lib.igs_server_last_error(None)
+
+
 def test_status_strings(lib):
     for code in (0, 1, 2, -1, -2, -3, -4, -5, -6):
         assert lib.igs_status_string(code)

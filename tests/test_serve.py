@@ -1,0 +1,122 @@
+"""Request server (include/igs_serve.h): each request against the CPU oracle, gangs of several
+CTAs, the same result alone and in a mix, admission by device memory, the queue limit.
+
+Tolerances as in the batched and precision forms: converged FP64 requests have the oracle's
+status, step counts within +-2 and x within 1e-8 (relative); FP32-IR requests reach
+beta <= tol with x within 1e-10 of the oracle's FP64 solution at tol = 1e-14.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2205_07805_gb300 as pkg
+    from paper_2205_07805_gb300 import build
+    build.build()
+    pkg.load_library()
+    return pkg
+
+
+def _cases():
+    out = []
+    for i, (side, pe) in enumerate([(20, 1.0), (33, 40.0), (48, 90.0), (63, 10.0)]):
+        A, b, _, _ = gen.cd2d(side, pe, seed=30 + i)
+        out.append((A, b))
+    for A, b, _, _ in gen.banded_batch(count=3, nmin=300, nmax=3000, seed=31):
+        out.append((A, b))
+    return out
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("rows_per_cta", [4096, 256])
+def test_served_requests_match_oracle(pkg, rows_per_cta):
+    """rows_per_cta = 256 puts every request but the smallest on a gang of several CTAs."""
+    cases = _cases()
+    norms = [gen.norm2_power(A, iters=100) for A, _ in cases]
+    with pkg.Server(max_restart_m=40, arena_bytes=1 << 30, slots=3, rows_per_cta=rows_per_cta) as sv:
+        ids = [sv.submit(A, b, A_norm2=nA, m=40, gs=2, tol=1e-12, max_restarts=200)
+               for (A, b), nA in zip(cases, norms)]
+        done = {c["id"]: c for c in sv.run_all()}
+        for rid, (A, b), nA in zip(ids, cases, norms):
+            c = done[rid]
+            o = oracle.gmres(A, b, m=40, gs=2, tol=1e-12, max_cycles=200, normA=nA)
+            x = sv.take(rid)
+            assert c["status"] == o["status"] == 0, (c, o["status"])
+            assert abs(c["steps"] - o["steps"]) <= 2, (c["steps"], o["steps"])
+            err = np.linalg.norm(x - o["x"]) / np.linalg.norm(o["x"])
+            assert err <= 1e-8, (A.n, c["gang_ctas"], err)
+            if rows_per_cta == 256 and A.n > 512:
+                assert c["gang_ctas"] > 1
+
+
+@pytest.mark.gpu
+def test_served_fp32_ir_requests(pkg):
+    cases = _cases()[:3]
+    norms = [gen.norm2_power(A, iters=100) for A, _ in cases]
+    with pkg.Server(max_restart_m=60, arena_bytes=1 << 30, slots=3, rows_per_cta=512) as sv:
+        ids = [sv.submit(A, b, A_norm2=nA, m=60, gs=2, tol=1e-14, max_restarts=100, precision="fp32_ir")
+               for (A, b), nA in zip(cases, norms)]
+        done = {c["id"]: c for c in sv.run_all()}
+        for rid, (A, b), nA in zip(ids, cases, norms):
+            o = oracle.gmres(A, b, m=60, gs=2, tol=1e-14, max_cycles=100, normA=nA)
+            x = sv.take(rid)
+            assert done[rid]["status"] == 0 and done[rid]["beta"] <= 1e-14
+            assert np.linalg.norm(x - o["x"]) <= 1e-10 * np.linalg.norm(o["x"])
+
+
+@pytest.mark.gpu
+def test_same_result_alone_and_in_a_mix(pkg):
+    A, b, _, _ = gen.cd2d(70, 30.0, seed=40)             # n = 4900: a gang of 10 at 512 rows
+    nA = gen.norm2_power(A, iters=60)
+    others = _cases()
+    with pkg.Server(max_restart_m=50, arena_bytes=1 << 30, slots=1, rows_per_cta=512) as sv:
+        rid = sv.submit(A, b, A_norm2=nA, m=50, tol=1e-12, max_restarts=100)
+        alone = {c["id"]: c for c in sv.run_all()}[rid]
+        x_alone = sv.take(rid)
+    with pkg.Server(max_restart_m=50, arena_bytes=1 << 30, slots=4, rows_per_cta=512) as sv:
+        ids = []
+        for i, (Ao, bo) in enumerate(others):
+            ids.append(sv.submit(Ao, bo, m=50, tol=1e-10 if i % 2 else 1e-12, max_restarts=100,
+                                 precision="fp32_ir" if i % 3 == 0 else "fp64"))
+            if i == 3:
+                rid = sv.submit(A, b, A_norm2=nA, m=50, tol=1e-12, max_restarts=100)
+            sv.pump()
+        mixed = {c["id"]: c for c in sv.run_all()}[rid]
+        x_mix = sv.take(rid)
+    assert np.array_equal(x_alone, x_mix)
+    assert alone["steps"] == mixed["steps"] and alone["beta"] == mixed["beta"]
+    assert alone["gang_ctas"] == mixed["gang_ctas"] > 1
+
+
+@pytest.mark.gpu
+def test_admission_by_device_memory_and_queue_limit(pkg):
+    cases = _cases()[:4]
+    # an arena that holds the largest request but not two of them
+    with pkg.Server(max_restart_m=40, arena_bytes=1 << 30, slots=4) as probe:
+        rid = probe.submit(*cases[3], m=40)
+        need = max(c["device_bytes"] for c in probe.run_all())
+    with pkg.Server(max_restart_m=40, arena_bytes=int(need * 1.5), slots=4, max_queue=3) as sv:
+        ids = [sv.submit(A, b, m=40, tol=1e-12, max_restarts=100) for A, b in cases[:3]]
+        assert all(i is not None for i in ids)
+        assert sv.submit(*cases[3], m=40) is None             # the queue is full
+        done = sv.run_all()
+        st = sv.stats()
+        assert st["arena_peak"] <= st["arena_bytes"]
+        assert len(done) == 3 and all(c["status"] == 0 for c in done)
+
+
+@pytest.mark.gpu
+def test_numeric_error_is_isolated(pkg):
+    cases = _cases()[:3]
+    with pkg.Server(max_restart_m=40, arena_bytes=1 << 30, slots=3, rows_per_cta=512) as sv:
+        bad = cases[1][1].copy()
+        bad[5] = np.nan
+        ids = [sv.submit(cases[0][0], cases[0][1], m=40), sv.submit(cases[1][0], bad, m=40),
+               sv.submit(cases[2][0], cases[2][1], m=40)]
+        done = {c["id"]: c for c in sv.run_all()}
+    assert done[ids[1]]["status"] == pkg.ENUMERIC
+    assert done[ids[0]]["status"] == 0 and done[ids[2]]["status"] == 0

@@ -24,7 +24,7 @@ _LIB_PATH = os.path.join(_OUT_DIR, "libigs_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MGS, IGS = 0, 1
+MGS, IGS, ONE_REDUCE = 0, 1, 2  # MGS-GMRES, Alg. 4.1, Alg. 4.2
 OK, NOT_CONVERGED, BREAKDOWN, EINVAL, ENOMEM, ENUMERIC = 0, 1, 2, -1, -2, -4
 
 _P = np.ctypeslib.ndpointer

@@ -26,7 +26,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORA_MGS = 0, ORA_IGS = 1 };
+enum { ORA_MGS = 0, ORA_IGS = 1, ORA_ONE_REDUCE = 2 };
 enum { ORA_OK = 0, ORA_NOT_CONVERGED = 1, ORA_BREAKDOWN = 2, ORA_EINVAL = -1, ORA_ENOMEM = -2,
        ORA_ENUMERIC = -4 };
 
@@ -345,6 +345,122 @@ out:
     return done;
 }
 
+/* Alg. 4.2 ("Low-Synch One-Reduce hybrid MGS-CGS GMRES"), one cycle, one global reduction
+ * per column.  The vector entering iteration k is u_{k-1}, the output of the previous
+ * iteration's single projection (step 13), not yet re-orthogonalised; the reduction of step 4
+ * gives r^(2) = V_{k-2}^T u_{k-1}, ||u_{k-1}||^2, r^(0) = V_{k-2}^T A u_{k-1} and
+ * u_{k-1}^T A u_{k-1}.
+ *
+ * Readings where the printed algorithm is garbled or silent:
+ *  - Step 2: u_2 = w_2 - v_1 H_{1,1} (the printed division by H_{1,1} is taken as a typo).
+ *  - Hessenberg columns are completed one iteration late: column k-2 (1-based) gets
+ *    H_{1:k-2,k-2} = q + r^(3) (step 14) and H_{k-1,k-2} = gamma_{k-1}, where q is the
+ *    first-projection coefficient vector of the previous iteration (step 15).
+ *  - Step 15 is q = r^(1) - H_{1:k-1,1:k-2} r^(3) / gamma_{k-1}: the derivation (eq. "Aw":
+ *    A w_{k-1} = A u_{k-1} - V_{k-1} H r^(2), and step 13 subtracting V r^(1)) fixes r^(1)
+ *    and the 1/gamma that the printed step 15 (r^(0), r^(3)) leaves out; r^(3) replaces r^(2)
+ *    there as it does in step 14.
+ *  - Step 10 uses r^(2) (Jacobi) and step 14 uses r^(3) = (I + L)^{-1} r^(2), as printed.
+ *  - L's new row (step 9) is r^(2) / gamma = u_{k-1}^T V_{k-2} / gamma, as printed (not
+ *    v^T V as in Alg. 4.1).
+ *  - gamma (step 6, the lagged norm) = sqrt(||u||^2 - ||r^(2)||^2); a non-positive argument
+ *    is a breakdown (gamma = 0).
+ *  - The cycle builds m columns from m products with A (step 2 and k = 3..m+1) and a flush
+ *    re-orthogonalises u_{m+1} (one more reduction, no product) to set column m.
+ */
+static int one_reduce_cycle(int64_t n, const int64_t *rp, const int32_t *ci, const double *va,
+                            const double *r0, int m, double *V, double *H, double *L, double rho,
+                            givens_ls *G, cycle_ctl *ctl, int *status)
+{
+    const int ldh = m + 1, ldl = m + 1;
+    double *z = (double *)malloc((size_t)n * sizeof(double));
+    double *u = (double *)malloc((size_t)n * sizeof(double));
+    double *zs = (double *)malloc((size_t)n * sizeof(double));
+    double *r1 = (double *)calloc((size_t)m + 2, sizeof(double));
+    double *r2 = (double *)calloc((size_t)m + 2, sizeof(double));
+    double *r3 = (double *)calloc((size_t)m + 2, sizeof(double));
+    double *s0 = (double *)calloc((size_t)m + 2, sizeof(double));
+    double *q = (double *)calloc((size_t)m + 2, sizeof(double));
+    int done = 0, stopped = 0;
+    if (!z || !u || !zs || !r1 || !r2 || !r3 || !s0 || !q) { *status = ORA_ENOMEM; goto out; }
+
+    /* Step 1: v_1 = r_0 / rho. */
+    for (int64_t i = 0; i < n; ++i) V[i] = r0[i] / rho;
+    /* Step 2: w_2 = A v_1, H_11 = v_1^T w_2, u_2 = w_2 - v_1 H_11; H_11 is the first entry of
+     * column 1's first-projection coefficients q. */
+    {
+        ora_spmv(n, rp, ci, va, V, z);
+        const double h11 = ora_dot(n, V, z);
+        for (int64_t i = 0; i < n; ++i) u[i] = z[i] - V[i] * h11;
+        q[0] = h11;
+    }
+    for (int k = 3; k <= m + 2; ++k) {
+        const int nb = k - 2;            /* normalised columns v_1..v_{k-2} */
+        const int flush = k == m + 2;    /* last: re-orthogonalise u_{m+1} only */
+        /* Step 4, the one global reduction. */
+        if (!flush) ora_spmv(n, rp, ci, va, u, z);
+        for (int c = 0; c < nb; ++c) r2[c] = ora_dot(n, V + (int64_t)c * n, u);
+        const double uu = ora_dot(n, u, u);
+        double t = 0.0;
+        if (!flush) {
+            for (int c = 0; c < nb; ++c) s0[c] = ora_dot(n, V + (int64_t)c * n, z);
+            t = ora_dot(n, u, z);
+        }
+        /* Step 5: r^(3) = (I + L_{k-2})^{-1} r^(2) (normal equations). */
+        unit_lower_solve(nb, L, ldl, r2, r3);
+        /* Step 6: the lagged norm. */
+        double rr = 0.0;
+        for (int c = 0; c < nb; ++c) rr += r2[c] * r2[c];
+        const double g2 = uu - rr;
+        const double gamma = g2 > 0.0 ? sqrt(g2) : (g2 == g2 ? 0.0 : g2);
+        /* Step 14: column k-2 (1-based) complete. */
+        for (int c = 0; c < nb; ++c) H[(int64_t)(nb - 1) * ldh + c] = q[c] + r3[c];
+        H[(int64_t)(nb - 1) * ldh + nb] = gamma;
+        if (!isfinite(gamma)) { *status = ORA_ENUMERIC; break; }
+        {
+            double res = givens_add_column(G, H, nb - 1);
+            record(ctl, nb - 1, res, lower_fro(L, ldl, nb));
+            done = nb;
+            if (is_breakdown(H, ldh, nb - 1, gamma)) { *status = ORA_BREAKDOWN; break; }
+            if (converged(ctl, res)) { stopped = 1; break; }
+        }
+        /* Steps 9-11 (also at the flush, so that a cycle returns m+1 basis vectors and
+         * m+1 rows of L): L row = r^(2) / gamma, v_{k-1} = (u_{k-1} - V_{k-2} r^(2)) / gamma. */
+        for (int c = 0; c < nb; ++c) L[(int64_t)nb * ldl + c] = r2[c] / gamma;
+        {
+            double *vnew = V + (int64_t)nb * n;
+            project_out(n, nb, V, r2, u, vnew);
+            for (int64_t i = 0; i < n; ++i) vnew[i] = vnew[i] / gamma;
+        }
+        if (flush) break;
+        /* Steps 7-8: r^(0) / gamma, its last entry once more. */
+        for (int c = 0; c < nb; ++c) s0[c] = s0[c] / gamma;
+        t = t / gamma / gamma;
+        /* (Steps 10-11, w_{k-1} = u_{k-1} - V_{k-2} r^(2) (Jacobi) and v_{k-1} = w_{k-1} / gamma,
+         * are above.)  Step 12: r^(1) = [I 0; -L_{k-1,1:k-2} 1] r^(0) (the last entry by
+         * "Stephen's trick"). */
+        for (int c = 0; c < nb; ++c) r1[c] = s0[c];
+        {
+            double lr = 0.0;
+            for (int c = 0; c < nb; ++c) lr += L[(int64_t)nb * ldl + c] * s0[c];
+            r1[nb] = t - lr;
+        }
+        /* Step 13: u_k = A u_{k-1} / gamma - V_{k-1} r^(1). */
+        for (int64_t i = 0; i < n; ++i) zs[i] = z[i] / gamma;
+        project_out(n, nb + 1, V, r1, zs, u);
+        /* Step 15: first-projection coefficients of column k-1: q = r^(1) - H r^(3) / gamma. */
+        for (int i = 0; i <= nb; ++i) {
+            double hs = 0.0;
+            for (int c = 0; c < nb; ++c) hs += H[(int64_t)c * ldh + i] * (r3[c] / gamma);
+            q[i] = r1[i] - hs;
+        }
+    }
+    (void)stopped;
+out:
+    free(z); free(u); free(zs); free(r1); free(r2); free(r3); free(s0); free(q);
+    return done;
+}
+
 /* Public: one Arnoldi cycle on r0 (no in-cycle stop).  V, H, L as described at the top
  * (caller-allocated, zero-filled by this routine).  Returns the number of completed
  * columns; *rho_out = ||r0||; *status_out per the ORA_* codes. */
@@ -353,7 +469,8 @@ int ora_arnoldi(int64_t n, const int64_t *rp, const int32_t *ci, const double *v
                 double *rho_out, int *status_out)
 {
     int status = ORA_OK;
-    if (n <= 0 || m < 1 || (method != ORA_MGS && method != ORA_IGS) || gs < 1 || gs > 2) {
+    if (n <= 0 || m < 1 || (method != ORA_MGS && method != ORA_IGS && method != ORA_ONE_REDUCE) || gs < 1 ||
+        gs > 2) {
         *status_out = ORA_EINVAL;
         return 0;
     }
@@ -368,9 +485,11 @@ int ora_arnoldi(int64_t n, const int64_t *rp, const int32_t *ci, const double *v
     }
     givens_ls G;
     if (givens_init(&G, m, rho) != ORA_OK) { givens_free(&G); *status_out = ORA_ENOMEM; return 0; }
-    int done = method == ORA_MGS ? mgs_cycle(n, rp, ci, va, r0, m, V, H, rho, &G, NULL, &status)
-                                 : igs_cycle(n, rp, ci, va, r0, m, gs, V, H, L, rho, &G, NULL,
-                                             &status);
+    int done = method == ORA_MGS
+                   ? mgs_cycle(n, rp, ci, va, r0, m, V, H, rho, &G, NULL, &status)
+                   : method == ORA_IGS
+                         ? igs_cycle(n, rp, ci, va, r0, m, gs, V, H, L, rho, &G, NULL, &status)
+                         : one_reduce_cycle(n, rp, ci, va, r0, m, V, H, L, rho, &G, NULL, &status);
     givens_free(&G);
     *status_out = status;
     return done;
@@ -414,8 +533,8 @@ int ora_gmres(int64_t n, const int64_t *rp, const int32_t *ci, const double *va,
               double *hist_lfro, int64_t *hist_len, double *beta_out, int *cycles_out,
               int64_t *steps_out)
 {
-    if (n <= 0 || m < 1 || (method != ORA_MGS && method != ORA_IGS) || gs < 1 || gs > 2 ||
-        max_cycles < 1)
+    if (n <= 0 || m < 1 || (method != ORA_MGS && method != ORA_IGS && method != ORA_ONE_REDUCE) || gs < 1 ||
+        gs > 2 || max_cycles < 1)
         return ORA_EINVAL;
     double *V = (double *)malloc((size_t)n * (m + 1) * sizeof(double));
     double *H = (double *)malloc((size_t)(m + 1) * m * sizeof(double));
@@ -457,7 +576,9 @@ int ora_gmres(int64_t n, const int64_t *rp, const int32_t *ci, const double *va,
         int cst = ORA_OK;
         int done = method == ORA_MGS
                        ? mgs_cycle(n, rp, ci, va, r, m, V, H, rho, &G, &ctl, &cst)
-                       : igs_cycle(n, rp, ci, va, r, m, gs, V, H, L, rho, &G, &ctl, &cst);
+                       : method == ORA_IGS
+                             ? igs_cycle(n, rp, ci, va, r, m, gs, V, H, L, rho, &G, &ctl, &cst)
+                             : one_reduce_cycle(n, rp, ci, va, r, m, V, H, L, rho, &G, &ctl, &cst);
         int64_t room = hist_cap - hlen;
         hlen += done < room ? done : (room > 0 ? room : 0);
         steps += done;

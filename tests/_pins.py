@@ -247,6 +247,95 @@ def pin_mgs_equals_igs1_early(impl=None):
     return k >= 3 and err <= 1e-12, f"{k} columns with kappa(B) < 1e4: rel diff {err:.3g}"
 
 
+# --------------------------------------------------------------------------------------
+# Alg. 4.2 (one-reduce hybrid MGS-CGS GMRES).  The paper states no theory for it (Sec. 4:
+# stability analysis is future work) but reports that its results are comparable to
+# Alg. 4.1's: O(eps) orthogonality, sigma_min(V_k) near one, and subdiagonals from the lagged
+# norm agreeing closely with Alg. 4.1's (Sec. 5, Sec. 6).  The pins below fix exactly that,
+# plus what holds for any Arnoldi process: the Arnoldi relation, H unique against the
+# Krylov QR, and k = n exactness.
+
+def pin_one_reduce_arnoldi_and_krylov(impl=None):
+    """Alg. 4.2: A V_k = V_{k+1} H to 1e-13 relative, and H / V against LAPACK's QR of the
+    Krylov matrix (H is unique) to 1e-9."""
+    worst = 0.0
+    for A, m in ((scaled_random(40, 1), 20), (gen.dense_usv(60, 2, 1e-8)[0], 60)):
+        r0 = np.random.default_rng(7).standard_normal(A.n)
+        out = oracle.arnoldi(A, r0, m, oracle.ONE_REDUCE, 2, impl=impl)
+        if out["ncols"] != m:
+            return False, f"only {out['ncols']} of {m} columns"
+        worst = max(worst, arnoldi_relation(A, out))
+    A = scaled_random(30, 3)
+    D = csr_to_dense(A)
+    r0 = np.random.default_rng(5).standard_normal(30)
+    k = 6
+    K = np.column_stack([np.linalg.matrix_power(D, i) @ r0 for i in range(k + 1)])
+    Q, R = np.linalg.qr(K)
+    Q = Q * np.sign(np.diag(R))[None, :]
+    Href = Q.T @ D @ Q[:, :k]
+    out = oracle.arnoldi(A, r0, k, oracle.ONE_REDUCE, 2, impl=impl)
+    qr = max(np.linalg.norm(out["H"][:k + 1, :k] - Href) / np.linalg.norm(Href),
+             np.linalg.norm(out["V"][:, :k + 1] - Q))
+    return worst <= 1e-13 and qr <= 1e-9, f"Arnoldi relation {worst:.3g}, vs Krylov QR {qr:.3g}"
+
+
+def pin_one_reduce_orthogonality(impl=None):
+    """Alg. 4.2 keeps ||I - V_k^T V_k||_F at O(eps) and sigma_min(V_k) near one (the paper's
+    observation for all its examples) at kappa(A) = 1e10, k = n = 200: thresholds of the
+    two-iteration Alg. 4.1 pin."""
+    A, b, _, _ = gen.dense_usv(200, 0)
+    out = oracle.arnoldi(A, b, 200, oracle.ONE_REDUCE, 2, impl=impl)
+    loss = orth_loss(out["V"], 200)
+    smin = np.linalg.svd(out["V"][:, :200], compute_uv=False)[-1]
+    return loss <= 1e-13 and smin >= 1 - 1e-12, f"||I-V^TV||_F {loss:.3g}, sigma_min {smin:.16f}"
+
+
+def pin_one_reduce_matches_two_reduce(impl=None):
+    """The lagged-norm subdiagonals and the H columns of Alg. 4.2 agree with Alg. 4.1's (two
+    GS iterations) to 1e-10 relative while kappa(B_k) < 1e6 (the paper: results comparable,
+    R_kk from the lagged norm agree closely)."""
+    worst, cols = 0.0, 0
+    for A in (scaled_random(50, 10), gen.dense_usv(80, 4, 1e-8)[0]):
+        D = csr_to_dense(A)
+        r0 = np.random.default_rng(10).standard_normal(A.n)
+        a = oracle.arnoldi(A, r0, 40, oracle.ONE_REDUCE, 2, impl=impl)
+        b = oracle.arnoldi(A, r0, 40, oracle.IGS, 2, impl=impl)
+        for j in range(min(a["ncols"], b["ncols"])):
+            if np.linalg.cond(np.column_stack([r0, D @ b["V"][:, :j + 1]])) >= 1e6:
+                break
+            hb = b["H"][:j + 2, j]
+            worst = max(worst, np.linalg.norm(a["H"][:j + 2, j] - hb) / np.linalg.norm(hb),
+                        abs(a["H"][j + 1, j] - hb[j + 1]) / abs(hb[j + 1]))
+            cols += 1
+    return cols >= 20 and worst <= 1e-10, f"{cols} columns compared, worst rel diff {worst:.3g}"
+
+
+def pin_one_reduce_solves(impl=None):
+    """Alg. 4.2 GMRES: k = n returns A^{-1} b (LAPACK) with beta at the rounding level; on the
+    Simoncini-Szyld example its Arnoldi residual keeps decreasing far below eps like
+    Alg. 4.1's (no MGS-type stagnation)."""
+    rng = np.random.default_rng(12)
+    n = 40
+    U = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    W = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    D = 11.0 * (U * np.linspace(1, 10, n)[None, :]) @ W.T
+    A = csr_from_dense(D)
+    b = rng.standard_normal(n)
+    out = oracle.gmres(A, b, m=n, method=oracle.ONE_REDUCE, tol=0.0, max_cycles=1,
+                       normA=float(np.linalg.norm(D, 2)), impl=impl)
+    err = np.linalg.norm(out["x"] - np.linalg.solve(D, b)) / np.linalg.norm(np.linalg.solve(D, b))
+    g = GOLDEN["simoncini"]
+    As, bs, _, _ = gen.simoncini(0)
+    sm = oracle.gmres(As, bs, m=100, method=oracle.ONE_REDUCE, tol=0.0, max_cycles=1, normA=g["normA"],
+                      impl=impl)
+    smin = (sm["hist_res"] / np.linalg.norm(bs)).min()
+    ok = err <= 1e-12 and out["beta"] <= 1e-15 and smin <= 1e-15
+    return ok, f"k=n x err {err:.2g}, beta {out['beta']:.2g}; Simoncini min res {smin:.2g}"
+
+
+ONE_REDUCE_PINS = [pin_one_reduce_arnoldi_and_krylov, pin_one_reduce_orthogonality,
+                   pin_one_reduce_matches_two_reduce, pin_one_reduce_solves]
+
 ALL_PINS = [pin_spmv, pin_arnoldi_relation, pin_krylov_qr, pin_L_is_gram, pin_orthogonality_two_gs,
             pin_orthogonality_one_gs, pin_givens_lstsq, pin_kn_exact, pin_backward_error_closed_forms,
-            pin_simoncini, pin_walker, pin_embree, pin_mgs_equals_igs1_early]
+            pin_simoncini, pin_walker, pin_embree, pin_mgs_equals_igs1_early] + ONE_REDUCE_PINS

@@ -7,7 +7,10 @@ flipping the sign of r^(3) in the Hessenberg column (step 17) and dropping the (
 on r^(2) (step 15).  r^(3) is the second Gauss-Seidel correction; its size is the first
 pass's loss of orthogonality times ||u_k||, which is O(eps) ||H_{:,k-1}|| (Sec. 3), and
 with two iterations L itself is O(eps), so both edits move H by O(eps) only (measured:
-the Arnoldi-relation residual goes from ~1e-16 to ~5e-16)."""
+the Arnoldi-relation residual goes from ~1e-16 to ~5e-16).  For the same reason three
+edits of Alg. 4.2 are absent: the lagged norm without ||r^(2)||^2 (step 6), step 14 without
+r^(3), and L transposed in step 5's solve; r^(2) = V^T u is the first projection's loss of
+orthogonality, so each of these moves results by second-order terms only."""
 import os
 
 import pytest
@@ -45,6 +48,18 @@ MUTANTS = [
      "for (int64_t i = 0; i < n; ++i) w2[i] -= h11 * V[i];", ""),
     ("backward error omits ||A|| ||x||",
      "rn / (ora_nrm2(n, b) + normA * ora_nrm2(n, x));", "rn / ora_nrm2(n, b);"),
+    # Alg. 4.2 (one-reduce)
+    ("Alg. 4.2 drops Stephen's trick (step 12)", "r1[nb] = t - lr;", "r1[nb] = t;"),
+    ("Alg. 4.2 step 8 divides u^T A u by gamma once", "t = t / gamma / gamma;", "t = t / gamma;"),
+    ("Alg. 4.2 without the Jacobi re-orthogonalisation (step 10)",
+     "project_out(n, nb, V, r2, u, vnew);", "for (int64_t i = 0; i < n; ++i) vnew[i] = u[i];"),
+    ("Alg. 4.2 step 15 adds H r^(3) / gamma", "q[i] = r1[i] - hs;", "q[i] = r1[i] + hs;"),
+    ("Alg. 4.2 step 13 without 1/gamma", "zs[i] = z[i] / gamma;", "zs[i] = z[i];"),
+    ("Alg. 4.2 L row not scaled (step 9)",
+     "L[(int64_t)nb * ldl + c] = r2[c] / gamma;", "L[(int64_t)nb * ldl + c] = r2[c];"),
+    ("Alg. 4.2 r^(0) not scaled (step 7)", "s0[c] = s0[c] / gamma;", "s0[c] = s0[c];"),
+    ("Alg. 4.2 step 15 with r^(2) and no 1/gamma",
+     "hs += H[(int64_t)c * ldh + i] * (r3[c] / gamma);", "hs += H[(int64_t)c * ldh + i] * r2[c];"),
 ]
 
 

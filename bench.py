@@ -17,7 +17,8 @@ GB300) with its HBM throughput alongside; `cpu_baseline` times the CPU oracle on
 cycle of the same workload.  With --gpus N > 1 (torchrun) every rank runs an independent
 replica (the method has no data-parallel exchange on one system): weak scaling.
 
-The line also carries `precision`: the FP32-basis form inside FP64 iterative refinement
+The line also carries `one_reduce`: Alg. 4.2 (one global reduction per column) on the same
+workload and cycles; `precision`: the FP32-basis form inside FP64 iterative refinement
 against the FP64 form on the 160^3 convection-diffusion system (n = 4.1M, m = 200) to
 beta <= 1e-14, with the FP32 multi-dot's HBM roofline; `served`: a Poisson stream of
 2-D convection-diffusion requests (2000/s, sides 64..1024) replayed against the request
@@ -726,6 +727,24 @@ def main():
         rate, dt = oracle_cycle_rate(A, b, M)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"one full cycle ({M} Arnoldi columns) of the same workload, {dt:.1f} s"}
+    # ---- Alg. 4.2 (one-reduce) on the same workload: the same K cycles, device-timed ----
+    def step_1r():
+        return solver.solve(b_dev, m=M, tol=0.0, max_restarts=1, x_out=x_dev, hist_cap=0, method="one_reduce")
+
+    for _ in range(args.warmup):
+        o1 = step_1r()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_1r()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    ms1, _, steps1 = reduce_replicas(ms1, 0.0, args.steps * o1["steps"], dist, "cuda")
+    line["one_reduce"] = {"metric": METRIC, "value": steps1 / (ms1 / 1e3), "unit": UNIT,
+                          "ms_per_step": ms1 / args.steps, "method": "Alg. 4.2 (one global reduction per column)",
+                          "speedup_vs_alg41_gs2": (steps1 / (ms1 / 1e3)) / value if args.gs == 2 else None}
     solver.close()
     if not args.no_precision:
         line["precision"] = run_precision(args, pkg, torch, local, dist)

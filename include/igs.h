@@ -45,7 +45,14 @@ enum {
 };
 
 /* Orthogonalisation method of an Arnoldi cycle. */
-enum { IGS_METHOD_IGS = 1 };
+/* Arnoldi process of a solve (igs_solve_opts.method, igs_arnoldi_ex). */
+enum {
+    IGS_METHOD_IGS = 1,        /* Alg. 4.1, two-reduce IGS with 1 or 2 Gauss-Seidel iterations  */
+    IGS_METHOD_ONE_REDUCE = 2  /* Alg. 4.2, one-reduce hybrid MGS-CGS: one global reduction per
+                                  column (lagged norm, Jacobi re-orthogonalisation of the lagged
+                                  vector, "Stephen's trick"); gs_iters is ignored.  The paper
+                                  leaves its stability analysis open (Sec. 4).                 */
+};
 
 typedef struct igs_ctx igs_ctx;
 
@@ -88,6 +95,8 @@ typedef struct {
                              created with fp32_basis); anything else: IGS_EINVAL            */
     double inner_tol;     /* IGS_PREC_FP32_IR: relative residual reduction per FP32 cycle;
                              <= 0: 1e-6.  Ignored for FP64                                   */
+    int method;           /* 0 or IGS_METHOD_IGS: Alg. 4.1; IGS_METHOD_ONE_REDUCE: Alg. 4.2
+                             (FP64 only)                                                     */
 } igs_solve_opts;
 
 /* Results of igs_solve.  Input fields are marked "in". */
@@ -159,6 +168,12 @@ int igs_arnoldi(igs_ctx *ctx, const double *r0, int m, int gs_iters, int on_devi
 
 /* y = A x with the context's matrix (n entries each; host or device per on_device). */
 int igs_spmv(igs_ctx *ctx, const double *x, double *y, int on_device);
+
+/* igs_arnoldi with the Arnoldi process chosen: method IGS_METHOD_IGS (Alg. 4.1, gs_iters 1
+ * or 2) or IGS_METHOD_ONE_REDUCE (Alg. 4.2; L then holds the rows u_{k-1}^T V_{k-2} / gamma of
+ * the lagged vectors, as the algorithm defines them).  Same arguments and results otherwise. */
+int igs_arnoldi_ex(igs_ctx *ctx, const double *r0, int m, int method, int gs_iters, int on_device,
+                   double *V, int64_t ldv, double *H, double *L, int *ncols, double *rho);
 
 /* Fill *info.  Returns IGS_OK or IGS_EINVAL. */
 int igs_get_info(const igs_ctx *ctx, igs_info *info);

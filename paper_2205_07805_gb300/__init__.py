@@ -26,7 +26,7 @@ KCLASS_NAMES = ["spmv", "dots", "update", "small", "cycle"]
 # Every function declared in include/igs.h.
 EXPORTED_SYMBOLS = ["igs_create", "igs_destroy", "igs_solve", "igs_arnoldi", "igs_spmv",
                     "igs_get_info", "igs_profile_enable", "igs_profile_get", "igs_launch_count",
-                    "igs_status_string", "igs_last_error", "igs_block_dots_static"]
+                    "igs_status_string", "igs_last_error", "igs_block_dots_static", "igs_arnoldi_ex"]
 # Every function declared in include/igs_batch.h.
 EXPORTED_BATCH_SYMBOLS = ["igs_batch_create", "igs_batch_destroy", "igs_batch_solve",
                           "igs_batch_set_config", "igs_batch_tune", "igs_batch_get_info",
@@ -57,10 +57,12 @@ class _CreateOpts(C.Structure):
 class _SolveOpts(C.Structure):
     _fields_ = [("restart_m", C.c_int), ("gs_iters", C.c_int), ("tol_beta", C.c_double),
                 ("max_restarts", C.c_int), ("inputs_on_device", C.c_int), ("precision", C.c_int),
-                ("inner_tol", C.c_double)]
+                ("inner_tol", C.c_double), ("method", C.c_int)]
 
 
 PRECISIONS = {"fp64": 0, "fp32_ir": 1}
+# Arnoldi processes: Alg. 4.1 (two-reduce IGS) and Alg. 4.2 (one-reduce hybrid MGS-CGS).
+METHODS = {"igs": 1, "one_reduce": 2}
 
 
 class _Result(C.Structure):
@@ -155,6 +157,8 @@ def load_library(path: str | None = None):
     lib.igs_solve.restype = i32
     lib.igs_arnoldi.argtypes = [vp, vp, i32, i32, i32, vp, i64, vp, vp, C.POINTER(i32), C.POINTER(dbl)]
     lib.igs_arnoldi.restype = i32
+    lib.igs_arnoldi_ex.argtypes = [vp, vp, i32, i32, i32, i32, vp, i64, vp, vp, C.POINTER(i32), C.POINTER(dbl)]
+    lib.igs_arnoldi_ex.restype = i32
     lib.igs_spmv.argtypes = [vp, vp, vp, i32]
     lib.igs_spmv.restype = i32
     lib.igs_get_info.argtypes = [vp, C.POINTER(_Info)]
@@ -294,7 +298,8 @@ class Solver:
     # ------------------------------------------------------------------------------
     def solve(self, b, x0=None, m: int = 30, gs: int = 2, tol: float = 1e-13,
               max_restarts: int = 10, x_out=None, hist_cap: int | None = None,
-              want_H: bool = False, precision: str = "fp64", inner_tol: float = 0.0) -> dict:
+              want_H: bool = False, precision: str = "fp64", inner_tol: float = 0.0,
+              method: str = "igs") -> dict:
         """Restarted IGS-GMRES(m) (``igs_solve``).  Returns ``dict(x, status, beta, rho0,
         steps, cycles, hist_res, hist_lfro[, H])``.  With a CUDA tensor ``b`` the inputs and
         ``x`` stay on the device.  ``precision="fp32_ir"`` runs the cycles on the FP32 basis
@@ -323,8 +328,10 @@ class Solver:
                       C.c_void_p(H.ctypes.data) if want_H else None, m + 1, 0.0, 0.0, 0, 0)
         if precision not in PRECISIONS:
             raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+        if method not in METHODS:
+            raise ValueError(f"method must be one of {sorted(METHODS)}")
         opts = _SolveOpts(int(m), int(gs), float(tol), int(max_restarts), 1 if dev else 0,
-                          PRECISIONS[precision], float(inner_tol))
+                          PRECISIONS[precision], float(inner_tol), METHODS[method])
         rc = self._lib.igs_solve(self._h, bp, xp, C.byref(opts), C.byref(res))
         if rc < 0:
             self._err(rc, "igs_solve")
@@ -335,7 +342,7 @@ class Solver:
             out["H"] = H
         return out
 
-    def arnoldi(self, r0, m: int, gs: int = 2, V=None, H=None, L=None) -> dict:
+    def arnoldi(self, r0, m: int, gs: int = 2, V=None, H=None, L=None, method: str = "igs") -> dict:
         """One Arnoldi cycle (``igs_arnoldi``).  Host input gives numpy outputs
         (V: n x (m+1), H: (m+1) x m, L: (m+1) x (m+1) row-major); a CUDA tensor input gives
         CUDA tensor outputs unless output tensors are passed."""
@@ -356,8 +363,11 @@ class Solver:
             vptr, hptr, lptr = V.ctypes.data, H.ctypes.data, L.ctypes.data
         ncols = C.c_int(0)
         rho = C.c_double(0.0)
-        rc = self._lib.igs_arnoldi(self._h, rp, int(m), int(gs), 1 if dev else 0, C.c_void_p(vptr),
-                                   self.n, C.c_void_p(hptr), C.c_void_p(lptr), C.byref(ncols), C.byref(rho))
+        if method not in METHODS:
+            raise ValueError(f"method must be one of {sorted(METHODS)}")
+        rc = self._lib.igs_arnoldi_ex(self._h, rp, int(m), METHODS[method], int(gs), 1 if dev else 0,
+                                      C.c_void_p(vptr), self.n, C.c_void_p(hptr), C.c_void_p(lptr),
+                                      C.byref(ncols), C.byref(rho))
         if rc < 0:
             self._err(rc, "igs_arnoldi")
         if dev:  # tensors were laid out column-major via transposed shapes

@@ -149,9 +149,12 @@ double upd_bytes(const igs::Workspace &w, int p) { return 8.0 * w.n * (p + 2); }
 // Enqueue one restart cycle (see the file comment).  Precondition: ctx->w.r = b - A x,
 // st->rnorm/xnorm/bnorm set (by the solve set-up or the previous cycle's end).
 cudaError_t enqueue_cycle32(igs_ctx *ctx, Issuer &is, int m, int gs);
+cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m);
 
+// gs = 0 selects Alg. 4.2 (one-reduce); 1 or 2 Alg. 4.1 with that many GS iterations.
 cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
 {
+    if (gs == 0) return enqueue_cycle_1r(ctx, is, m);
     if (prec == IGS_PREC_FP32_IR) return enqueue_cycle32(ctx, is, m, gs);
     const igs::Workspace &w = ctx->w;
     cudaStream_t s = is.s;
@@ -375,6 +378,95 @@ cudaError_t enqueue_cycle32(igs_ctx *ctx, Issuer &is, int m, int gs)
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_lsq(w, m, st_));
     RUN(igs::KC_CYCLE, 4.0 * w.n * m + 16.0 * w.n, 2.0 * w.n * m, s, igs::launch_xupdate32(w, st_));
     // r = b - A x, ||r||, ||x||, beta(x) in FP64.
+    RUN(igs::KC_CYCLE, spmv_bytes(w) + 8.0 * w.n, 2.0 * w.nnz, s, igs::launch_spmv(w, w.x, w.r, w.b, false, st_));
+    int nblk = 0;
+    RUN(igs::KC_CYCLE, 16.0 * w.n, 4.0 * w.n, s, igs::launch_norms(w, w.r, w.x, nullptr, &nblk, st_));
+    RUN(igs::KC_CYCLE, 0, 0, s, igs::launch_beta(w, nblk, st_));
+#undef RUN
+    return cudaSuccess;
+}
+
+// One cycle of Alg. 4.2 (one-reduce hybrid MGS-CGS GMRES; the readings are the oracle's).
+// Per column: the SpMV on u_{k-1} (held in V[:, nb]), the one reduction [V_nb, u]^T [u, A u]
+// (the step-5 multi-dot), the single-block step (r^(3), the lagged norm, column nb-1 of H,
+// L, Stephen's trick, q), and one fused pass over V_nb forming v_{k-1} and u_k.  The Givens
+// rotation of each completed column runs on a side branch as in Alg. 4.1.
+cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m)
+{
+    const igs::Workspace &w = ctx->w;
+    cudaStream_t s = is.s;
+    const int64_t ld = w.ld;
+    double *V = w.V;
+    auto col = [&](int c) { return V + (int64_t)c * ld; };
+    cudaError_t e;
+#define RUN(cls, bytes, flops, on, expr)                                          \
+    do {                                                                          \
+        e = is.run((cls), (bytes), (flops), [&](cudaStream_t st_) { (void)st_; return (expr); }, (on)); \
+        if (e != cudaSuccess) return e;                                           \
+    } while (0)
+    // Step 1: rho = ||r0||, v1 = r0 / rho.
+    RUN(igs::KC_CYCLE, 0, 0, s, igs::launch_cycle_start(w, 0, st_));
+    RUN(igs::KC_CYCLE, 16.0 * w.n, w.n, s, igs::launch_scale(w, w.r, col(0), 0, false, st_));
+    // Step 2: w2 = A v1, H11 = v1^T w2, u_2 = w2 - v1 H11 (into V[:, 1]).
+    igs::DotsPlan pl{};
+    RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, col(0), col(1), nullptr, false, st_));
+    RUN(igs::KC_DOTS, dots_bytes(w, 1, 1), 2.0 * w.n, s, igs::launch_dots(w, 1, col(1), nullptr, false, st_, &pl));
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_prime(w, pl, st_));
+    RUN(igs::KC_UPDATE, upd_bytes(w, 1), 2.0 * w.n, s,
+        igs::launch_update(w, 1, w.r1v, false, 1.0, col(1), col(1), false, false, false, st_));
+
+    bool pending_join = false;
+    auto join_side = [&]() -> cudaError_t {
+        if (pending_join && is.capture) {
+            cudaError_t ee = cudaStreamWaitEvent(s, ctx->ev_join, 0);
+            if (ee != cudaSuccess) return ee;
+        }
+        pending_join = false;
+        return cudaSuccess;
+    };
+    auto fork_givens = [&](int j) -> cudaError_t {
+        cudaStream_t on = s;
+        if (is.capture) {
+            cudaError_t ee = cudaEventRecord(ctx->ev_fork, s);
+            if (ee == cudaSuccess) ee = cudaStreamWaitEvent(is.side, ctx->ev_fork, 0);
+            if (ee != cudaSuccess) return ee;
+            on = is.side;
+        }
+        cudaError_t ee = is.run(igs::KC_SMALL, 0, 0, [&](cudaStream_t st_) { return igs::launch_givens(w, j, st_); }, on);
+        if (ee != cudaSuccess) return ee;
+        if (is.capture) {
+            ee = cudaEventRecord(ctx->ev_join, is.side);
+            if (ee != cudaSuccess) return ee;
+            pending_join = true;
+        }
+        return cudaSuccess;
+    };
+    for (int k = 3; k <= m + 1; ++k) {
+        const int nb = k - 2;
+        double *u = col(nb);
+        // Step 4: A u_{k-1}, then the one reduction [V_nb, u]^T [u, A u].
+        RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, u, w.z, nullptr, true, st_));
+        RUN(igs::KC_DOTS, dots_bytes(w, nb + 1, 2), 4.0 * w.n * (nb + 1), s,
+            igs::launch_dots(w, nb + 1, u, w.z, true, st_, &pl));
+        if ((e = join_side()) != cudaSuccess) return e;
+        // Steps 5-9, 12, 14, 15: column nb-1 complete; its Givens rotation on the side.
+        RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, nb, false, pl, st_));
+        if ((e = fork_givens(nb - 1)) != cudaSuccess) return e;
+        // Steps 10-11, 13: v_{k-1} and u_k in one pass.
+        RUN(igs::KC_UPDATE, 8.0 * w.n * (nb + 4), 4.0 * w.n * nb, s, igs::launch_update_1r(w, nb, w.z, false, st_));
+    }
+    // Flush: the reduction of u_{m+1} (no product), column m-1 complete, v_{m+1}.
+    RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
+        igs::launch_dots(w, m + 1, col(m), nullptr, true, st_, &pl));
+    if ((e = join_side()) != cudaSuccess) return e;
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, m, true, pl, st_));
+    RUN(igs::KC_UPDATE, 8.0 * w.n * (m + 2), 2.0 * w.n * m, s, igs::launch_update_1r(w, m, w.z, true, st_));
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));
+    // Least squares y = argmin ||rho e1 - H y||, x_m = x_0 + V_m y_m.
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_lsq(w, m, st_));
+    RUN(igs::KC_CYCLE, upd_bytes(w, m), 2.0 * w.n * m, s,
+        igs::launch_update(w, 0, w.y, true, 1.0, w.x, w.x, false, true, false, st_));
+    // r = b - A x, ||r||, ||x||, beta(x).
     RUN(igs::KC_CYCLE, spmv_bytes(w) + 8.0 * w.n, 2.0 * w.nnz, s, igs::launch_spmv(w, w.x, w.r, w.b, false, st_));
     int nblk = 0;
     RUN(igs::KC_CYCLE, 16.0 * w.n, 4.0 * w.n, s, igs::launch_norms(w, w.r, w.x, nullptr, &nblk, st_));
@@ -783,9 +875,15 @@ int igs_spmv(igs_ctx *ctx, const double *x, double *y, int on_device)
 int igs_solve(igs_ctx *ctx, const double *b, const double *x0, const igs_solve_opts *opts, igs_result *res)
 {
     if (!ctx || !b || !opts || !res || !res->x) return ctx ? fail(ctx, IGS_EINVAL, "null argument") : IGS_EINVAL;
-    const int m = opts->restart_m, gs = opts->gs_iters;
+    const int m = opts->restart_m;
+    const int method = opts->method == 0 ? IGS_METHOD_IGS : opts->method;
+    if (method != IGS_METHOD_IGS && method != IGS_METHOD_ONE_REDUCE) return fail(ctx, IGS_EINVAL, "unknown method");
     if (m < 1 || m > ctx->w.mmax) return fail(ctx, IGS_EINVAL, "restart_m %d outside [1, %d]", m, ctx->w.mmax);
-    if (gs != 1 && gs != 2) return fail(ctx, IGS_EINVAL, "gs_iters must be 1 or 2");
+    if (method == IGS_METHOD_IGS && opts->gs_iters != 1 && opts->gs_iters != 2)
+        return fail(ctx, IGS_EINVAL, "gs_iters must be 1 or 2");
+    if (method == IGS_METHOD_ONE_REDUCE && opts->precision != IGS_PREC_FP64)
+        return fail(ctx, IGS_EINVAL, "the one-reduce method runs in FP64 only");
+    const int gs = method == IGS_METHOD_ONE_REDUCE ? 0 : opts->gs_iters;  // 0: Alg. 4.2 cycle
     if (opts->max_restarts < 1) return fail(ctx, IGS_EINVAL, "max_restarts must be >= 1");
     if (!(opts->tol_beta >= 0.0)) return fail(ctx, IGS_EINVAL, "tol_beta must be >= 0");
     if (res->H && res->H_ld < m + 1) return fail(ctx, IGS_EINVAL, "H_ld < m+1");
@@ -857,9 +955,17 @@ int igs_solve(igs_ctx *ctx, const double *b, const double *x0, const igs_solve_o
 int igs_arnoldi(igs_ctx *ctx, const double *r0, int m, int gs, int on_device, double *V, int64_t ldv,
                 double *H, double *L, int *ncols, double *rho)
 {
+    return igs_arnoldi_ex(ctx, r0, m, IGS_METHOD_IGS, gs, on_device, V, ldv, H, L, ncols, rho);
+}
+
+int igs_arnoldi_ex(igs_ctx *ctx, const double *r0, int m, int method, int gs, int on_device, double *V,
+                   int64_t ldv, double *H, double *L, int *ncols, double *rho)
+{
     if (!ctx || !r0) return ctx ? fail(ctx, IGS_EINVAL, "null argument") : IGS_EINVAL;
     if (m < 1 || m > ctx->w.mmax) return fail(ctx, IGS_EINVAL, "m %d outside [1, %d]", m, ctx->w.mmax);
-    if (gs != 1 && gs != 2) return fail(ctx, IGS_EINVAL, "gs_iters must be 1 or 2");
+    if (method != IGS_METHOD_IGS && method != IGS_METHOD_ONE_REDUCE) return fail(ctx, IGS_EINVAL, "unknown method");
+    if (method == IGS_METHOD_IGS && gs != 1 && gs != 2) return fail(ctx, IGS_EINVAL, "gs_iters must be 1 or 2");
+    if (method == IGS_METHOD_ONE_REDUCE) gs = 0;  // the Alg. 4.2 cycle
     if (V && ldv < ctx->w.n) return fail(ctx, IGS_EINVAL, "ldv < n");
     CK(cudaSetDevice(ctx->device));
     igs::Workspace &w = ctx->w;

@@ -167,6 +167,10 @@ cudaError_t launch_step_a(const Workspace &w, int k, int gs, const DotsPlan &pl,
 cudaError_t launch_step_b(const Workspace &w, int k, const DotsPlan &pl, cudaStream_t s);
 cudaError_t launch_flush(const Workspace &w, int m, const DotsPlan &pl, cudaStream_t s);
 cudaError_t launch_givens(const Workspace &w, int j, cudaStream_t s);
+// Alg. 4.2 (one-reduce): the single-block step (nb normalised columns; flush: completion of
+// the last column only) and the fused basis update (v and the next u in one pass).
+cudaError_t launch_step_1r(const Workspace &w, int nb, bool flush, const DotsPlan &pl, cudaStream_t s);
+cudaError_t launch_update_1r(const Workspace &w, int nb, const double *z, bool vonly, cudaStream_t s);
 cudaError_t launch_lsq(const Workspace &w, int m, cudaStream_t s);
 cudaError_t launch_beta(const Workspace &w, int nblk, cudaStream_t s);
 cudaError_t launch_init_state(const Workspace &w, double tol, double normA, double inner_tol,

@@ -842,6 +842,170 @@ __global__ void __launch_bounds__(kSmallThreads) k_flush(SmallArgs a, int m, int
     if (t == 0) a.lfro2[m] = a.lfro2[m - 1] + rs;
 }
 
+// =====================================================================================
+// Alg. 4.2 (one-reduce hybrid MGS-CGS GMRES).  V[:, nb] holds u_{k-1}, the output of the
+// previous iteration's single projection (nb = k-2 normalised columns before it); the one
+// reduction gives (partials of the step-5 multi-dot over p = nb+1 columns with x0 = u,
+// x1 = A u): value c < nb is r^(2)_c = V[:,c].u, value nb is ||u||^2, value nb+1+c is
+// V[:,c].(A u), value 2nb+1 is u.(A u).  The first-projection coefficients q of the pending
+// Hessenberg column live in r0v (for nb = 1: H_11 from the prime, in H[0]).
+// =====================================================================================
+// Steps 5-9, 12, 14, 15 (and the flush, step 14 only with the normalisation's data):
+//   r^(3) = (I + L_nb)^{-1} r^(2), gamma = sqrt(||u||^2 - ||r^(2)||^2) (lagged norm),
+//   H_{0:nb-1, nb-1} = q + r^(3), H_{nb, nb-1} = gamma (column nb-1 complete), breakdown test;
+//   L row nb = r^(2) / gamma; with flush == 0 also r^(0) / gamma (its last entry twice),
+//   r^(1) = [r^(0)_{0:nb-1}; r^(0)_nb - L_nb . r^(0)_{0:nb-1}] (Stephen's trick) and the new
+//   q = r^(1) - H_{0:nb, 0:nb-1} r^(3) / gamma.  Outputs: r2v = r^(2), r1v = r^(1), r0v = q,
+//   st->inv_gamma.
+__global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, int flush, int nrb)
+{
+    IGS_PDL_ENTER();
+    DevState *st = a.st;
+    if (halted(st)) return;
+    if (st->stop_reason != 0) {  // the previous column met the stop test
+        if (threadIdx.x == 0) st->halt = 1;
+        return;
+    }
+    extern __shared__ double dsm[];
+    const int nv = flush ? nb + 1 : 2 * (nb + 1);
+    double *buf = dsm;            // combined partials (nv)
+    double *r3s = buf + 2 * (nb + 1);
+    double *tmp = r3s + nb;
+    double *qs = tmp + nb;        // q of the completed column (nb)
+    double *Lsm = qs + nb;        // packed L_nb
+    __shared__ double s_ig, s_g2;
+    __shared__ int s_stop;
+    const int t = threadIdx.x;
+    const double lf2_prev = t == 0 ? a.lfro2[nb - 1] : 0.0;
+    reduce_partials(a.part, nv, nrb, buf);
+    for (int c = t; c < nb; c += blockDim.x) qs[c] = nb == 1 ? a.H[0] : a.r0v[c];
+    if (t < 32) {
+        // ||r^(2)||^2 (fixed shuffle tree), the lagged norm's argument
+        double rr = 0.0;
+        for (int c = t; c < nb; c += 32) rr = fma(buf[c], buf[c], rr);
+        for (int o = 16; o > 0; o >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, o);
+        if (t == 0) s_g2 = buf[nb] - rr;
+    }
+    __syncthreads();
+    // step 5: r^(3) = (I + L_nb)^{-1} r^(2)
+    stage_lower(a.L, a.ldl, nb, Lsm);
+    unit_lower_solve(Lsm, nb, buf, r3s, tmp, neumann_terms(a.lfro2[nb - 1]));
+    // step 14: column nb-1 complete
+    for (int c = t; c < nb; c += blockDim.x) a.H[(int64_t)(nb - 1) * a.ldh + c] = qs[c] + r3s[c];
+    __syncthreads();
+    if (t == 0) {
+        const double g2 = s_g2;
+        int stop = 0;
+        double gam = 0.0, ig = 0.0;
+        if (g2 != g2 || isinf(g2)) {
+            stop = -4;
+        } else {
+            if (g2 > 0.0) {
+                gam = sqrt(g2);
+                ig = 1.0 / gam;
+            }
+            a.H[(int64_t)(nb - 1) * a.ldh + nb] = gam;
+            double hn2 = 0.0;
+            for (int c = 0; c < nb; ++c) {
+                const double h = a.H[(int64_t)(nb - 1) * a.ldh + c];
+                hn2 = fma(h, h, hn2);
+            }
+            if (gam == 0.0 || gam <= kBreakdownFactor * sqrt(hn2)) stop = 2;
+        }
+        if (stop != 0) {
+            st->halt = 1;
+            st->stop_reason = stop;
+            st->stop_cols = nb;
+        }
+        st->inv_gamma = ig;
+        s_ig = ig;
+        s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop != 0) return;
+    const double ig = s_ig;
+    // step 9: L row nb = r^(2) / gamma, and ||L_{nb+1}||_F^2
+    if (t < 32) {
+        double rowsq = 0.0;
+        for (int c = t; c < nb; c += 32) {
+            const double l = buf[c] * ig;
+            a.L[(int64_t)c * a.ldl + nb] = l;
+            rowsq = fma(l, l, rowsq);
+        }
+        for (int o = 16; o > 0; o >>= 1) rowsq += __shfl_down_sync(0xffffffffu, rowsq, o);
+        if (t == 0) a.lfro2[nb] = lf2_prev + rowsq;
+    }
+    for (int c = t; c < nb; c += blockDim.x) a.r2v[c] = buf[c];
+    if (flush) return;
+    __syncthreads();
+    // steps 7-8 and 12 (Stephen's trick for the last entry of r^(1))
+    double *r1s = tmp;  // reuse (nb + 1 entries fit: tmp, qs are contiguous)
+    for (int c = t; c < nb; c += blockDim.x) r1s[c] = buf[nb + 1 + c] * ig;
+    __syncthreads();
+    if (t < 32) {
+        double lr = 0.0;
+        for (int c = t; c < nb; c += 32) lr = fma(buf[c] * ig, r1s[c], lr);
+        for (int o = 16; o > 0; o >>= 1) lr += __shfl_down_sync(0xffffffffu, lr, o);
+        if (t == 0) r1s[nb] = buf[2 * nb + 1] * ig * ig - lr;
+    }
+    __syncthreads();
+    // step 15: q = r^(1) - H_{0:nb, 0:nb-1} r^(3) / gamma
+    for (int i = t; i <= nb; i += blockDim.x) {
+        double hs = 0.0;
+        for (int c = 0; c < nb; ++c) hs = fma(a.H[(int64_t)c * a.ldh + i], r3s[c] * ig, hs);
+        a.r0v[i] = r1s[i] - hs;
+        a.r1v[i] = r1s[i];
+    }
+}
+
+// Steps 10-11 and 13 in one pass over V_nb (two FMAs per basis element):
+//   v = (u - V_nb r^(2)) / gamma into V[:, nb] (in place of u),
+//   u_new = z / gamma - V_nb r^(1)_{0:nb-1} - v r^(1)_nb into V[:, nb+1] (when vonly == 0).
+__global__ void __launch_bounds__(kStreamThreads)
+k_update_1r(double *V, int64_t ld, int nb, int64_t n, const double *__restrict__ r2,
+            const double *__restrict__ r1, const double *__restrict__ z, int vonly, const DevState *st)
+{
+    IGS_PDL_ENTER();
+    if (halted(st)) return;
+    extern __shared__ double sc[];  // r2 (nb), r1 (nb + 1)
+    double *s2 = sc, *s1 = sc + nb;
+    for (int c = threadIdx.x; c < nb; c += blockDim.x) s2[c] = r2[c];
+    if (!vonly)
+        for (int c = threadIdx.x; c <= nb; c += blockDim.x) s1[c] = r1[c];
+    __syncthreads();
+    const double ig = st->inv_gamma;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double *vi = V + i;
+        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+        int c = 0;
+        for (; c + 3 < nb; c += 4) {
+            double v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = vi[(int64_t)(c + q) * ld];
+            a0 = fma(v[0], s2[c], a0);
+            a1 = fma(v[1], s2[c + 1], a1);
+            a0 = fma(v[2], s2[c + 2], a0);
+            a1 = fma(v[3], s2[c + 3], a1);
+            if (!vonly) {
+                b0 = fma(v[0], s1[c], b0);
+                b1 = fma(v[1], s1[c + 1], b1);
+                b0 = fma(v[2], s1[c + 2], b0);
+                b1 = fma(v[3], s1[c + 3], b1);
+            }
+        }
+        for (; c < nb; ++c) {
+            const double v = vi[(int64_t)c * ld];
+            a0 = fma(v, s2[c], a0);
+            if (!vonly) b0 = fma(v, s1[c], b0);
+        }
+        double *un = V + (int64_t)nb * ld + i;
+        const double vnew = (*un - (a0 + a1)) * ig;
+        *un = vnew;
+        if (!vonly) V[(int64_t)(nb + 1) * ld + i] = fma(z[i], ig, -((b0 + b1) + vnew * s1[nb]));
+    }
+}
+
 // Givens least squares for column j (Sec. 1 eq. "llse"; the paper names no method).
 // The j earlier rotations are applied to the new column as a parallel scan: rotation i maps
 // the running entry a_i to a_{i+1} = -s_i a_i + c_i h_{i+1} and emits c_i a_i + s_i h_{i+1};
@@ -1200,6 +1364,7 @@ cudaError_t configure_kernels(const Workspace &w)
     // what the context's largest restart length needs.
     cudaError_t e = allow_smem((const void *)k_step_a, small_solve_smem(w.mmax, 5));
     if (e == cudaSuccess) e = allow_smem((const void *)k_step_b, small_solve_smem(w.mmax, 3));
+    if (e == cudaSuccess) e = allow_smem((const void *)k_step_1r, small_solve_smem(w.mmax + 1, 6));
     if (e == cudaSuccess) {
         int dev = 0, optin = 0;
         cudaFuncAttributes fa{};
@@ -1232,6 +1397,22 @@ cudaError_t launch_step_b(const Workspace &w, int k, const DotsPlan &pl, cudaStr
 cudaError_t launch_flush(const Workspace &w, int m, const DotsPlan &pl, cudaStream_t s)
 {
     launch_k(w.pdl, k_flush, dim3(1), dim3(kSmallThreads), 0, s, small_args(w), m, pl.rblocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_1r(const Workspace &w, int nb, bool flush, const DotsPlan &pl, cudaStream_t s)
+{
+    const size_t smem = small_solve_smem(nb + 1, 6);
+    launch_k(w.pdl, k_step_1r, dim3(1), dim3(kSmallThreads), smem, s, small_args(w), nb, flush ? 1 : 0, pl.rblocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_1r(const Workspace &w, int nb, const double *z, bool vonly, cudaStream_t s)
+{
+    const size_t smem = sizeof(double) * (size_t)(2 * nb + 2);
+    const int grid = (int)((w.n + kStreamThreads - 1) / kStreamThreads);
+    launch_k(false, k_update_1r, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, nb, w.n,
+             (const double *)w.r2v, (const double *)w.r1v, z, vonly ? 1 : 0, (const DevState *)w.st);
     return cudaGetLastError();
 }
 

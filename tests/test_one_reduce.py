@@ -1,0 +1,89 @@
+"""Alg. 4.2 (one-reduce hybrid MGS-CGS GMRES) on the GPU against the CPU oracle's Alg. 4.2
+(needs a GB300; -m gpu).
+
+Tolerances as for Alg. 4.1 with two GS iterations (the paper: Alg. 4.2's results are
+comparable to Alg. 4.1's, with O(eps) orthogonality): H columns within 1e-10 relative while
+kappa(B_k) < 1e6, the Arnoldi relation and ||I - V^T V||_F within 1e-13, ||L||_F in the
+oracle's size class (its rows u_{k-1}^T V_{k-2} / gamma are rounding-level quantities),
+solves with the oracle's status, step counts within +-2 and beta <= tol.
+"""
+import numpy as np
+import pytest
+
+import _parity as P
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2205_07805_gb300 as pkg
+    from paper_2205_07805_gb300 import build
+    build.build()
+    pkg.load_library()
+    return pkg
+
+
+CASES = {
+    "cd2d_63": gen.cd2d(63, 50.0, seed=1),
+    "random_1000": (gen.random_sparse(1000, 12, seed=3, diag_shift=6.0), None, None, {}),
+    "dense_200": gen.dense_usv(200, 0),
+    "walker": gen.walker(),
+}
+
+
+def _rhs(name, A, b):
+    return b if b is not None else np.random.default_rng(17).standard_normal(A.n)
+
+
+@pytest.mark.parametrize("name,m", [("cd2d_63", 60), ("random_1000", 50), ("dense_200", 200), ("walker", 10)])
+def test_one_reduce_arnoldi_parity(pkg, name, m):
+    A, b, _, info = CASES[name]
+    r0 = _rhs(name, A, b)
+    normA = info.get("normA") or float(np.linalg.norm(gen.csr_to_dense(A), 2))
+    with pkg.Solver(A, max_restart_m=m, A_norm2=normA) as s:
+        g = s.arnoldi(r0, m, method="one_reduce")
+    o = oracle.arnoldi(A, r0, m, oracle.ONE_REDUCE, 2)
+    assert g["ncols"] == o["ncols"] and g["status"] == o["status"], (g["ncols"], o["ncols"])
+    k = o["ncols"]
+    kap = P.kappa_prefix(A, r0, o["V"], k)
+    herr = P.h_column_errors(g["H"], o["H"], k)
+    well = kap < 1e6
+    assert well[0]
+    assert np.all(herr[well] <= 1e-10), f"max H column error {herr[well].max():.3g}"
+    Vg = g["V"]
+    assert P.arnoldi_relation(A, Vg, g["H"], k, normA) <= 1e-13
+    assert P.orth_loss(Vg, min(k, A.n)) <= 1e-13
+    # L's rows u_{k-1}^T V_{k-2} / gamma are the first projection's loss of orthogonality, a
+    # rounding-level quantity: two roundings agree in size class only
+    kk = k + 1 if g["status"] == 0 else k
+    lg, lo = np.linalg.norm(g["L"][:kk, :kk]), np.linalg.norm(o["L"][:kk, :kk])
+    assert lg <= max(10 * lo, 1e-13) and lo <= max(10 * lg, 1e-13), (lg, lo)
+
+
+@pytest.mark.parametrize("name,m,tol,cycles", [("cd2d_63", 40, 1e-12, 60), ("walker", 10, 1e-15, 3),
+                                               ("dense_200", 200, 1e-14, 1), ("random_1000", 40, 1e-13, 40)])
+def test_one_reduce_solve_parity(pkg, name, m, tol, cycles):
+    A, b, _, info = CASES[name]
+    b = _rhs(name, A, b)
+    normA = info.get("normA") or gen.norm2_power(A)
+    o = oracle.gmres(A, b, m=m, method=oracle.ONE_REDUCE, tol=tol, max_cycles=cycles, normA=normA)
+    with pkg.Solver(A, max_restart_m=m, A_norm2=normA) as s:
+        g = s.solve(b, m=m, tol=tol, max_restarts=cycles, method="one_reduce")
+        g2 = s.solve(b, m=m, gs=2, tol=tol, max_restarts=cycles)  # Alg. 4.1 on the same system
+    assert g["status"] == o["status"], (g["status"], o["status"], g["beta"], o["beta"])
+    if o["status"] == oracle.OK:
+        assert g["beta"] <= tol
+        assert abs(g["steps"] - o["steps"]) <= 2, (g["steps"], o["steps"])
+        assert abs(g["steps"] - g2["steps"]) <= max(2, g2["steps"] // 20), (g["steps"], g2["steps"])
+
+
+def test_one_reduce_rejects_fp32(pkg):
+    A, b, _, _ = gen.cd2d(16, 10.0, seed=0)
+    with pkg.Solver(A, max_restart_m=10, A_norm2=8.0, fp32_basis=True) as s:
+        with pytest.raises(pkg.IGSError):
+            s.solve(b, m=10, method="one_reduce", precision="fp32_ir")
+        with pytest.raises(ValueError):
+            s.solve(b, m=10, method="cgs")

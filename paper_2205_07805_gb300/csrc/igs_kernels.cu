@@ -350,9 +350,9 @@ k_dots(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t rows
 // =====================================================================================
 // Basis update (Alg. 4.1 steps 7, 11, 13 and 16; x_m = x_0 + V_m y_m at cycle end):
 //   out[i] = a * src[i] - sum_{c<p} V[i,c] coef[c]
-// Thread per row, coalesced over rows for each column.  With norm_last, column p-1 (the
-// lagged w_{k-1}) is first normalised in place, v = w * inv_gamma (step 7), and
-// a = inv_gamma (step 11).
+// Two rows per thread (16-byte loads), coalesced over rows for each column.  With
+// norm_last, column p-1 (the lagged w_{k-1}) is first normalised in place,
+// v = w * inv_gamma (step 7), and a = inv_gamma (step 11).
 // =====================================================================================
 __global__ void __launch_bounds__(kStreamThreads)
 k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coef, int neg_coef,
@@ -367,35 +367,45 @@ k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coe
     for (int c = threadIdx.x; c < p; c += blockDim.x) sc[c] = neg_coef ? -coef[c] : coef[c];
     __syncthreads();
     const int pc = norm_last ? p - 1 : p;
+    // Two rows per thread (16-byte loads; ld is even and the pad rows stay zero).
+    const int64_t npairs = (n + 1) >> 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (int64_t pr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pr < npairs; pr += stride) {
+        const int64_t i = 2 * pr;
         const double *vi = V + i;
-        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+        double x0 = 0.0, x1 = 0.0, y0 = 0.0, y1 = 0.0;
         int c = 0;
-        // eight independent loads in flight per thread, four FMA chains
         for (; c + 7 < pc; c += 8) {
-            double v[8];
+            double2 v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = vi[(int64_t)(c + q) * ld];
-            acc0 = fma(v[0], sc[c], acc0);
-            acc1 = fma(v[1], sc[c + 1], acc1);
-            acc2 = fma(v[2], sc[c + 2], acc2);
-            acc3 = fma(v[3], sc[c + 3], acc3);
-            acc0 = fma(v[4], sc[c + 4], acc0);
-            acc1 = fma(v[5], sc[c + 5], acc1);
-            acc2 = fma(v[6], sc[c + 6], acc2);
-            acc3 = fma(v[7], sc[c + 7], acc3);
+            for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const double2 *>(vi + (int64_t)(c + q) * ld);
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                x0 = fma(v[q].x, sc[c + q], x0);
+                y0 = fma(v[q].y, sc[c + q], y0);
+                x1 = fma(v[q + 1].x, sc[c + q + 1], x1);
+                y1 = fma(v[q + 1].y, sc[c + q + 1], y1);
+            }
         }
-        for (; c < pc; ++c) acc0 = fma(vi[(int64_t)c * ld], sc[c], acc0);
-        acc0 += acc2;
-        acc1 += acc3;
+        for (; c < pc; ++c) {
+            const double2 v = *reinterpret_cast<const double2 *>(vi + (int64_t)c * ld);
+            x0 = fma(v.x, sc[c], x0);
+            y0 = fma(v.y, sc[c], y0);
+        }
         if (norm_last) {
-            double *vl = V + (int64_t)(p - 1) * ld + i;
-            const double v = *vl * a;
+            double2 *vl = reinterpret_cast<double2 *>(V + (int64_t)(p - 1) * ld + i);
+            double2 v = *vl;
+            v.x *= a;
+            v.y *= a;
             *vl = v;
-            acc1 = fma(v, sc[p - 1], acc1);
+            x1 = fma(v.x, sc[p - 1], x1);
+            y1 = fma(v.y, sc[p - 1], y1);
         }
-        out[i] = fma(a, src[i], -(acc0 + acc1));
+        const double2 sv = *reinterpret_cast<const double2 *>(src + i);
+        double2 o;
+        o.x = fma(a, sv.x, -(x0 + x1));
+        o.y = fma(a, sv.y, -(y0 + y1));
+        *reinterpret_cast<double2 *>(out + i) = o;
     }
 }
 
@@ -1261,7 +1271,7 @@ cudaError_t launch_update(const Workspace &w, int p, const double *coef, bool ne
     const size_t smem = sizeof(double) * (size_t)(pmax > 0 ? pmax : 1);
     // one row per thread: the whole vector is resident at once (occupancy, not a grid-stride
     // loop, hides the loads' latency)
-    const int grid = (int)((w.n + kStreamThreads - 1) / kStreamThreads);
+    const int grid = (int)(((w.n + 1) / 2 + kStreamThreads - 1) / kStreamThreads);
     launch_k(false, k_update, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef, neg_coef ? 1 : 0,
                                                           alpha, src, out, norm_last ? 1 : 0,
                                                           p_from_state ? 1 : 0, w.st,

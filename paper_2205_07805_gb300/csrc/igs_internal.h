@@ -18,6 +18,9 @@ constexpr int kDotsColsPerBlock = 4;
 constexpr int kBlocksPerSM = 2;
 // Resident blocks per SM of the multi-dot kernel (256 threads, <= 80 registers).
 constexpr int kDotsBlocksPerSM = 3;
+// Basis update grid: a whole number of blocks per SM, each with an equal row range (the update
+// is bound by the FP64 pipe, so an uneven block count per SM costs its share directly).
+constexpr int kUpdateBlocksPerSM = 4;
 // Fused update + second reduction: rows per tile (= threads per block), blocks per combine
 // group, and the largest dynamic shared memory it may use (p up to ~216 columns).
 constexpr int kFusedRows = 128;

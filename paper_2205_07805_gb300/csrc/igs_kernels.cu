@@ -60,16 +60,20 @@ __device__ void reduce_partials(const double *__restrict__ part, int nv, int nrb
         double s = 0.0;
         if (v < nv) {
             double a[kRedRegs];
-            int rb0 = sub;
             double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
-            for (; rb0 < nrb; rb0 += kRedRegs * tpv) {  // one pass unless nrb > kRedRegs * 32
+            // one pass unless nrb > kRedRegs * 32; the adds stop at the warp-uniform count
+            // jmax of loaded partials (every FP64 add costs the warp's sub-partition dearly)
+            for (int pass0 = 0; pass0 < nrb; pass0 += kRedRegs * tpv) {
+                const int rb0 = pass0 + sub;
+                const int jmax = min(kRedRegs, (nrb - pass0 + tpv - 1) / tpv);
 #pragma unroll
                 for (int j = 0; j < kRedRegs; ++j) {
                     const int rb = rb0 + j * tpv;
-                    a[j] = rb < nrb ? part[(int64_t)rb * nv + v] : 0.0;
+                    a[j] = (j < jmax && rb < nrb) ? part[(int64_t)rb * nv + v] : 0.0;
                 }
 #pragma unroll
                 for (int j = 0; j < kRedRegs; j += 4) {
+                    if (j >= jmax) break;
                     acc0 += a[j];
                     acc1 += a[j + 1];
                     acc2 += a[j + 2];
@@ -84,15 +88,46 @@ __device__ void reduce_partials(const double *__restrict__ part, int nv, int nrb
     __syncthreads();
 }
 
+// FP64 -> FP32 of v * 2^-e, rounded to nearest even, in integer arithmetic only (on this
+// GPU one FP64-pipe instruction, a conversion included, holds a sub-partition for 64
+// cycles).  Requires |v| 2^-e < 2^127; results below the FP32 normal range become +-0.
+__device__ __forceinline__ float f64_scaled_to_f32(double v, int e)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const int be = (int)((b >> 52) & 0x7ff);
+    const int fe = be - 1023 - e + 127;
+    if (be == 0 || fe <= 0) return __int_as_float((int)sign);
+    const unsigned long long m = b & 0xfffffffffffffull;
+    unsigned int r = ((unsigned int)fe << 23) | (unsigned int)(m >> 29);
+    const unsigned int rem = (unsigned int)(m & 0x1fffffffu);
+    if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) r += 1u;
+    return __int_as_float((int)(sign | r));
+}
+
+// FP32 -> FP64 of y * 2^e, exact, in integer arithmetic only.  FP32 zeros and subnormals,
+// and results below the FP64 normal range, give +-0; requires y 2^e < 2^1024.
+__device__ __forceinline__ double f32_scaled_to_f64(float y, int e)
+{
+    const unsigned int b = (unsigned int)__float_as_int(y);
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    const int fe = (int)((b >> 23) & 0xff);
+    const int dei = fe - 127 + 1023 + e;
+    if (fe == 0 || dei <= 0) return __longlong_as_double((long long)sign);
+    const unsigned long long de = (unsigned long long)dei;
+    return __longlong_as_double((long long)(sign | (de << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
 // Packed strictly-lower triangle of L_p in shared memory: column c holds rows c+1..p-1
 // starting at colstart(c) = c(2p - c - 1)/2.
 __device__ __forceinline__ int packed_col(int c, int p) { return c * (2 * p - c - 1) / 2; }
 
 // Copy rows/columns 0..p-1 of the device L (column-major, Lc[c*ldl + i] = L(i,c)) into the
-// packed shared layout.  The element loop is flattened and keeps eight loads in flight per
-// thread, so the copy costs a few L2 round trips rather than one per column.  Ends with a
-// barrier.
-__device__ void stage_lower(const double *__restrict__ Lc, int ldl, int p, double *Lsm)
+// packed shared layout, as FP64, or rounded to FP32 when f32 is set (the FP32 Neumann
+// correction of unit_lower_solve).  The element loop is flattened and keeps eight loads in
+// flight per thread, so the copy costs a few L2 round trips rather than one per column.
+// Ends with a barrier.
+__device__ void stage_lower(const double *__restrict__ Lc, int ldl, int p, double *Lsm, bool f32)
 {
     const int T = blockDim.x, t = threadIdx.x;
     const int total = p * (p - 1) / 2;
@@ -115,9 +150,15 @@ __device__ void stage_lower(const double *__restrict__ Lc, int ldl, int p, doubl
                 dst[j] = e;
             }
         }
+        float *Lf = reinterpret_cast<float *>(Lsm);
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (dst[j] >= 0) Lsm[dst[j]] = v[j];
+        for (int j = 0; j < 8; ++j) {
+            if (dst[j] < 0) continue;
+            if (f32)
+                Lf[dst[j]] = f64_scaled_to_f32(v[j], 0);
+            else
+                Lsm[dst[j]] = v[j];
+        }
     }
     __syncthreads();
 }
@@ -132,10 +173,69 @@ __device__ void stage_lower(const double *__restrict__ Lc, int ldl, int p, doubl
 // term is one lane-parallel matrix-vector product instead of p dependent steps.  With two
 // Gauss-Seidel iterations ||L||_F is O(eps) and t = 2.  Otherwise the classical
 // column-oriented forward substitution runs (terms = 0; see neumann_terms).
+//
+// With f32 set (terms == 2 and (p+2) ||L||_F <= 2^-36, see neumann_fp32) the one correction
+// term L rhs is evaluated in FP32: rhs is scaled by a power of two to [-2, 2), L was staged
+// as FP32, and x = rhs - 2^e (L rhs)_32.  Rounding L, rhs and the length-p sums to FP32 errs
+// by at most (p+2) 2^-24 ||L||_F ||rhs|| <= 2^-60 ||rhs||, the bound the truncation already
+// meets (entries flushed below the FP32 normal range add at most p 2^-125 max|rhs|), while
+// the FP64 pipe of the one SM running this block would take microseconds for the p^2/2
+// products.  Scaling and conversions are integer operations; the FP64 pipe does only the p
+// final subtractions.
 __device__ void unit_lower_solve(const double *Lsm, int p, const double *rhs, double *x,
-                                 double *tmp, int terms)
+                                 double *tmp, int terms, bool f32)
 {
     const int T = blockDim.x, t = threadIdx.x;
+    if (f32) {
+        __shared__ int s_wmax[kSmallThreads / 32];
+        const int lane = t & 31, wid = t >> 5;
+        // e = largest binary exponent of rhs (biased exponent field; a subnormal counts as
+        // -1022, above its true exponent, which keeps |rhs| 2^-e < 2)
+        int e = -1022;
+        for (int i = t; i < p; i += T) {
+            const int be = (int)((__double_as_longlong(rhs[i]) >> 52) & 0x7ff);
+            e = max(e, be - 1023);
+        }
+        e = __reduce_max_sync(0xffffffffu, e);
+        if (lane == 0) s_wmax[wid] = e;
+        __syncthreads();
+        int emax = s_wmax[0];
+        for (int q = 1; q < T / 32; ++q) emax = max(emax, s_wmax[q]);
+        emax = min(emax, 1000);  // a non-finite rhs stays non-finite below
+        float *xf = reinterpret_cast<float *>(tmp);
+        const float *Lf = reinterpret_cast<const float *>(Lsm);
+        float *yf = xf + p;  // tmp holds 2p floats
+        for (int i = t; i < p; i += T) xf[i] = f64_scaled_to_f32(rhs[i], emax);
+        __syncthreads();
+        // Rows a and p-1-a (equal total length) form pair a; tpp threads share a pair and
+        // take every tpp-th column, then combine by a fixed shuffle tree.
+        const int npair = (p + 1) >> 1;
+        int tpp = 32;
+        while (tpp > 1 && npair * tpp > T) tpp >>= 1;
+        for (int base = 0; base < npair * tpp; base += T) {
+            const int q = base + t, a = q / tpp, h = q % tpp;
+            const bool act = a < npair;
+            const int r0 = a, r1 = p - 1 - a;
+            float s0 = 0.0f, s1 = 0.0f;
+            if (act) {
+                for (int c = h; c < r0; c += tpp) s0 = fmaf(Lf[packed_col(c, p) + r0 - c - 1], xf[c], s0);
+                if (r1 != r0)
+                    for (int c = h; c < r1; c += tpp) s1 = fmaf(Lf[packed_col(c, p) + r1 - c - 1], xf[c], s1);
+            }
+            for (int o = tpp >> 1; o > 0; o >>= 1) {
+                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            }
+            if (act && h == 0) {
+                yf[r0] = s0;
+                if (r1 != r0) yf[r1] = s1;
+            }
+        }
+        __syncthreads();
+        for (int i = t; i < p; i += T) x[i] = rhs[i] - f32_scaled_to_f64(yf[i], emax);
+        __syncthreads();
+        return;
+    }
     if (terms >= 1) {
         for (int i = t; i < p; i += T) x[i] = rhs[i];
         __syncthreads();
@@ -201,6 +301,14 @@ __device__ __forceinline__ int neumann_terms(double lfro2)
     const int d = -(ex + 1);                          // ||L||_F < 2^(-d/2), d >= 30
     const int terms = (120 + d - 1) / d;
     return terms < 2 ? 2 : terms;
+}
+
+// Whether unit_lower_solve may evaluate the Neumann correction in FP32: two terms, and
+// (p+2) ||L||_F <= 2^-36 (lfro2 = ||L||_F^2; false for a non-finite value).
+__device__ __forceinline__ bool neumann_fp32(double lfro2, int p, int terms)
+{
+    const double q = (double)(p + 2);
+    return terms == 2 && q * q * lfro2 <= 0x1p-72;
 }
 
 // ||col[0:len]||^2 by the block's last warp (fixed shuffle tree), stored in *out.  Called
@@ -368,9 +476,13 @@ k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coe
     __syncthreads();
     const int pc = norm_last ? p - 1 : p;
     // Two rows per thread (16-byte loads; ld is even and the pad rows stay zero).
+    // Block b owns the contiguous pair range [b ppb, (b+1) ppb): with a grid of a whole
+    // number of blocks per SM every SM gets the same share of the FP64 work.
     const int64_t npairs = (n + 1) >> 1;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t pr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pr < npairs; pr += stride) {
+    const int64_t ppb = (npairs + gridDim.x - 1) / gridDim.x;
+    const int64_t pr_lo = (int64_t)blockIdx.x * ppb;
+    const int64_t pr_hi = pr_lo + ppb < npairs ? pr_lo + ppb : npairs;
+    for (int64_t pr = pr_lo + threadIdx.x; pr < pr_hi; pr += blockDim.x) {
         const int64_t i = 2 * pr;
         const double *vi = V + i;
         double x0 = 0.0, x1 = 0.0, y0 = 0.0, y1 = 0.0;
@@ -708,7 +820,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
     double *tmp = r1s + pp;         // solve scratch
     double *Lsm = tmp + pp;         // packed L_p
     __shared__ double s_inv_gamma;
-    __shared__ int s_stop, s_terms;
+    __shared__ int s_stop, s_terms, s_f32;
     __shared__ double s_hn2;
     const int p = k - 1, t = threadIdx.x;
     const double lf2_prev = t == 0 ? a.lfro2[p - 2] : 0.0;  // issued early
@@ -755,6 +867,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
             const double lf2 = lf2_prev + rowsq;
             a.lfro2[p - 1] = lf2;
             s_terms = neumann_terms(lf2);
+            s_f32 = neumann_fp32(lf2, p, s_terms);
         }
     } else {
         // steps 8-9 (other warps): r^(0) / gamma, its last entry once more
@@ -766,9 +879,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
     }
     __syncthreads();
     // step 12
-    stage_lower(a.L, a.ldl, p, Lsm);
     const int terms = s_terms;
-    unit_lower_solve(Lsm, p, r0s, r1s, tmp, terms);
+    const bool f32 = s_f32 != 0;
+    stage_lower(a.L, a.ldl, p, Lsm, f32);
+    unit_lower_solve(Lsm, p, r0s, r1s, tmp, terms, f32);
     for (int c = t; c < p; c += blockDim.x) {
         a.r1v[c] = r1s[c];
         if (gs == 1) a.H[(int64_t)(p - 1) * a.ldh + c] = r1s[c];
@@ -780,15 +894,19 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
 //   r^(3) = (I + L_{k-1})^{-1} r^(2),  H_{1:k-1,k-1} = r^(1) + r^(3).
 __global__ void __launch_bounds__(kSmallThreads) k_step_b(SmallArgs a, int k, int nrb)
 {
-    IGS_PDL_ENTER();
-    DevState *st = a.st;
-    if (halted(st)) return;
     extern __shared__ double dsm[];
     const int p = k - 1, t = threadIdx.x;
     double *r2s = dsm, *r3s = r2s + p, *tmp = r3s + p, *Lsm = tmp + p;
+    // L_{k-1} and ||L||_F were written by k_step_a, which completed before the multi-dot this
+    // kernel follows was launched: they are staged before waiting for that multi-dot.
+    const int terms = neumann_terms(a.lfro2[p - 1]);
+    const bool f32 = neumann_fp32(a.lfro2[p - 1], p, terms);
+    stage_lower(a.L, a.ldl, p, Lsm, f32);
+    IGS_PDL_ENTER();
+    DevState *st = a.st;
+    if (halted(st)) return;
     reduce_partials(a.part, p, nrb, r2s);
-    stage_lower(a.L, a.ldl, p, Lsm);
-    unit_lower_solve(Lsm, p, r2s, r3s, tmp, neumann_terms(a.lfro2[p - 1]));
+    unit_lower_solve(Lsm, p, r2s, r3s, tmp, terms, f32);
     for (int c = t; c < p; c += blockDim.x) {
         a.r3v[c] = r3s[c];
         a.H[(int64_t)(p - 1) * a.ldh + c] = a.r1v[c] + r3s[c];
@@ -898,8 +1016,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, 
     }
     __syncthreads();
     // step 5: r^(3) = (I + L_nb)^{-1} r^(2)
-    stage_lower(a.L, a.ldl, nb, Lsm);
-    unit_lower_solve(Lsm, nb, buf, r3s, tmp, neumann_terms(a.lfro2[nb - 1]));
+    const int terms = neumann_terms(a.lfro2[nb - 1]);
+    const bool f32 = neumann_fp32(a.lfro2[nb - 1], nb, terms);
+    stage_lower(a.L, a.ldl, nb, Lsm, f32);
+    unit_lower_solve(Lsm, nb, buf, r3s, tmp, terms, f32);
     // step 14: column nb-1 complete
     for (int c = t; c < nb; c += blockDim.x) a.H[(int64_t)(nb - 1) * a.ldh + c] = qs[c] + r3s[c];
     __syncthreads();
@@ -1271,7 +1391,7 @@ cudaError_t launch_update(const Workspace &w, int p, const double *coef, bool ne
     const size_t smem = sizeof(double) * (size_t)(pmax > 0 ? pmax : 1);
     // one row per thread: the whole vector is resident at once (occupancy, not a grid-stride
     // loop, hides the loads' latency)
-    const int grid = (int)(((w.n + 1) / 2 + kStreamThreads - 1) / kStreamThreads);
+    const int grid = w.num_sms * kUpdateBlocksPerSM;
     launch_k(false, k_update, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef, neg_coef ? 1 : 0,
                                                           alpha, src, out, norm_last ? 1 : 0,
                                                           p_from_state ? 1 : 0, w.st,

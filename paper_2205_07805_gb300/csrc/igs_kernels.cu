@@ -385,11 +385,13 @@ k_spmv_warp(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ c
 // =====================================================================================
 // Block multi-dot (Alg. 4.1 step 5, the one global reduction per iteration; step 14).
 // part[rb*(NQ*p) + q*p + c] = sum over the rows of row block rb of V[:,c] * X_q.
-// Grid: x = row blocks, y = column groups (p columns split evenly).  Thread t of a block
-// owns column c_lo + t % cw and streams its own contiguous row slice t / cw: no lane ever
-// spends an FP64 add on combining other lanes' products until the slice tree at the end.
-// With NQ = 2 each V element feeds two FMAs ([V, w]^T [w, z]); with NQ = 1 two chains over
-// alternate rows keep two independent FMAs in flight.
+// Grid: x = row blocks (rows on multiples of 64), y = column groups (p columns split
+// evenly, at most 4 per group).  Warp w of a block streams column c_lo + w % cwp over its
+// row sub-slice w / cwp in 64-row segments: each lane loads two consecutive rows, so one
+// warp instruction reads 512 contiguous bytes of the column (HBM row locality; scattered
+// 16-byte lane loads ran 7 % slower).  No lane spends an FP64 add on other lanes' products
+// until the fixed-order tree over the column's lane partials at the end.  With NQ = 2 each
+// V element feeds two FMAs ([V, w]^T [w, z]).
 // =====================================================================================
 template <int NQ>
 __global__ void __launch_bounds__(kStreamThreads, kDotsBlocksPerSM)
@@ -399,59 +401,66 @@ k_dots(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t rows
 {
     IGS_PDL_ENTER();
     if (check_halt && halted(st)) return;
+    constexpr int W = kStreamThreads / 32;
     __shared__ double red[NQ][kStreamThreads];
     const int rb = blockIdx.x, G = gridDim.y, cg = blockIdx.y;
     const int c_lo = (int)((int64_t)cg * p / G), c_hi = (int)((int64_t)(cg + 1) * p / G);
     const int cw = c_hi - c_lo;
-    const int S = blockDim.x / cw;
-    const int t = threadIdx.x, cl = t % cw, s = t / cw;
+    const int cwp = cw <= 1 ? 1 : cw <= 2 ? 2 : cw <= 4 ? 4 : 8;
+    const int S = W / cwp;          // warps (row sub-slices) per column
+    const int K = S * 32;           // lane partials per column
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int cl = wid % cwp, s = wid / cwp;
     const int64_t r_lo = (int64_t)rb * rows;
     const int64_t r_hi = r_lo + rows < n4 ? r_lo + rows : n4;
     double a0 = 0.0, a1 = 0.0;
-    if (s < S && r_lo < r_hi) {
-        // slice boundaries on multiples of 4 rows (n4 and rows are multiples of 4)
-        const int64_t nquad = (r_hi - r_lo) >> 2;
-        const int64_t i0 = r_lo + 4 * (nquad * s / S), i1 = r_lo + 4 * (nquad * (s + 1) / S);
+    if (cl < cw && r_lo < r_hi) {
+        const int64_t nseg = (r_hi - r_lo + 63) >> 6;  // 64-row segments: 512 bytes per column
+        const int64_t g0 = nseg * s / S, g1 = nseg * (s + 1) / S;
         const double *__restrict__ vc = V + (int64_t)(c_lo + cl) * ld;
-        for (int64_t i = i0; i < i1; i += 4) {
-            const double2 va = *reinterpret_cast<const double2 *>(vc + i);
-            const double2 vb = *reinterpret_cast<const double2 *>(vc + i + 2);
-            const double2 xa = *reinterpret_cast<const double2 *>(x0 + i);
-            const double2 xb = *reinterpret_cast<const double2 *>(x0 + i + 2);
-            if (NQ == 2) {
-                const double2 ya = *reinterpret_cast<const double2 *>(x1 + i);
-                const double2 yb = *reinterpret_cast<const double2 *>(x1 + i + 2);
-                a0 = fma(va.x, xa.x, a0); a1 = fma(va.x, ya.x, a1);
-                a0 = fma(va.y, xa.y, a0); a1 = fma(va.y, ya.y, a1);
-                a0 = fma(vb.x, xb.x, a0); a1 = fma(vb.x, yb.x, a1);
-                a0 = fma(vb.y, xb.y, a0); a1 = fma(vb.y, yb.y, a1);
-            } else {
-                a0 = fma(va.x, xa.x, a0); a1 = fma(va.y, xa.y, a1);
-                a0 = fma(vb.x, xb.x, a0); a1 = fma(vb.y, xb.y, a1);
+#pragma unroll 4
+        for (int64_t g = g0; g < g1; ++g) {
+            const int64_t i = r_lo + (g << 6) + 2 * lane;
+            if (i < r_hi) {
+                const double2 v = *reinterpret_cast<const double2 *>(vc + i);
+                const double2 xa = *reinterpret_cast<const double2 *>(x0 + i);
+                if (NQ == 2) {
+                    const double2 ya = *reinterpret_cast<const double2 *>(x1 + i);
+                    a0 = fma(v.x, xa.x, a0);
+                    a1 = fma(v.x, ya.x, a1);
+                    a0 = fma(v.y, xa.y, a0);
+                    a1 = fma(v.y, ya.y, a1);
+                } else {
+                    a0 = fma(v.x, xa.x, a0);
+                    a1 = fma(v.y, xa.y, a1);
+                }
             }
         }
     }
-    if (NQ == 1) {
-        red[0][t] = a0 + a1;
-    } else {
-        red[0][t] = a0;
-        red[NQ - 1][t] = a1;
-    }
-    // fixed-order tree over the S slices of each column
-    int Sp = S;
-    while (Sp > 1) {
-        const int h = (Sp + 1) >> 1;
-        __syncthreads();
-        if (s < Sp - h) {
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) red[q][t] += red[q][t + h * cw];
+    // lane partials of column cl at red[q][cl * K + s * 32 + lane]; fixed-order tree per column
+    if (cl < cw) {
+        const int k = s * 32 + lane;
+        if (NQ == 1) {
+            red[0][cl * K + k] = a0 + a1;
+        } else {
+            red[0][cl * K + k] = a0;
+            red[NQ - 1][cl * K + k] = a1;
         }
-        Sp = h;
+    }
+    for (int h = K >> 1; h >= 1; h >>= 1) {
+        __syncthreads();
+        if (t < cwp * h) {
+            const int c = t / h, k = t % h;
+            if (c < cw) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) red[q][c * K + k] += red[q][c * K + k + h];
+            }
+        }
     }
     __syncthreads();
-    if (s == 0) {
+    if (t < cw) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) part[(int64_t)rb * NQ * p + (int64_t)q * p + c_lo + cl] = red[q][t];
+        for (int q = 0; q < NQ; ++q) part[(int64_t)rb * NQ * p + (int64_t)q * p + c_lo + t] = red[q][t * K];
     }
 }
 
@@ -1342,7 +1351,7 @@ DotsPlan plan_dots_slots(const Workspace &w, int p, int slots)
     if (rblocks > maxrb) rblocks = (int)maxrb;
     if (rblocks < 1) rblocks = 1;
     int64_t rows = (n4 + rblocks - 1) / rblocks;
-    rows = (rows + 3) & ~int64_t(3);
+    rows = (rows + 63) & ~int64_t(63);  // 64-row (512-byte) segments of the multi-dot
     rblocks = (int)((n4 + rows - 1) / rows);
     pl.groups = groups;
     pl.rblocks = rblocks;

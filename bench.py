@@ -424,6 +424,19 @@ def serve_config(duration):
             "step": "the whole stream: arrivals for window_s, then the admitted backlog drains"}
 
 
+def norm_bound(A):
+    """sqrt(||A||_1 ||A||_inf) >= ||A||_2: the norm the server's beta uses for a request
+    without one, so that the one-at-a-time solves stop at the same beta."""
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    av = np.abs(A.val)
+    return float(np.sqrt(np.bincount(A.colind, av, A.n).max() * np.bincount(rows, av, A.n).max()))
+
+
+def serve_n(side):
+    """Unknowns of the side x side grid of a served request."""
+    return side * side
+
+
 def serve_stream(seed, duration):
     """Seeded arrival stream: (arrival time, grid side, Peclet, tol, precision, rhs seed)."""
     rng = np.random.default_rng(seed)
@@ -437,16 +450,18 @@ def serve_stream(seed, duration):
                     "fp32_ir" if rng.integers(0, 2) else "fp64", int(rng.integers(1 << 30))))
 
 
-def run_served(args, pkg, torch, local, dist, duration, drain_s, one_at_a_time=4):
+def run_served(args, pkg, torch, local, dist, duration, drain_s, oaat_budget_s=60.0):
     """Replay the arrival stream against the request server: a request is materialised (its
     matrix generated) and submitted at its arrival time when the server's backlog has room,
-    else it is refused (counted).  Latency = completion - arrival.  Then solves one at a time
-    through igs_solve (FP64) on a sample of the same distribution."""
+    else it is refused (counted).  Latency = completion - arrival.  Then the completed
+    requests are solved again one at a time through igs_solve (FP64), in an order spread
+    over the run, until all are done or oaat_budget_s has passed; if the budget ends it
+    first, the one-at-a-time time of the rest is extrapolated by work (n x served steps)."""
     ws, rank, _ = dist_env()
     stream = serve_stream(SEED + rank, duration)
-    max_queue = 16
-    sv = pkg.Server(max_restart_m=SERVE_M, arena_bytes=SERVE_ARENA, slots=8, rows_per_cta=4096,
-                    max_queue=max_queue, device=local)
+    max_queue = args.serve_backlog
+    sv = pkg.Server(max_restart_m=SERVE_M, arena_bytes=SERVE_ARENA, slots=args.serve_slots,
+                    rows_per_cta=4096, max_queue=max_queue, device=local, graph_min_n=args.serve_graph_min_n)
     arrivals, done, refused = {}, [], 0
     t_start = sv.clock()
     k = 0
@@ -480,27 +495,35 @@ def run_served(args, pkg, torch, local, dist, duration, drain_s, one_at_a_time=4
     svc = np.array([c["t_done"] - c["t_admit"] for c in done]) if done else np.array([np.nan])
     ok = sum(1 for c in done if c["status"] == 0)
     line = {"metric": "served solves/s", "value": len(done) / (t_end - t_start), "unit": "solves/s",
-            "config": serve_config(duration), "offered": len(stream), "submitted": st["submitted"],
+            "config": {**serve_config(duration), "slots": args.serve_slots, "backlog": max_queue,
+                       "graph_min_n": args.serve_graph_min_n},
+            "offered": len(stream), "submitted": st["submitted"],
             "refused_backlog_full": refused, "completed": len(done), "completed_ok": ok,
             "unfinished_at_end": st["queued"] + st["running"], "wall_s": t_end - t_start,
             "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
             "service_p50_s": float(np.percentile(svc, 50)),
             "arena_peak_bytes": st["arena_peak"], "gpu_launches": st["launches"],
             "by_precision": {p: sum(1 for c in done if arrivals[c["id"]][2] == p) for p in ("fp64", "fp32_ir")},
+            "by_path": {"gang": sum(1 for c in done if c["path"] == 0),
+                        "graph_lane": sum(1 for c in done if c["path"] == 1)},
             "max_backlog": max_queue}
-    if one_at_a_time and done:
-        # the same requests (a sample of those the server completed, spread over the run),
-        # one at a time through igs_solve in FP64 with graph-captured cycles
-        sample = [done[i] for i in np.linspace(0, len(done) - 1, min(one_at_a_time, len(done))).astype(int)]
-        by_id = {i: s_ for i, s_ in zip(range(len(stream)), stream)}
-        t_tot, n_ok, served_s = 0.0, 0, 0.0
-        for c in sample:
+    if oaat_budget_s > 0 and done:
+        # the same requests, one at a time through igs_solve in FP64 with graph-captured
+        # cycles (set-up and capture outside the timing), in an order spread over the run
+        order = list(range(0, len(done), 2)) + list(range(1, len(done), 2))
+        work = {c["id"]: float(c["steps"]) * serve_n(arrivals[c["id"]][1]) for c in done}
+        t_tot, n_ok, n_run, w_run = 0.0, 0, 0, 0.0
+        t_budget = time.perf_counter() + oaat_budget_s
+        for j in order:
+            if time.perf_counter() > t_budget:
+                break
+            c = done[j]
             t_arr, side, prec, tol = arrivals[c["id"]]
-            rs = next(x[5] for x in stream if abs(x[0] + t_start - t_arr) < 1e-9)
-            pe = next(x[2] for x in stream if abs(x[0] + t_start - t_arr) < 1e-9)
-            A, b, _, _ = gen.cd2d(side, pe, rs)
+            src = next(x for x in stream if abs(x[0] + t_start - t_arr) < 1e-9)
+            A, b, _, _ = gen.cd2d(side, src[2], src[5])
             st_ = torch.cuda.current_stream()
-            with pkg.Solver(A, max_restart_m=SERVE_M, device=local, stream=st_.cuda_stream) as so:
+            with pkg.Solver(A, max_restart_m=SERVE_M, A_norm2=norm_bound(A), device=local,
+                            stream=st_.cuda_stream) as so:
                 bd = torch.from_numpy(b).cuda()
                 xd = torch.empty_like(bd)
                 so.solve(bd, m=SERVE_M, gs=2, tol=tol, max_restarts=1, x_out=xd, hist_cap=0)  # capture
@@ -510,13 +533,18 @@ def run_served(args, pkg, torch, local, dist, duration, drain_s, one_at_a_time=4
                 torch.cuda.synchronize()
                 t_tot += time.perf_counter() - t0
                 n_ok += r["status"] == 0
-            served_s += c["t_done"] - c["t_admit"]
-        del by_id
-        line["one_at_a_time"] = {"value": len(sample) / t_tot, "unit": "solves/s", "converged": n_ok,
+            n_run += 1
+            w_run += work[c["id"]]
+        w_all = sum(work.values())
+        t_all = t_tot * (w_all / w_run) if n_run < len(done) else t_tot
+        line["one_at_a_time"] = {"value": len(done) / t_all, "unit": "solves/s", "converged": n_ok,
                                  "path": "igs_solve per request (FP64, whole GPU, context set-up and "
                                          "graph capture outside the timing)",
-                                 "sample": f"{len(sample)} of the completed requests, solved again one at a time",
-                                 "sample_served_service_s": served_s, "sample_one_at_a_time_s": t_tot}
+                                 "requests": f"{n_run} of the {len(done)} completed requests solved again "
+                                             f"one at a time ({t_tot:.1f} s)"
+                                             + ("" if n_run == len(done) else
+                                                "; the rest extrapolated by work = n x served steps"),
+                                 "one_at_a_time_s": t_all}
         line["speedup_vs_one_at_a_time"] = line["value"] / line["one_at_a_time"]["value"]
     return line
 
@@ -558,6 +586,11 @@ def main():
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream sub-measurement")
     ap.add_argument("--serve-window", type=float, default=0.0,
                     help="arrival window in seconds (default: 60 for --workload served, 20 in the main line)")
+    ap.add_argument("--serve-slots", type=int, default=16, help="gang requests in flight on the GPU at once")
+    ap.add_argument("--serve-backlog", type=int, default=16,
+                    help="requests waiting for admission at most (arrivals beyond it are refused)")
+    ap.add_argument("--serve-graph-min-n", type=int, default=250000,
+                    help="requests with n >= this take the server's graph lane (0: gangs only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -583,7 +616,7 @@ def main():
         clocks = Clocks(local)
         clocks.start()
         window = args.serve_window or 60.0
-        sl = run_served(args, pkg, torch, local, dist, window, drain_s=120.0, one_at_a_time=8)
+        sl = run_served(args, pkg, torch, local, dist, window, drain_s=120.0, oaat_budget_s=300.0)
         clk = clocks.stop()
         line = {"metric": sl["metric"], "value": sl["value"], "unit": sl["unit"], "n_gpus": ws, "steps": 1,
                 "warmup": 0, "ms_per_step": 1e3 * sl["wall_s"], "higher_is_better": True, "scaling": "weak",
@@ -750,7 +783,7 @@ def main():
         line["precision"] = run_precision(args, pkg, torch, local, dist)
     if not args.no_served:
         line["served"] = run_served(args, pkg, torch, local, dist, args.serve_window or 20.0, drain_s=30.0,
-                                    one_at_a_time=4)
+                                    oaat_budget_s=40.0)
     if not args.no_batched:
         bl = run_batched(args, pkg, torch, local, dist)
         line["batched"] = {k: bl[k] for k in ("metric", "value", "unit", "ms_per_step", "arnoldi_steps_per_s",

@@ -69,6 +69,12 @@ typedef struct {
     int fp32_basis;     /* nonzero: also allocate an FP32 Krylov basis and FP32 copy of A's
                            values (4 (n+32)(m+2) + 4 nnz bytes more), which solves with
                            precision = IGS_PREC_FP32_IR require                             */
+    int stream_alloc;   /* nonzero: the context's device memory comes from the device's
+                           stream-ordered pool (cudaMallocAsync on the context's stream) and
+                           igs_destroy returns it with cudaFreeAsync, so that neither call
+                           waits for work on other streams (cudaFree would).  Needs a given
+                           A_norm2 > 0 for the guarantee (the estimate's scratch is not
+                           pooled)                                                          */
 } igs_create_opts;
 
 /* Arithmetic of igs_solve's Arnoldi cycles. */

@@ -9,9 +9,11 @@
  * How the server works
  *  - Submitting copies the request to the host side of the server; nothing waits on the GPU.
  *  - igs_server_pump admits queued requests in arrival order while a launch slot (one CUDA
- *    stream each) is free and the request's device memory fits in the server's arena (the
+ *    stream each) is free, the request's device memory fits in the server's arena (the
  *    "HBM budget": A, b, x, the Krylov basis, the Givens factors and exchange buffers of the
- *    request are carved out of one device allocation made at create).  An admitted request is
+ *    request are carved out of one device allocation made at create), and its gang fits on
+ *    the GPU beside the running gangs (the CTA budget: all running gangs are co-resident at
+ *    once, so a large gang is never starved by smaller ones launched after it).  An admitted request is
  *    copied to the GPU and solved by ONE kernel launch: a cooperative gang of G CTAs (G grows
  *    with n, about rows_per_cta rows per CTA) that runs all cycles on the device, keeping the
  *    basis, the Hessenberg/Givens state and every scalar there.  Requests on different slots
@@ -19,11 +21,16 @@
  *    memory free up.
  *  - The same pump call finds finished requests (CUDA events), copies x to host memory held by
  *    the server, releases their device memory, and queues a completion record.
- *  - A request's result depends only on the request (its matrix, b, x0 and options): it is
- *    bitwise the same alone and in any mix (its gang size is a function of n alone, and no
- *    arithmetic of one request touches another's data).
+ *  - Large requests (n >= graph_min_n, when set) take the graph lane instead: a worker thread
+ *    of the server solves them one at a time with the single-system library of igs.h (its
+ *    whole-GPU kernels are the faster executor for one large system), concurrently with the
+ *    gangs of the other requests.
+ *  - A request's result depends only on the request (its matrix, b, x0 and options) and the
+ *    server's options: it is bitwise the same alone and in any mix (its lane and gang size are
+ *    functions of n, and no arithmetic of one request touches another's data).
  *
- * Calls on one server must be serialised by the caller (one thread drives it).  Status codes
+ * Calls on one server must be serialised by the caller (one thread drives it; the graph lane's
+ * worker is internal and synchronised with the calls).  Status codes
  * are the IGS_* codes of igs.h; IGS_ETIMEOUT in a completion means the request's gang could
  * not synchronise within its bounded wait (no GPU hang: every wait in the kernel is bounded).
  */
@@ -46,11 +53,16 @@ typedef struct {
     int device;             /* CUDA device ordinal                                           */
     int max_restart_m;      /* largest restart length of any request, 1..IGS_SERVE_MAX_M      */
     int64_t arena_bytes;    /* device memory for admitted requests (the admission budget)    */
-    int slots;              /* requests in flight at once (one stream each), 1..64; 0: 8      */
+    int slots;              /* requests in flight at once (one stream each), 1..256; 0: 8     */
     int rows_per_cta;       /* target rows per CTA of a request's gang (>= 256, multiple of
                                32); 0: 4096                                                  */
     int max_queue;          /* requests waiting for admission at most; a submit beyond it is
                                refused with IGS_ENOMEM ("queue full").  0: no limit          */
+    int64_t graph_min_n;    /* requests with n >= graph_min_n take the graph lane: one at a
+                               time, on a worker thread of the server, through igs_create /
+                               igs_solve (igs.h: whole-GPU kernels, graph-captured cycles,
+                               pooled device memory outside the arena), beside the gangs.
+                               0: no graph lane                                              */
 } igs_server_opts;
 
 typedef struct {
@@ -80,7 +92,11 @@ typedef struct {
     int64_t device_bytes;   /* arena bytes the request held                                   */
     double t_submit, t_admit, t_done;  /* server clock (seconds since create): submitted,
                                launched, and found finished by igs_server_pump               */
+    int path;               /* IGS_SERVE_PATH_GANG or IGS_SERVE_PATH_GRAPH (gang_ctas is 0 and
+                               device_bytes the context's memory on the graph lane)          */
 } igs_completion;
+
+enum { IGS_SERVE_PATH_GANG = 0, IGS_SERVE_PATH_GRAPH = 1 };
 
 typedef struct {
     int64_t submitted, queued, running, completed;

@@ -26,6 +26,7 @@ struct igs_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;  // user-visible ordering stream
     bool own_stream = false;
+    bool stream_alloc = false;  // device memory from the stream-ordered pool
     cudaStream_t cap = nullptr;     // private capture stream
     cudaStream_t side = nullptr;    // private side stream (Givens branch during capture)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -78,12 +79,15 @@ int dalloc(igs_ctx *ctx, T **p, size_t count)
 {
     void *q = nullptr;
     const size_t bytes = sizeof(T) * (count > 0 ? count : 1);
-    cudaError_t e = cudaMalloc(&q, bytes);
+    cudaError_t e = ctx->stream_alloc ? cudaMallocAsync(&q, bytes, ctx->stream) : cudaMalloc(&q, bytes);
     if (e != cudaSuccess)
         return fail(ctx, IGS_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
-    e = cudaMemset(q, 0, bytes);
+    e = ctx->stream_alloc ? cudaMemsetAsync(q, 0, bytes, ctx->stream) : cudaMemset(q, 0, bytes);
     if (e != cudaSuccess) {
-        cudaFree(q);
+        if (ctx->stream_alloc)
+            cudaFreeAsync(q, ctx->stream);
+        else
+            cudaFree(q);
         return fail(ctx, IGS_ECUDA, "cudaMemset failed: %s", cudaGetErrorString(e));
     }
     ctx->allocs.push_back(q);
@@ -610,7 +614,12 @@ void igs_destroy(igs_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (auto &kv : ctx->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->stream_alloc && ctx->stream) {
+        for (void *p : ctx->allocs) cudaFreeAsync(p, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+    } else {
+        for (void *p : ctx->allocs) cudaFree(p);
+    }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
@@ -688,6 +697,7 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
         }
         ctx->own_stream = true;
     }
+    ctx->stream_alloc = o.stream_alloc != 0;
     if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -741,14 +751,18 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
             (rc = dalloc(ctx, &w.counters, (size_t)((maxblk + igs::kFusedGroup - 1) / igs::kFusedGroup + 1))))
             return bail(rc);
     }
+    // host -> device copies; with pooled memory they follow the allocations on the stream
+    auto upload = [&](void *dst, const void *src, size_t bytes) {
+        if (!ctx->stream_alloc) return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+        cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+        return e == cudaSuccess ? cudaStreamSynchronize(ctx->stream) : e;
+    };
     {
         std::vector<int> rp32((size_t)n + 1);
         for (int64_t i = 0; i <= n; ++i) rp32[(size_t)i] = (int)rowptr[i];
-        cudaError_t e = cudaMemcpy(rp, rp32.data(), sizeof(int) * rp32.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && nnz > 0)
-            e = cudaMemcpy(ci, colind, sizeof(int) * (size_t)nnz, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && nnz > 0)
-            e = cudaMemcpy(va, vals, sizeof(double) * (size_t)nnz, cudaMemcpyHostToDevice);
+        cudaError_t e = upload(rp, rp32.data(), sizeof(int) * rp32.size());
+        if (e == cudaSuccess && nnz > 0) e = upload(ci, colind, sizeof(int) * (size_t)nnz);
+        if (e == cudaSuccess && nnz > 0) e = upload(va, vals, sizeof(double) * (size_t)nnz);
         if (e != cudaSuccess) {
             fail(ctx, IGS_ECUDA, "copying A: %s", cudaGetErrorString(e));
             return bail(IGS_ECUDA);
@@ -764,8 +778,7 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
             return bail(rc);
         std::vector<float> v32((size_t)(nnz > 0 ? nnz : 1));
         for (int64_t q = 0; q < nnz; ++q) v32[(size_t)q] = (float)vals[q];
-        cudaError_t e = nnz > 0 ? cudaMemcpy(w.val32, v32.data(), sizeof(float) * (size_t)nnz, cudaMemcpyHostToDevice)
-                                : cudaSuccess;
+        cudaError_t e = nnz > 0 ? upload(w.val32, v32.data(), sizeof(float) * (size_t)nnz) : cudaSuccess;
         if (e != cudaSuccess) {
             fail(ctx, IGS_ECUDA, "copying A (FP32): %s", cudaGetErrorString(e));
             return bail(IGS_ECUDA);

@@ -17,6 +17,10 @@
 #include <deque>
 #include <map>
 #include <string>
+#include <condition_variable>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -119,8 +123,25 @@ struct ResultBlock {
     int cycles;
 };
 
+// A request on the graph lane: its own copies of the inputs, and the results the worker
+// thread writes (only the worker touches a job between hand-over and completion).
+struct GraphJob {
+    int64_t id = 0;
+    igs_request opt{};
+    double normA = 0.0;
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> colind;
+    std::vector<double> vals, b, x0, x;
+    int status = IGS_OK;
+    double beta = 0.0;
+    int64_t steps = 0, device_bytes = 0;
+    int cycles = 0;
+};
+
 struct Request {
     int64_t id = 0;
+    bool graph = false;  // runs on the graph lane (whole-GPU kernels, one request at a time)
+    std::unique_ptr<GraphJob> job;
     igs_request opt{};
     int n = 0, n2 = 0, ldv = 0, G = 1, chunk = 32, nslices = 0;
     bool f32 = false, has_x0 = false;
@@ -162,6 +183,19 @@ struct igs_server {
     std::deque<int64_t> completions;
     int64_t next_id = 1, submitted = 0, completed = 0, launches = 0;
     int max_gang[2] = {1, 1};       // largest co-resident gang (FP64, FP32 kernels)
+    int cta_budget = 1;             // CTAs of all running gangs at most (all co-resident at once)
+    int running_ctas = 0;
+    // graph lane: requests with n >= graph_min_n, solved one at a time by a worker thread
+    // through igs_create/igs_solve (the whole-GPU kernels and CUDA graphs of igs.h)
+    int64_t graph_min_n = 0;
+    std::deque<int64_t> graph_queue;       // waiting for the lane (FIFO)
+    int64_t graph_busy = -1;               // request on the lane, -1: idle
+    std::thread graph_thread;
+    std::mutex graph_mu;
+    std::condition_variable graph_cv;
+    std::unique_ptr<igs::serve::GraphJob> graph_in, graph_out;  // hand-over / finished (under graph_mu)
+    bool graph_stop = false;
+    cudaStream_t graph_stream = nullptr;
     size_t smem_max[2] = {0, 0};
     std::chrono::steady_clock::time_point t0;
     std::string err;
@@ -274,9 +308,87 @@ int launch_request(igs_server *s, Request &r, cudaStream_t st)
     return IGS_OK;
 }
 
-// Finished slots: collect results, release memory.
+// One graph-lane request through the single-system library on the lane's stream (pooled
+// device memory, so that creating and destroying the context never waits for the gangs).
+void run_graph_job(igs_server *s, igs::serve::GraphJob &j)
+{
+    const igs_request &q = j.opt;
+    j.x.assign((size_t)q.n, 0.0);
+    igs_create_opts co{};
+    co.stream = s->graph_stream;
+    co.device = s->device;
+    co.max_restart_m = q.restart_m;
+    co.A_norm2 = j.normA;
+    co.fp32_basis = q.precision == IGS_PREC_FP32_IR;
+    co.stream_alloc = 1;
+    igs_ctx *ctx = nullptr;
+    int rc = igs_create(&ctx, q.n, q.nnz, j.rowptr.data(), j.colind.data(), j.vals.data(), &co);
+    if (rc != IGS_OK) {
+        j.status = rc;
+        return;
+    }
+    igs_info info{};
+    if (igs_get_info(ctx, &info) == IGS_OK) j.device_bytes = info.device_bytes;
+    igs_solve_opts so{};
+    so.restart_m = q.restart_m;
+    so.gs_iters = q.gs_iters;
+    so.tol_beta = q.tol_beta;
+    so.max_restarts = q.max_restarts;
+    so.inputs_on_device = 0;
+    so.precision = q.precision;
+    so.inner_tol = q.inner_tol;
+    so.method = IGS_METHOD_IGS;
+    igs_result res{};
+    res.x = j.x.data();
+    rc = igs_solve(ctx, j.b.data(), j.x0.empty() ? nullptr : j.x0.data(), &so, &res);
+    j.status = rc;
+    j.beta = res.beta;
+    j.steps = res.steps;
+    j.cycles = res.cycles;
+    igs_destroy(ctx);
+}
+
+// The graph lane's worker thread: takes the handed-over job, solves it, hands it back.
+void graph_worker(igs_server *s)
+{
+    cudaSetDevice(s->device);
+    for (;;) {
+        std::unique_ptr<igs::serve::GraphJob> job;
+        {
+            std::unique_lock<std::mutex> lk(s->graph_mu);
+            s->graph_cv.wait(lk, [&] { return s->graph_stop || s->graph_in != nullptr; });
+            if (s->graph_stop) return;
+            job = std::move(s->graph_in);
+        }
+        run_graph_job(s, *job);
+        std::lock_guard<std::mutex> lk(s->graph_mu);
+        s->graph_out = std::move(job);
+    }
+}
+
+// Finished requests: collect results, release memory.
 int collect(igs_server *s)
 {
+    std::unique_ptr<igs::serve::GraphJob> fin;
+    {
+        std::lock_guard<std::mutex> lk(s->graph_mu);
+        fin = std::move(s->graph_out);
+    }
+    if (fin) {
+        Request &r = s->reqs[fin->id];
+        r.status = fin->status;
+        r.res.status = fin->status;
+        r.res.beta = fin->beta;
+        r.res.steps = fin->steps;
+        r.res.cycles = fin->cycles;
+        r.bytes = fin->device_bytes;
+        r.x_host = std::move(fin->x);
+        r.t_done = now_s(s);
+        r.done = true;
+        s->graph_busy = -1;
+        s->completions.push_back(r.id);
+        s->completed++;
+    }
     for (int k = 0; k < s->slots; ++k) {
         const int64_t id = s->slot_req[(size_t)k];
         if (id < 0) continue;
@@ -300,6 +412,7 @@ int collect(igs_server *s)
         }
         r.t_done = now_s(s);
         r.done = true;
+        s->running_ctas -= r.G;
         s->arena.release(r.arena_off, r.bytes);
         r.arena_off = -1;
         s->slot_req[(size_t)k] = -1;
@@ -309,9 +422,24 @@ int collect(igs_server *s)
     return IGS_OK;
 }
 
-// Admit queued requests (FIFO) while a slot is free and the arena has room.
+// Admit queued requests (FIFO) while a slot is free, the arena has room and the request's
+// gang fits beside the running ones (the CTA budget: every admitted gang is co-resident at
+// once, so no cooperative launch waits for SMs that later, smaller gangs could take first).
 int admit(igs_server *s)
 {
+    if (s->graph_busy < 0 && !s->graph_queue.empty()) {
+        const int64_t id = s->graph_queue.front();
+        s->graph_queue.pop_front();
+        Request &r = s->reqs[id];
+        {
+            std::lock_guard<std::mutex> lk(s->graph_mu);
+            s->graph_in = std::move(r.job);
+        }
+        s->graph_cv.notify_one();
+        s->graph_busy = id;
+        s->launches++;
+        r.t_admit = now_s(s);
+    }
     while (!s->queue.empty()) {
         int k = -1;
         for (int j = 0; j < s->slots; ++j)
@@ -321,6 +449,7 @@ int admit(igs_server *s)
             }
         if (k < 0) return IGS_OK;
         Request &r = s->reqs[s->queue.front()];
+        if (s->running_ctas + r.G > s->cta_budget) return IGS_OK;
         int64_t off = 0;
         if (!s->arena.alloc(r.bytes, &off)) return IGS_OK;
         r.arena_off = off;
@@ -342,6 +471,7 @@ int admit(igs_server *s)
         cudaError_t e = cudaEventRecord(s->events[(size_t)k], st);
         if (e != cudaSuccess) return sfail(s, IGS_ECUDA, "event record", e);
         s->launches++;
+        s->running_ctas += r.G;
         r.t_admit = now_s(s);
         // host copies are on the device now
         std::vector<int64_t>().swap(r.sell_off);
@@ -370,7 +500,7 @@ int igs_server_create(igs_server **out, const igs_server_opts *opts)
         return IGS_EINVAL;
     const int slots = opts->slots > 0 ? opts->slots : 8;
     const int rpc = opts->rows_per_cta > 0 ? opts->rows_per_cta : 4096;
-    if (slots > 64 || rpc < 256 || rpc % 32 != 0) return IGS_EINVAL;
+    if (slots > 256 || rpc < 256 || rpc % 32 != 0 || opts->graph_min_n < 0) return IGS_EINVAL;
     igs_server *s = new (std::nothrow) igs_server();
     if (!s) return IGS_ENOMEM;
     auto bail = [&](int code) {
@@ -382,6 +512,7 @@ int igs_server_create(igs_server **out, const igs_server_opts *opts)
     s->slots = slots;
     s->rows_per_cta = rpc;
     s->max_queue = opts->max_queue > 0 ? opts->max_queue : 0;
+    s->graph_min_n = opts->graph_min_n;
     s->t0 = std::chrono::steady_clock::now();
     if (cudaSetDevice(s->device) != cudaSuccess) return bail(IGS_ECUDA);
     cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -403,6 +534,7 @@ int igs_server_create(igs_server **out, const igs_server_opts *opts)
             return bail(IGS_ECUDA);
         s->max_gang[t] = std::max(1, nb) * s->num_sms;
     }
+    s->cta_budget = std::min(s->max_gang[0], s->max_gang[1]);
     if (cudaMalloc(reinterpret_cast<void **>(&s->arena_base), (size_t)opts->arena_bytes) != cudaSuccess)
         return bail(IGS_ENOMEM);
     s->arena.init(opts->arena_bytes);
@@ -413,6 +545,14 @@ int igs_server_create(igs_server **out, const igs_server_opts *opts)
         if (cudaStreamCreateWithFlags(&s->streams[(size_t)k], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&s->events[(size_t)k], cudaEventDisableTiming) != cudaSuccess)
             return bail(IGS_ECUDA);
+    if (s->graph_min_n > 0) {
+        if (cudaStreamCreateWithFlags(&s->graph_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(IGS_ECUDA);
+        try {
+            s->graph_thread = std::thread(graph_worker, s);
+        } catch (...) {
+            return bail(IGS_ENOMEM);
+        }
+    }
     *out = s;
     return IGS_OK;
 }
@@ -420,7 +560,18 @@ int igs_server_create(igs_server **out, const igs_server_opts *opts)
 void igs_server_destroy(igs_server *s)
 {
     if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->graph_mu);
+        s->graph_stop = true;
+        s->graph_in.reset();
+    }
+    s->graph_cv.notify_all();
+    if (s->graph_thread.joinable()) s->graph_thread.join();  // a running graph-lane solve ends first
     cudaSetDevice(s->device);
+    if (s->graph_stream) {
+        cudaStreamSynchronize(s->graph_stream);
+        cudaStreamDestroy(s->graph_stream);
+    }
     for (auto st : s->streams)
         if (st) cudaStreamSynchronize(st);
     for (auto st : s->streams)
@@ -445,7 +596,8 @@ int igs_server_submit(igs_server *s, const igs_request *q, int64_t *id_out)
         (q->precision != IGS_PREC_FP64 && q->precision != IGS_PREC_FP32_IR))
         return sfail(s, IGS_EINVAL, "bad request options");
     if (q->rowptr[0] != 0 || q->rowptr[n] != nnz) return sfail(s, IGS_EINVAL, "rowptr[0] must be 0, rowptr[n] = nnz");
-    if (s->max_queue > 0 && (int64_t)s->queue.size() >= s->max_queue) return sfail(s, IGS_ENOMEM, "queue full");
+    if (s->max_queue > 0 && (int64_t)(s->queue.size() + s->graph_queue.size()) >= s->max_queue)
+        return sfail(s, IGS_ENOMEM, "queue full");
     std::vector<double> rowabs((size_t)n, 0.0), colabs((size_t)n, 0.0);
     for (int64_t i = 0; i < n; ++i) {
         if (q->rowptr[i + 1] < q->rowptr[i]) return sfail(s, IGS_EINVAL, "rowptr decreases");
@@ -477,11 +629,40 @@ int igs_server_submit(igs_server *s, const igs_request *q, int64_t *id_out)
         const double ninf = *std::max_element(rowabs.begin(), rowabs.end());
         r.normA = std::sqrt(n1 * ninf);
     }
-    // gang: about rows_per_cta rows per CTA, rows split on multiples of 32
+    if (s->graph_min_n > 0 && n >= s->graph_min_n) {
+        // graph lane: the library solves it with whole-GPU kernels; keep the CSR form
+        auto job = std::make_unique<igs::serve::GraphJob>();
+        job->id = r.id;
+        job->opt = r.opt;
+        job->opt.colind = nullptr;
+        job->opt.vals = nullptr;
+        job->opt.b = nullptr;
+        job->opt.x0 = nullptr;
+        job->normA = r.normA;
+        job->rowptr.assign(q->rowptr, q->rowptr + n + 1);
+        job->colind.assign(q->colind, q->colind + nnz);
+        job->vals.assign(q->vals, q->vals + nnz);
+        job->b.assign(q->b, q->b + n);
+        if (r.has_x0) job->x0.assign(q->x0, q->x0 + n);
+        r.graph = true;
+        r.G = 0;
+        r.job = std::move(job);
+        r.t_submit = now_s(s);
+        const int64_t id = r.id;
+        s->reqs.emplace(id, std::move(r));
+        s->graph_queue.push_back(id);
+        s->submitted++;
+        *id_out = id;
+        return IGS_OK;
+    }
+    // gang: about rows_per_cta rows per CTA, rows split on multiples of 32.  A gang of more
+    // CTAs than SMs is rounded up to a whole number of CTAs per SM (within the CTA budget),
+    // so that when it runs alone no SM carries more of its rows than another.
     int G = (r.n2 + s->rows_per_cta - 1) / s->rows_per_cta;
+    if (G > s->num_sms) G = std::min((G + s->num_sms - 1) / s->num_sms * s->num_sms, std::max(G, s->cta_budget));
     int chunk = ((r.n2 + G - 1) / G + 31) / 32 * 32;
     G = (r.n2 + chunk - 1) / chunk;
-    if (G > s->max_gang[r.f32 ? 1 : 0]) return sfail(s, IGS_EINVAL, "system too large for one co-resident gang");
+    if (G > s->cta_budget) return sfail(s, IGS_EINVAL, "system too large for one co-resident gang");
     r.G = G;
     r.chunk = chunk;
     r.smem = r.f32 ? sizeof(double) * (size_t)sysdev::smem_layout<float>(chunk, r.opt.restart_m).total
@@ -527,7 +708,7 @@ int igs_server_pump(igs_server *s, int *running)
     int rc = collect(s);
     if (rc == IGS_OK) rc = admit(s);
     if (running) {
-        int k = 0;
+        int k = s->graph_busy >= 0 ? 1 : 0;
         for (auto id : s->slot_req) k += id >= 0;
         *running = k;
     }
@@ -550,6 +731,7 @@ int igs_server_poll(igs_server *s, igs_completion *out, int max_out, int *n_out)
         c.cycles = r.res.cycles;
         c.gang_ctas = r.G;
         c.device_bytes = r.bytes;
+        c.path = r.graph ? IGS_SERVE_PATH_GRAPH : IGS_SERVE_PATH_GANG;
         c.t_submit = r.t_submit;
         c.t_admit = r.t_admit;
         c.t_done = r.t_done;
@@ -574,7 +756,8 @@ int igs_server_get_stats(const igs_server *s, igs_server_stats *o)
     if (!s || !o) return IGS_EINVAL;
     std::memset(o, 0, sizeof(*o));
     o->submitted = s->submitted;
-    o->queued = (int64_t)s->queue.size();
+    o->queued = (int64_t)(s->queue.size() + s->graph_queue.size());
+    o->running = s->graph_busy >= 0 ? 1 : 0;
     for (auto id : s->slot_req) o->running += id >= 0;
     o->completed = s->completed;
     o->arena_bytes = s->arena.size();

@@ -52,7 +52,7 @@ def test_server_rejects_bad_options_before_touching_the_device(lib):
     import paper_2205_07805_gb300 as pkg
     h = C.c_void_p()
     for opts in [(0, 0, 1 << 20, 0, 0, 0), (0, 200, 1 << 20, 0, 0, 0), (0, 50, 0, 0, 0, 0),
-                 (0, 50, 1 << 20, 65, 0, 0), (0, 50, 1 << 20, 0, 100, 0)]:
+                 (0, 50, 1 << 20, 257, 0, 0), (0, 50, 1 << 20, 0, 100, 0), (0, 50, 1 << 20, 0, 0, 0, -1)]:
         o = pkg._ServerOpts(*opts)
         assert lib.igs_server_create(C.byref(h), C.byref(o)) == -1 and not h.value
     assert lib.igs_server_create(None, None) == -1

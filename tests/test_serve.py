@@ -120,3 +120,43 @@ def test_numeric_error_is_isolated(pkg):
         done = {c["id"]: c for c in sv.run_all()}
     assert done[ids[1]]["status"] == pkg.ENUMERIC
     assert done[ids[0]]["status"] == 0 and done[ids[2]]["status"] == 0
+
+
+@pytest.mark.gpu
+def test_graph_lane_requests_match_oracle_and_mix(pkg):
+    """Requests with n >= graph_min_n run on the graph lane (the whole-GPU kernels of igs.h,
+    one at a time on the server's worker thread) beside gang requests: FP64 against the
+    oracle as above, FP32-IR to beta <= 1e-14, and the graph request bitwise the same alone
+    and in a mix."""
+    big = [gen.cd2d(side, pe, seed=50 + k)[:2] for k, (side, pe) in enumerate([(52, 30.0), (56, 70.0)])]
+    small = _cases()[:3]
+    norms_big = [gen.norm2_power(A, iters=100) for A, _ in big]
+    norms_small = [gen.norm2_power(A, iters=100) for A, _ in small]
+    gmin = 2500                   # the two grids (n = 2704, 3136); the small cases have n <= 2304
+    with pkg.Server(max_restart_m=40, arena_bytes=1 << 30, slots=3, rows_per_cta=512, graph_min_n=gmin) as sv:
+        ids_b = [sv.submit(A, b, A_norm2=nA, m=40, gs=2, tol=1e-12, max_restarts=200)
+                 for (A, b), nA in zip(big, norms_big)]
+        id_f = sv.submit(big[0][0], big[0][1], A_norm2=norms_big[0], m=40, gs=2, tol=1e-14, max_restarts=100,
+                         precision="fp32_ir")
+        ids_s = [sv.submit(A, b, A_norm2=nA, m=40, gs=2, tol=1e-12, max_restarts=200)
+                 for (A, b), nA in zip(small, norms_small)]
+        done = {c["id"]: c for c in sv.run_all()}
+        xs = {rid: sv.take(rid) for rid in ids_b + [id_f] + ids_s}
+    for rid, (A, b), nA in zip(ids_b, big, norms_big):
+        c = done[rid]
+        assert c["path"] == 1 and c["gang_ctas"] == 0
+        o = oracle.gmres(A, b, m=40, gs=2, tol=1e-12, max_cycles=200, normA=nA)
+        assert c["status"] == o["status"] == 0 and abs(c["steps"] - o["steps"]) <= 2, (c, o["steps"])
+        assert np.linalg.norm(xs[rid] - o["x"]) <= 1e-8 * np.linalg.norm(o["x"])
+    c = done[id_f]
+    o = oracle.gmres(big[0][0], big[0][1], m=40, gs=2, tol=1e-14, max_cycles=100, normA=norms_big[0])
+    assert c["path"] == 1 and c["status"] == 0 and c["beta"] <= 1e-14
+    assert np.linalg.norm(xs[id_f] - o["x"]) <= 1e-10 * np.linalg.norm(o["x"])
+    for rid in ids_s:
+        assert done[rid]["path"] == 0 and done[rid]["status"] == 0
+    with pkg.Server(max_restart_m=40, arena_bytes=1 << 30, slots=1, rows_per_cta=512, graph_min_n=gmin) as sv:
+        rid = sv.submit(big[1][0], big[1][1], A_norm2=norms_big[1], m=40, gs=2, tol=1e-12, max_restarts=200)
+        alone = {c["id"]: c for c in sv.run_all()}[rid]
+        x_alone = sv.take(rid)
+    assert alone["steps"] == done[ids_b[1]]["steps"] and alone["beta"] == done[ids_b[1]]["beta"]
+    assert np.array_equal(x_alone, xs[ids_b[1]])

@@ -7,7 +7,8 @@ Arnoldi columns, Givens least squares, x update and the true backward error), i.
 Arnoldi steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--gs 1|2] [--impl reference]
-                  [--workload cd2d|batched] [--no-batched]
+                  [--workload cd2d|batched|precision|served] [--no-batched] [--no-precision]
+                  [--no-served] [--serve-slots S] [--serve-backlog Q] [--serve-graph-min-n N]
 
 Prints one JSON line (rank 0).  `value` is device-timed throughput with b already in HBM
 (CUDA events on the library's stream); `e2e` is the same metric through the C interface
@@ -22,8 +23,10 @@ workload and cycles; `precision`: the FP32-basis form inside FP64 iterative refi
 against the FP64 form on the 160^3 convection-diffusion system (n = 4.1M, m = 200) to
 beta <= 1e-14, with the FP32 multi-dot's HBM roofline; `served`: a Poisson stream of
 2-D convection-diffusion requests (2000/s, sides 64..1024) replayed against the request
-server (include/igs_serve.h) for a 20 s window (60 s with --workload served), with served
-solves/s, p50/p99 latency and the refused backlog; and `batched`: the batched form (include/igs_batch.h) on 4096 banded
+server (include/igs_serve.h: gangs, plus the graph lane for n >= --serve-graph-min-n) for a
+20 s window (60 s with --workload served), with served solves/s, p50/p99 latency, the
+refused backlog, and the same completed requests solved one at a time through igs_solve
+(FP64) for comparison; and `batched`: the batched form (include/igs_batch.h) on 4096 banded
 systems (n ~ U{64..2048}, 7 diagonals, m = 50, every system to beta <= 1e-12) in solves/s,
 its FP64 roofline, and the same systems solved one at a time by igs_solve (a sample) for
 comparison.  `--workload batched` prints that measurement as the main line instead.

@@ -136,6 +136,16 @@ double igs_server_clock(const igs_server *srv);
 
 const char *igs_server_last_error(const igs_server *srv);
 
+/* Self-test of the gangs' bounded waits (no server needed).  Launches a cooperative gang of
+ * G CTAs (2 <= G <= the SM count) on `device` through four of the solver's gang barriers.
+ * stall = 0: they complete; returns IGS_OK.  stall = 1: the barrier's arrival counter
+ * starts at a value no arrival brings to G (a flag nothing sets), so every CTA's wait runs
+ * out after its bound (a few seconds), raises the gang's abort flag and returns; the call then
+ * returns IGS_ETIMEOUT with *abort_out = 1 (nullable) and the device stays usable.  This is
+ * how the timeout path is tested without faulting or hanging a GPU.  Errors: IGS_EINVAL,
+ * IGS_ECUDA. */
+int igs_server_gang_selftest(int device, int G, int stall, int *abort_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,7 +34,8 @@ EXPORTED_BATCH_SYMBOLS = ["igs_batch_create", "igs_batch_destroy", "igs_batch_so
 # Every function declared in include/igs_serve.h.
 EXPORTED_SERVE_SYMBOLS = ["igs_server_create", "igs_server_destroy", "igs_server_submit",
                           "igs_server_pump", "igs_server_poll", "igs_server_take_result",
-                          "igs_server_get_stats", "igs_server_clock", "igs_server_last_error"]
+                          "igs_server_get_stats", "igs_server_clock", "igs_server_last_error",
+                          "igs_server_gang_selftest"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -212,6 +213,8 @@ def load_library(path: str | None = None):
     lib.igs_server_clock.restype = dbl
     lib.igs_server_last_error.argtypes = [vp]
     lib.igs_server_last_error.restype = C.c_char_p
+    lib.igs_server_gang_selftest.argtypes = [i32, i32, i32, C.POINTER(i32)]
+    lib.igs_server_gang_selftest.restype = i32
     if path is None:
         _lib = lib
     return lib

@@ -62,6 +62,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_serve_solve(ServeArgs<T> a)
     sysdev::d_solve<T>(a.sys, gg, sm, L, sh);
 }
 
+// Four gang barriers of the solver (igs_server_gang_selftest); ok[g] = 1 if CTA g passed
+// them all, 0 if its bounded wait gave up or saw another CTA's abort.
+__global__ void __launch_bounds__(kThreads) k_gang_selftest(sysdev::GangSync *sync, int *ok)
+{
+    __shared__ sysdev::Shared sh;
+    if (threadIdx.x == 0) sysdev::init_shared(sh);
+    __syncthreads();
+    sysdev::Gang gg{};
+    gg.G = gridDim.x;
+    gg.g = blockIdx.x;
+    gg.sync = sync;
+    bool pass = true;
+    for (int r = 0; r < 4 && pass; ++r) pass = sysdev::gang_barrier(gg, sh);
+    if (threadIdx.x == 0) ok[blockIdx.x] = pass ? 1 : 0;
+}
+
 // First-fit allocator over [0, size) with coalescing free ranges (256-byte granules).
 class Arena {
 public:
@@ -768,6 +784,44 @@ int igs_server_get_stats(const igs_server *s, igs_server_stats *o)
 }
 
 double igs_server_clock(const igs_server *s) { return s ? now_s(s) : 0.0; }
+
+int igs_server_gang_selftest(int device, int G, int stall, int *abort_out)
+{
+    using namespace igs;
+    if (G < 2 || (stall != 0 && stall != 1)) return IGS_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return IGS_ECUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || G > sms)
+        return IGS_EINVAL;
+    sysdev::GangSync *sync = nullptr;
+    int *ok = nullptr;
+    cudaStream_t st = nullptr;
+    int rc = IGS_ECUDA;
+    std::vector<int> h((size_t)G, 0);
+    sysdev::GangSync hs{};
+    // stalled: an arrival count that no arrival brings to G, so that every wait runs out
+    hs.count = stall ? 0x40000000u : 0u;
+    if (cudaMalloc(&sync, sizeof(sysdev::GangSync)) == cudaSuccess && cudaMalloc(&ok, sizeof(int) * G) == cudaSuccess &&
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaMemcpyAsync(sync, &hs, sizeof(hs), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+        cudaMemsetAsync(ok, 0, sizeof(int) * G, st) == cudaSuccess) {
+        void *args[] = {&sync, &ok};
+        if (cudaLaunchCooperativeKernel(reinterpret_cast<void *>(serve::k_gang_selftest), dim3(G),
+                                        dim3(serve::kThreads), args, 0, st) == cudaSuccess &&
+            cudaMemcpyAsync(h.data(), ok, sizeof(int) * G, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaMemcpyAsync(&hs, sync, sizeof(hs), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess) {
+            int passed = 0;
+            for (int v : h) passed += v;
+            if (abort_out) *abort_out = hs.abort;
+            rc = passed == G ? IGS_OK : IGS_ETIMEOUT;
+        }
+    }
+    if (st) cudaStreamDestroy(st);
+    cudaFree(ok);
+    cudaFree(sync);
+    return rc;
+}
 
 const char *igs_server_last_error(const igs_server *s) { return s ? s->err.c_str() : "null server"; }
 

@@ -37,7 +37,7 @@ namespace sysdev {
 constexpr int kMaxM = 128;          // largest restart length (four rows per lane in warp solves)
 constexpr int kMaxSlices = 16;      // dot products over at most this many slices per CTA
 constexpr int kRowAlign = 32;       // gang row ranges start on multiples of 32 rows
-constexpr long long kSpinLimit = 1ll << 24;  // bounded gang waits (x ~100 ns)
+constexpr long long kSpinLimit = 1ll << 22;  // bounded gang waits: a few seconds (3.2 s measured)
 
 __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 

@@ -56,6 +56,8 @@ def test_server_rejects_bad_options_before_touching_the_device(lib):
         o = pkg._ServerOpts(*opts)
         assert lib.igs_server_create(C.byref(h), C.byref(o)) == -1 and not h.value
     assert lib.igs_server_create(None, None) == -1
+    assert lib.igs_server_gang_selftest(0, 1, 0, None) == -1      # a gang has >= 2 CTAs
+    assert lib.igs_server_gang_selftest(0, 4, 2, None) == -1      # stall is 0 or 1
     lib.igs_server_destroy(None)
     assert lib.igs_server_submit(None, None, None) == -1
     assert lib.igs_server_pump(None, None) == -1

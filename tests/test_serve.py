@@ -5,6 +5,9 @@ Tolerances as in the batched and precision forms: converged FP64 requests have t
 status, step counts within +-2 and x within 1e-8 (relative); FP32-IR requests reach
 beta <= tol with x within 1e-10 of the oracle's FP64 solution at tol = 1e-14.
 """
+import ctypes as C
+import time
+
 import numpy as np
 import pytest
 
@@ -160,3 +163,25 @@ def test_graph_lane_requests_match_oracle_and_mix(pkg):
         x_alone = sv.take(rid)
     assert alone["steps"] == done[ids_b[1]]["steps"] and alone["beta"] == done[ids_b[1]]["beta"]
     assert np.array_equal(x_alone, xs[ids_b[1]])
+
+
+@pytest.mark.gpu
+def test_gang_wait_runs_out_without_a_fault(pkg):
+    """The gangs' bounded waits: with the arrival counter started where no arrival completes
+    the barrier (a flag nothing sets), every CTA's wait gives up, the gang's abort flag is
+    raised and the call reports IGS_ETIMEOUT; the device then still runs gangs and solves."""
+    lib = pkg.load_library()
+    ab = C.c_int(-1)
+    assert lib.igs_server_gang_selftest(0, 8, 0, C.byref(ab)) == 0 and ab.value == 0
+    t0 = time.perf_counter()
+    assert lib.igs_server_gang_selftest(0, 8, 1, C.byref(ab)) == -5 and ab.value == 1
+    waited = time.perf_counter() - t0
+    print(f"stalled gang gave up after {waited:.2f} s")
+    assert waited < 30.0
+    assert lib.igs_server_gang_selftest(0, 8, 0, C.byref(ab)) == 0 and ab.value == 0
+    A, b, _, _ = gen.cd2d(40, 20.0, seed=60)
+    with pkg.Server(max_restart_m=30, arena_bytes=1 << 28, slots=1, rows_per_cta=512) as sv:
+        rid = sv.submit(A, b, m=30, tol=1e-12, max_restarts=100)
+        c = {c["id"]: c for c in sv.run_all()}[rid]
+        sv.take(rid)
+    assert c["status"] == 0 and c["gang_ctas"] > 1

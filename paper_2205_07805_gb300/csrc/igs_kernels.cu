@@ -1029,36 +1029,42 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, 
     const bool f32 = neumann_fp32(a.lfro2[nb - 1], nb, terms);
     stage_lower(a.L, a.ldl, nb, Lsm, f32);
     unit_lower_solve(Lsm, nb, buf, r3s, tmp, terms, f32);
-    // step 14: column nb-1 complete
-    for (int c = t; c < nb; c += blockDim.x) a.H[(int64_t)(nb - 1) * a.ldh + c] = qs[c] + r3s[c];
+    // step 14: column nb-1 complete (also kept in tmp for its norm)
+    for (int c = t; c < nb; c += blockDim.x) {
+        const double h = qs[c] + r3s[c];
+        a.H[(int64_t)(nb - 1) * a.ldh + c] = h;
+        tmp[c] = h;
+    }
     __syncthreads();
-    if (t == 0) {
-        const double g2 = s_g2;
-        int stop = 0;
-        double gam = 0.0, ig = 0.0;
-        if (g2 != g2 || isinf(g2)) {
-            stop = -4;
-        } else {
-            if (g2 > 0.0) {
-                gam = sqrt(g2);
-                ig = 1.0 / gam;
+    if (t < 32) {
+        // warp 0: ||H_{0:nb-1, nb-1}||^2 (fixed shuffle tree), then the scalar step on lane 0
+        // (1/gamma by rsqrt, the breakdown test on squares: no DSQRT or DDIV)
+        double hn2 = 0.0;
+        for (int c = t; c < nb; c += 32) hn2 = fma(tmp[c], tmp[c], hn2);
+        for (int o = 16; o > 0; o >>= 1) hn2 += __shfl_down_sync(0xffffffffu, hn2, o);
+        if (t == 0) {
+            const double g2 = s_g2;
+            int stop = 0;
+            double gam = 0.0, ig = 0.0;
+            if (g2 != g2 || isinf(g2)) {
+                stop = -4;
+            } else {
+                if (g2 > 0.0) {
+                    ig = rsqrt(g2);
+                    gam = g2 * ig;
+                }
+                a.H[(int64_t)(nb - 1) * a.ldh + nb] = gam;
+                if (gam == 0.0 || g2 <= kBreakdownFactor * kBreakdownFactor * hn2) stop = 2;
             }
-            a.H[(int64_t)(nb - 1) * a.ldh + nb] = gam;
-            double hn2 = 0.0;
-            for (int c = 0; c < nb; ++c) {
-                const double h = a.H[(int64_t)(nb - 1) * a.ldh + c];
-                hn2 = fma(h, h, hn2);
+            if (stop != 0) {
+                st->halt = 1;
+                st->stop_reason = stop;
+                st->stop_cols = nb;
             }
-            if (gam == 0.0 || gam <= kBreakdownFactor * sqrt(hn2)) stop = 2;
+            st->inv_gamma = ig;
+            s_ig = ig;
+            s_stop = stop;
         }
-        if (stop != 0) {
-            st->halt = 1;
-            st->stop_reason = stop;
-            st->stop_cols = nb;
-        }
-        st->inv_gamma = ig;
-        s_ig = ig;
-        s_stop = stop;
     }
     __syncthreads();
     if (s_stop != 0) return;
@@ -1089,9 +1095,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, 
     }
     __syncthreads();
     // step 15: q = r^(1) - H_{0:nb, 0:nb-1} r^(3) / gamma
+    for (int c = t; c < nb; c += blockDim.x) r3s[c] *= ig;
+    __syncthreads();
     for (int i = t; i <= nb; i += blockDim.x) {
         double hs = 0.0;
-        for (int c = 0; c < nb; ++c) hs = fma(a.H[(int64_t)c * a.ldh + i], r3s[c] * ig, hs);
+        for (int c = 0; c < nb; ++c) hs = fma(a.H[(int64_t)c * a.ldh + i], r3s[c], hs);
         a.r0v[i] = r1s[i] - hs;
         a.r1v[i] = r1s[i];
     }
@@ -1113,8 +1121,12 @@ k_update_1r(double *V, int64_t ld, int nb, int64_t n, const double *__restrict__
         for (int c = threadIdx.x; c <= nb; c += blockDim.x) s1[c] = r1[c];
     __syncthreads();
     const double ig = st->inv_gamma;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    // block b owns rows [b rpb, (b+1) rpb) (one row per thread with the launcher's grid; this
+    // form measured 7 % faster than the equivalent grid-stride loop)
+    const int64_t rpb = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t i_lo = (int64_t)blockIdx.x * rpb;
+    const int64_t i_hi = i_lo + rpb < n ? i_lo + rpb : n;
+    for (int64_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
         const double *vi = V + i;
         double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
         int c = 0;

@@ -749,6 +749,11 @@ def main():
                 "hbm_frac": bytes_per_launch / avg_s / 1e9 / hbm_peak,
                 "share_of_step": d["ms"] / total_ms if total_ms else None,
                 "kernel_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
+                "per_class": {k: {"hbm_gbs": v["bytes"] / (v["ms"] / 1e3) / 1e9,
+                                  "hbm_frac": v["bytes"] / (v["ms"] / 1e3) / 1e9 / hbm_peak,
+                                  "fp64_tflops": v["flops"] / (v["ms"] / 1e3) / 1e12,
+                                  "fp64_frac": v["flops"] / (v["ms"] / 1e3) / 1e12 / peak_tflops}
+                              for k, v in prof.items() if k in ("spmv", "dots", "update") and v["ms"] > 0},
                 "sm_clock_mhz": sm_clock}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

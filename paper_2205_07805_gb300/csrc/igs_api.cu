@@ -721,6 +721,7 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
         (rc = dalloc(ctx, &w.x, (size_t)w.ld)) || (rc = dalloc(ctx, &w.t, (size_t)w.ld)) ||
         (rc = dalloc(ctx, &w.H, (size_t)(M + 1) * M)) || (rc = dalloc(ctx, &w.R, (size_t)(M + 1) * M)) ||
         (rc = dalloc(ctx, &w.L, (size_t)(M + 1) * (M + 1))) ||
+        (rc = dalloc(ctx, &w.Lrow, (size_t)(M + 1) * M / 2 + 2)) ||
         (rc = dalloc(ctx, &w.Lout, (size_t)(M + 1) * (M + 1))) || (rc = dalloc(ctx, &w.cs, (size_t)M)) ||
         (rc = dalloc(ctx, &w.sn, (size_t)M)) || (rc = dalloc(ctx, &w.g, (size_t)M + 1)) ||
         (rc = dalloc(ctx, &w.lfro2, (size_t)M + 1)) || (rc = dalloc(ctx, &w.r0v, (size_t)M + 1)) ||

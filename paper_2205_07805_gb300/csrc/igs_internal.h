@@ -95,6 +95,7 @@ struct Workspace {
     double *z = nullptr, *u = nullptr, *r = nullptr, *b = nullptr, *x = nullptr, *t = nullptr;
     double *H = nullptr;           // (mmax+1) x mmax column-major, ldh = mmax+1
     double *L = nullptr;           // (mmax+1) x (mmax+1) column-major: L(i,c) at L[c*ldl + i]
+    double *Lrow = nullptr;        // the same, row-packed: L(i,c) at Lrow[i(i-1)/2 + c]
     double *Lout = nullptr;        // (mmax+1)^2 staging for the row-major copy handed out
     double *R = nullptr;           // Givens-rotated copy of H, same layout as H
     double *cs = nullptr, *sn = nullptr, *g = nullptr;  // rotations and rotated rhs

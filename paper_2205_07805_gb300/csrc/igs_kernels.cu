@@ -118,53 +118,38 @@ __device__ __forceinline__ double f32_scaled_to_f64(float y, int e)
     return __longlong_as_double((long long)(sign | (de << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
 }
 
-// Packed strictly-lower triangle of L_p in shared memory: column c holds rows c+1..p-1
-// starting at colstart(c) = c(2p - c - 1)/2.
-__device__ __forceinline__ int packed_col(int c, int p) { return c * (2 * p - c - 1) / 2; }
+// Row-packed strictly-lower triangle of L: row i (columns 0..i-1) starts at i(i-1)/2.  The
+// step kernels keep a global copy in this layout beside the column-major L, so that staging
+// rows 0..r-1 into shared memory is one contiguous copy.
+__device__ __forceinline__ int packed_row(int i) { return i * (i - 1) / 2; }
 
-// Copy rows/columns 0..p-1 of the device L (column-major, Lc[c*ldl + i] = L(i,c)) into the
-// packed shared layout, as FP64, or rounded to FP32 when f32 is set (the FP32 Neumann
-// correction of unit_lower_solve).  The element loop is flattened and keeps eight loads in
-// flight per thread, so the copy costs a few L2 round trips rather than one per column.
-// Ends with a barrier.
-__device__ void stage_lower(const double *__restrict__ Lc, int ldl, int p, double *Lsm, bool f32)
+// Start the copy of rows 0..rows-1 of the row-packed L (global, 16-byte aligned) into Lsm
+// (shared, 16-byte aligned) with 16-byte cp.async chunks; an odd last double is copied by a
+// plain load.  Nothing of Lsm beyond the rows is written.  lower_wait() completes it.
+__device__ void lower_prefetch(const double *__restrict__ Lrow, int rows, double *Lsm)
 {
-    const int T = blockDim.x, t = threadIdx.x;
-    const int total = p * (p - 1) / 2;
-    int c = 0, cstart = 0, clen = p - 1;  // column c occupies [cstart, cstart + clen)
-    for (int e0 = 0; e0 < total; e0 += 8 * T) {
-        double v[8];
-        int dst[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int e = e0 + t + j * T;
-            dst[j] = -1;
-            v[j] = 0.0;
-            if (e < total) {
-                while (e >= cstart + clen) {
-                    cstart += clen;
-                    ++c;
-                    --clen;
-                }
-                v[j] = Lc[(int64_t)c * ldl + c + 1 + (e - cstart)];
-                dst[j] = e;
-            }
-        }
-        float *Lf = reinterpret_cast<float *>(Lsm);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (dst[j] < 0) continue;
-            if (f32)
-                Lf[dst[j]] = f64_scaled_to_f32(v[j], 0);
-            else
-                Lsm[dst[j]] = v[j];
-        }
+    const int total = rows * (rows - 1) / 2;
+    const int chunks = total >> 1;
+    for (int q = threadIdx.x; q < chunks; q += blockDim.x) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(Lsm + 2 * q);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(Lrow + 2 * q) : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    if ((total & 1) && threadIdx.x == blockDim.x - 1) Lsm[total - 1] = Lrow[total - 1];
+}
+
+// Wait for this thread's cp.async copies (before a return that skips lower_wait).
+__device__ __forceinline__ void lower_drain() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Wait for this thread's cp.async copies, then for the block.
+__device__ __forceinline__ void lower_wait()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
 }
 
 // x = (I + L_p)^{-1} rhs for the unit lower-triangular I + L (Alg. 4.1 steps 12 and 15).
-// Lsm is the packed shared copy of L_p (stage_lower).  rhs and x live in shared memory (x
+// Lsm is the row-packed shared copy of L_p (lower_prefetch).  rhs and x live in shared memory (x
 // must not alias rhs; `tmp` is scratch of p entries).  Block-wide.
 //
 // When ||L||_F is small the solve is evaluated as the truncated Neumann series
@@ -175,8 +160,8 @@ __device__ void stage_lower(const double *__restrict__ Lc, int ldl, int p, doubl
 // column-oriented forward substitution runs (terms = 0; see neumann_terms).
 //
 // With f32 set (terms == 2 and (p+2) ||L||_F <= 2^-36, see neumann_fp32) the one correction
-// term L rhs is evaluated in FP32: rhs is scaled by a power of two to [-2, 2), L was staged
-// as FP32, and x = rhs - 2^e (L rhs)_32.  Rounding L, rhs and the length-p sums to FP32 errs
+// term L rhs is evaluated in FP32: rhs is scaled by a power of two to [-2, 2), L's entries are
+// rounded to FP32 as they are read, and x = rhs - 2^e (L rhs)_32.  Rounding L, rhs and the length-p sums to FP32 errs
 // by at most (p+2) 2^-24 ||L||_F ||rhs|| <= 2^-60 ||rhs||, the bound the truncation already
 // meets (entries flushed below the FP32 normal range add at most p 2^-125 max|rhs|), while
 // the FP64 pipe of the one SM running this block would take microseconds for the p^2/2
@@ -203,7 +188,6 @@ __device__ void unit_lower_solve(const double *Lsm, int p, const double *rhs, do
         for (int q = 1; q < T / 32; ++q) emax = max(emax, s_wmax[q]);
         emax = min(emax, 1000);  // a non-finite rhs stays non-finite below
         float *xf = reinterpret_cast<float *>(tmp);
-        const float *Lf = reinterpret_cast<const float *>(Lsm);
         float *yf = xf + p;  // tmp holds 2p floats
         for (int i = t; i < p; i += T) xf[i] = f64_scaled_to_f32(rhs[i], emax);
         __syncthreads();
@@ -218,9 +202,10 @@ __device__ void unit_lower_solve(const double *Lsm, int p, const double *rhs, do
             const int r0 = a, r1 = p - 1 - a;
             float s0 = 0.0f, s1 = 0.0f;
             if (act) {
-                for (int c = h; c < r0; c += tpp) s0 = fmaf(Lf[packed_col(c, p) + r0 - c - 1], xf[c], s0);
+                const double *l0 = Lsm + packed_row(r0), *l1 = Lsm + packed_row(r1);
+                for (int c = h; c < r0; c += tpp) s0 = fmaf(f64_scaled_to_f32(l0[c], 0), xf[c], s0);
                 if (r1 != r0)
-                    for (int c = h; c < r1; c += tpp) s1 = fmaf(Lf[packed_col(c, p) + r1 - c - 1], xf[c], s1);
+                    for (int c = h; c < r1; c += tpp) s1 = fmaf(f64_scaled_to_f32(l1[c], 0), xf[c], s1);
             }
             for (int o = tpp >> 1; o > 0; o >>= 1) {
                 s0 += __shfl_xor_sync(0xffffffffu, s0, o);
@@ -250,9 +235,10 @@ __device__ void unit_lower_solve(const double *Lsm, int p, const double *rhs, do
                 const int r0 = a, r1 = p - 1 - a;
                 double s0 = 0.0, s1 = 0.0;
                 if (act) {
-                    for (int c = h; c < r0; c += 2) s0 = fma(Lsm[packed_col(c, p) + r0 - c - 1], x[c], s0);
+                    const double *l0 = Lsm + packed_row(r0), *l1 = Lsm + packed_row(r1);
+                    for (int c = h; c < r0; c += 2) s0 = fma(l0[c], x[c], s0);
                     if (r1 != r0)
-                        for (int c = h; c < r1; c += 2) s1 = fma(Lsm[packed_col(c, p) + r1 - c - 1], x[c], s1);
+                        for (int c = h; c < r1; c += 2) s1 = fma(l1[c], x[c], s1);
                 }
                 s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
                 s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
@@ -279,11 +265,10 @@ __device__ void unit_lower_solve(const double *Lsm, int p, const double *rhs, do
         if ((c % T) == t) x[c] = xi[c / T];
         __syncthreads();
         const double xc = x[c];
-        const double *Lcol = Lsm + packed_col(c, p) - c - 1;  // Lcol[i] = L(i, c), i > c
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int i = t + T * q;
-            if (i > c && i < p) xi[q] = fma(-Lcol[i], xc, xi[q]);
+            if (i > c && i < p) xi[q] = fma(-Lsm[packed_row(i) + c], xc, xi[q]);
         }
     }
     __syncthreads();
@@ -714,7 +699,7 @@ k_scale(int64_t n, const double *src, double *dst, int which, const DevState *st
 // Small single-block steps.
 // =====================================================================================
 struct SmallArgs {
-    double *H, *L, *R, *cs, *sn, *g, *lfro2, *r0v, *r1v, *r2v, *r3v, *y, *hist_res, *hist_lfro;
+    double *H, *L, *Lrow, *R, *cs, *sn, *g, *lfro2, *r0v, *r1v, *r2v, *r3v, *y, *hist_res, *hist_lfro;
     const double *part;
     DevState *st;
     int ldh, ldl;
@@ -723,7 +708,7 @@ struct SmallArgs {
 static SmallArgs small_args(const Workspace &w)
 {
     SmallArgs a;
-    a.H = w.H; a.L = w.L; a.R = w.R; a.cs = w.cs; a.sn = w.sn; a.g = w.g; a.lfro2 = w.lfro2;
+    a.H = w.H; a.L = w.L; a.Lrow = w.Lrow; a.R = w.R; a.cs = w.cs; a.sn = w.sn; a.g = w.g; a.lfro2 = w.lfro2;
     a.r0v = w.r0v; a.r1v = w.r1v; a.r2v = w.r2v; a.r3v = w.r3v; a.y = w.y;
     a.hist_res = w.hist_res; a.hist_lfro = w.hist_lfro; a.part = w.part; a.st = w.st;
     a.ldh = w.ldh(); a.ldl = w.ldl();
@@ -821,17 +806,20 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
         if (threadIdx.x == 0) st->halt = 1;
         return;
     }
-    extern __shared__ double dsm[];
+    extern __shared__ __align__(16) double dsm[];
     const int pp = k - 1;
     double *buf = dsm;              // 2p combined partials
     double *r0s = buf + 2 * pp;     // r^(0)
     double *r1s = r0s + pp;         // r^(1)
     double *tmp = r1s + pp;         // solve scratch
-    double *Lsm = tmp + pp;         // packed L_p
+    double *Lsm = dsm + ((5 * pp + 1) & ~1);  // row-packed L_p (16-byte aligned)
     __shared__ double s_inv_gamma;
     __shared__ int s_stop, s_terms, s_f32;
     __shared__ double s_hn2;
     const int p = k - 1, t = threadIdx.x;
+    // rows 0..p-2 of L (earlier steps) load while the partials are combined; row p-1 is
+    // formed below and written to shared memory directly
+    lower_prefetch(a.Lrow, p - 1, Lsm);
     const double lf2_prev = t == 0 ? a.lfro2[p - 2] : 0.0;  // issued early
     // breakdown test needs ||H(0:p-2, p-2)||^2 (overlapped with the partial combine)
     last_warp_sumsq(a.H + (int64_t)(p - 2) * a.ldh, p - 1, &s_hn2);
@@ -861,7 +849,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
         s_stop = stop;
     }
     __syncthreads();
-    if (s_stop != 0) return;
+    if (s_stop != 0) {
+        lower_drain();
+        return;
+    }
     const double ig = s_inv_gamma;
     if (t < 32) {
         // step 10 (warp 0): the new L row, its squared norm and the Neumann term count
@@ -869,6 +860,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
         for (int c = t; c < p - 1; c += 32) {
             const double l = buf[c] * ig;
             a.L[(int64_t)c * a.ldl + (p - 1)] = l;
+            a.Lrow[packed_row(p - 1) + c] = l;
+            Lsm[packed_row(p - 1) + c] = l;
             rowsq = fma(l, l, rowsq);
         }
         for (int o = 16; o > 0; o >>= 1) rowsq += __shfl_down_sync(0xffffffffu, rowsq, o);
@@ -890,7 +883,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
     // step 12
     const int terms = s_terms;
     const bool f32 = s_f32 != 0;
-    stage_lower(a.L, a.ldl, p, Lsm, f32);
+    lower_wait();
     unit_lower_solve(Lsm, p, r0s, r1s, tmp, terms, f32);
     for (int c = t; c < p; c += blockDim.x) {
         a.r1v[c] = r1s[c];
@@ -903,18 +896,23 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
 //   r^(3) = (I + L_{k-1})^{-1} r^(2),  H_{1:k-1,k-1} = r^(1) + r^(3).
 __global__ void __launch_bounds__(kSmallThreads) k_step_b(SmallArgs a, int k, int nrb)
 {
-    extern __shared__ double dsm[];
+    extern __shared__ __align__(16) double dsm[];
     const int p = k - 1, t = threadIdx.x;
-    double *r2s = dsm, *r3s = r2s + p, *tmp = r3s + p, *Lsm = tmp + p;
+    double *r2s = dsm, *r3s = r2s + p, *tmp = r3s + p;
+    double *Lsm = dsm + ((3 * p + 1) & ~1);  // row-packed L_p (16-byte aligned)
     // L_{k-1} and ||L||_F were written by k_step_a, which completed before the multi-dot this
     // kernel follows was launched: they are staged before waiting for that multi-dot.
     const int terms = neumann_terms(a.lfro2[p - 1]);
     const bool f32 = neumann_fp32(a.lfro2[p - 1], p, terms);
-    stage_lower(a.L, a.ldl, p, Lsm, f32);
+    lower_prefetch(a.Lrow, p, Lsm);
     IGS_PDL_ENTER();
     DevState *st = a.st;
-    if (halted(st)) return;
+    if (halted(st)) {
+        lower_drain();
+        return;
+    }
     reduce_partials(a.part, p, nrb, r2s);
+    lower_wait();
     unit_lower_solve(Lsm, p, r2s, r3s, tmp, terms, f32);
     for (int c = t; c < p; c += blockDim.x) {
         a.r3v[c] = r3s[c];
@@ -973,6 +971,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_flush(SmallArgs a, int m, int
     for (int c = t; c < m; c += blockDim.x) {
         const double l = buf[c] * s_ig;
         a.L[(int64_t)c * a.ldl + m] = l;
+        a.Lrow[packed_row(m) + c] = l;
         rowsq = fma(l, l, rowsq);
     }
     const double rs = block_sum(rowsq, sh);
@@ -1003,13 +1002,14 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, 
         if (threadIdx.x == 0) st->halt = 1;
         return;
     }
-    extern __shared__ double dsm[];
+    extern __shared__ __align__(16) double dsm[];
     const int nv = flush ? nb + 1 : 2 * (nb + 1);
     double *buf = dsm;            // combined partials (nv)
     double *r3s = buf + 2 * (nb + 1);
     double *tmp = r3s + nb;
     double *qs = tmp + nb;        // q of the completed column (nb)
-    double *Lsm = qs + nb;        // packed L_nb
+    double *Lsm = dsm + ((5 * nb + 3) & ~1);  // row-packed L_nb (16-byte aligned)
+    lower_prefetch(a.Lrow, nb, Lsm);  // rows of earlier steps, while the partials combine
     __shared__ double s_ig, s_g2;
     __shared__ int s_stop;
     const int t = threadIdx.x;
@@ -1027,7 +1027,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, 
     // step 5: r^(3) = (I + L_nb)^{-1} r^(2)
     const int terms = neumann_terms(a.lfro2[nb - 1]);
     const bool f32 = neumann_fp32(a.lfro2[nb - 1], nb, terms);
-    stage_lower(a.L, a.ldl, nb, Lsm, f32);
+    lower_wait();
     unit_lower_solve(Lsm, nb, buf, r3s, tmp, terms, f32);
     // step 14: column nb-1 complete (also kept in tmp for its norm)
     for (int c = t; c < nb; c += blockDim.x) {
@@ -1075,6 +1075,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, 
         for (int c = t; c < nb; c += 32) {
             const double l = buf[c] * ig;
             a.L[(int64_t)c * a.ldl + nb] = l;
+            a.Lrow[packed_row(nb) + c] = l;
             rowsq = fma(l, l, rowsq);
         }
         for (int o = 16; o > 0; o >>= 1) rowsq += __shfl_down_sync(0xffffffffu, rowsq, o);
@@ -1500,7 +1501,7 @@ cudaError_t launch_prime(const Workspace &w, const DotsPlan &pl, cudaStream_t s)
 
 size_t small_solve_smem(int p, int vecs)
 {
-    return sizeof(double) * ((size_t)vecs * p + (size_t)p * (p - 1) / 2);
+    return sizeof(double) * ((size_t)vecs * p + 2 + (size_t)p * (p - 1) / 2);  // + alignment of L
 }
 
 static cudaError_t allow_smem(const void *fn, size_t bytes)

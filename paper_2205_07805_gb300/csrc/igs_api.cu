@@ -11,6 +11,7 @@
 #include "igs_internal.h"
 
 #include <cmath>
+#include <new>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -632,208 +633,217 @@ void igs_destroy(igs_ctx *ctx)
 int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
                const double *vals, const igs_create_opts *opts)
 {
-    igs_ctx *ctx = nullptr;
-    if (!out) return fail(nullptr, IGS_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (!rowptr || (nnz > 0 && (!colind || !vals))) return fail(nullptr, IGS_EINVAL, "null CSR array");
-    if (n < 1 || nnz < 0 || nnz >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31))
-        return fail(nullptr, IGS_EINVAL, "bad sizes n=%lld nnz=%lld", (long long)n, (long long)nnz);
-    if (rowptr[0] != 0 || rowptr[n] != nnz) return fail(nullptr, IGS_EINVAL, "rowptr[0] must be 0 and rowptr[n] = nnz");
-    for (int64_t i = 0; i < n; ++i)
-        if (rowptr[i + 1] < rowptr[i]) return fail(nullptr, IGS_EINVAL, "rowptr decreases at row %lld", (long long)i);
-    for (int64_t q = 0; q < nnz; ++q) {
-        if (colind[q] < 0 || colind[q] >= n) return fail(nullptr, IGS_EINVAL, "column index out of range at %lld", (long long)q);
-        if (!std::isfinite(vals[q])) return fail(nullptr, IGS_ENUMERIC, "non-finite matrix value at %lld", (long long)q);
-    }
-    igs_create_opts o{};
-    o.device = -1;
-    o.max_restart_m = 100;
-    if (opts) o = *opts;
-    if (o.max_restart_m <= 0) o.max_restart_m = 100;
-    if (o.max_restart_m > igs::kMaxRestart)
-        return fail(nullptr, IGS_EINVAL, "max_restart_m %d exceeds %d", o.max_restart_m, igs::kMaxRestart);
-    if (o.norm2_iters <= 0) o.norm2_iters = 100;
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            igs_ctx *ctx = nullptr;
+            if (!out) return fail(nullptr, IGS_EINVAL, "out is NULL");
+            *out = nullptr;
+            if (!rowptr || (nnz > 0 && (!colind || !vals))) return fail(nullptr, IGS_EINVAL, "null CSR array");
+            if (n < 1 || nnz < 0 || nnz >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31))
+                return fail(nullptr, IGS_EINVAL, "bad sizes n=%lld nnz=%lld", (long long)n, (long long)nnz);
+            if (rowptr[0] != 0 || rowptr[n] != nnz) return fail(nullptr, IGS_EINVAL, "rowptr[0] must be 0 and rowptr[n] = nnz");
+            for (int64_t i = 0; i < n; ++i)
+                if (rowptr[i + 1] < rowptr[i]) return fail(nullptr, IGS_EINVAL, "rowptr decreases at row %lld", (long long)i);
+            for (int64_t q = 0; q < nnz; ++q) {
+                if (colind[q] < 0 || colind[q] >= n) return fail(nullptr, IGS_EINVAL, "column index out of range at %lld", (long long)q);
+                if (!std::isfinite(vals[q])) return fail(nullptr, IGS_ENUMERIC, "non-finite matrix value at %lld", (long long)q);
+            }
+            igs_create_opts o{};
+            o.device = -1;
+            o.max_restart_m = 100;
+            if (opts) o = *opts;
+            if (o.max_restart_m <= 0) o.max_restart_m = 100;
+            if (o.max_restart_m > igs::kMaxRestart)
+                return fail(nullptr, IGS_EINVAL, "max_restart_m %d exceeds %d", o.max_restart_m, igs::kMaxRestart);
+            if (o.norm2_iters <= 0) o.norm2_iters = 100;
 
-    ctx = new igs_ctx();
-    // Basis-update implementation (all compute the same steps): "plain" (row per thread,
-    // default: fastest measured), "tma" (bulk-copy pipelined), "fused" (non-pipelined fused
-    // update + reduction).
-    // Programmatic dependent launch between the cycle's kernels (default on; IGS_PDL=0 off).
-    if (const char *pdl = getenv("IGS_PDL")) ctx->w.pdl = strcmp(pdl, "0") != 0;
-    if (const char *path = getenv("IGS_UPDATE_PATH")) {
-        ctx->use_tma = strcmp(path, "tma") == 0;
-        ctx->fused_update = strcmp(path, "fused") == 0;
-    }
-    int rc = IGS_OK;
-    auto bail = [&](int code) {
-        if (!ctx->err.empty()) g_create_err = ctx->err;
-        igs_destroy(ctx);
-        return code;
-    };
-    {
-        int dev = o.device;
-        if (dev < 0) {
-            if (cudaGetDevice(&dev) != cudaSuccess) {
-                ctx->err = "no CUDA device";
+            ctx = new igs_ctx();
+            // Basis-update implementation (all compute the same steps): "plain" (row per thread,
+            // default: fastest measured), "tma" (bulk-copy pipelined), "fused" (non-pipelined fused
+            // update + reduction).
+            // Programmatic dependent launch between the cycle's kernels (default on; IGS_PDL=0 off).
+            if (const char *pdl = getenv("IGS_PDL")) ctx->w.pdl = strcmp(pdl, "0") != 0;
+            if (const char *path = getenv("IGS_UPDATE_PATH")) {
+                ctx->use_tma = strcmp(path, "tma") == 0;
+                ctx->fused_update = strcmp(path, "fused") == 0;
+            }
+            int rc = IGS_OK;
+            auto bail = [&](int code) {
+                if (!ctx->err.empty()) g_create_err = ctx->err;
+                igs_destroy(ctx);
+                return code;
+            };
+            {
+                int dev = o.device;
+                if (dev < 0) {
+                    if (cudaGetDevice(&dev) != cudaSuccess) {
+                        ctx->err = "no CUDA device";
+                        return bail(IGS_ECUDA);
+                    }
+                }
+                ctx->device = dev;
+                cudaError_t e = cudaSetDevice(dev);
+                if (e != cudaSuccess) {
+                    fail(ctx, IGS_ECUDA, "cudaSetDevice(%d): %s", dev, cudaGetErrorString(e));
+                    return bail(IGS_ECUDA);
+                }
+                int sms = 0;
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                ctx->w.num_sms = sms > 0 ? sms : 1;
+            }
+            if (o.stream) {
+                ctx->stream = (cudaStream_t)o.stream;
+            } else {
+                if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+                    ctx->err = "cudaStreamCreate failed";
+                    return bail(IGS_ECUDA);
+                }
+                ctx->own_stream = true;
+            }
+            ctx->stream_alloc = o.stream_alloc != 0;
+            if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+                ctx->err = "stream/event creation failed";
                 return bail(IGS_ECUDA);
             }
-        }
-        ctx->device = dev;
-        cudaError_t e = cudaSetDevice(dev);
-        if (e != cudaSuccess) {
-            fail(ctx, IGS_ECUDA, "cudaSetDevice(%d): %s", dev, cudaGetErrorString(e));
-            return bail(IGS_ECUDA);
-        }
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        ctx->w.num_sms = sms > 0 ? sms : 1;
-    }
-    if (o.stream) {
-        ctx->stream = (cudaStream_t)o.stream;
-    } else {
-        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            ctx->err = "cudaStreamCreate failed";
-            return bail(IGS_ECUDA);
-        }
-        ctx->own_stream = true;
-    }
-    ctx->stream_alloc = o.stream_alloc != 0;
-    if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-        ctx->err = "stream/event creation failed";
-        return bail(IGS_ECUDA);
-    }
-    igs::Workspace &w = ctx->w;
-    w.n = n;
-    w.nnz = nnz;
-    w.ld = (n + 31) & ~int64_t(31);
-    w.mmax = o.max_restart_m;
-    w.spmv_warp_rows = nnz >= 16 * n;
-    const int M = w.mmax;
-    int *rp = nullptr, *ci = nullptr;
-    double *va = nullptr;
-    if ((rc = dalloc(ctx, &rp, (size_t)n + 1)) || (rc = dalloc(ctx, &ci, (size_t)nnz)) ||
-        (rc = dalloc(ctx, &va, (size_t)nnz)) || (rc = dalloc(ctx, &w.V, (size_t)w.ld * (M + 1))) ||
-        (rc = dalloc(ctx, &w.z, (size_t)w.ld)) || (rc = dalloc(ctx, &w.u, (size_t)w.ld)) ||
-        (rc = dalloc(ctx, &w.r, (size_t)w.ld)) || (rc = dalloc(ctx, &w.b, (size_t)w.ld)) ||
-        (rc = dalloc(ctx, &w.x, (size_t)w.ld)) || (rc = dalloc(ctx, &w.t, (size_t)w.ld)) ||
-        (rc = dalloc(ctx, &w.H, (size_t)(M + 1) * M)) || (rc = dalloc(ctx, &w.R, (size_t)(M + 1) * M)) ||
-        (rc = dalloc(ctx, &w.L, (size_t)(M + 1) * (M + 1))) ||
-        (rc = dalloc(ctx, &w.Lrow, (size_t)(M + 1) * M / 2 + 2)) ||
-        (rc = dalloc(ctx, &w.Lout, (size_t)(M + 1) * (M + 1))) || (rc = dalloc(ctx, &w.cs, (size_t)M)) ||
-        (rc = dalloc(ctx, &w.sn, (size_t)M)) || (rc = dalloc(ctx, &w.g, (size_t)M + 1)) ||
-        (rc = dalloc(ctx, &w.lfro2, (size_t)M + 1)) || (rc = dalloc(ctx, &w.r0v, (size_t)M + 1)) ||
-        (rc = dalloc(ctx, &w.r1v, (size_t)M + 1)) || (rc = dalloc(ctx, &w.r2v, (size_t)M + 1)) ||
-        (rc = dalloc(ctx, &w.r3v, (size_t)M + 1)) || (rc = dalloc(ctx, &w.y, (size_t)M + 1)) ||
-        (rc = dalloc(ctx, &w.hist_res, (size_t)M)) || (rc = dalloc(ctx, &w.hist_lfro, (size_t)M)) ||
-        (rc = dalloc(ctx, &w.st, 1)))
-        return bail(rc);
-    // partial-sum buffer: largest multi-dot launch (two vectors, up to m+1 columns) or norms
-    // (also holds the fused update's group partials: <= 2*SMs/kFusedGroup + 1 groups x p)
-    int64_t cap = 3 * (int64_t)w.num_sms;
-    {
-        const int64_t groups =
-            ((int64_t)igs::kTmaMaxBlocksPerSM * w.num_sms + igs::kFusedGroup - 1) / igs::kFusedGroup + 1;
-        if (groups * (M + 1) > cap) cap = groups * (M + 1);
-    }
-    for (int p = 1; p <= M + 1; ++p) {
-        const igs::DotsPlan pl = igs::plan_dots(w, p);
-        const int64_t need = 2 * (int64_t)p * pl.rblocks;
-        if (need > cap) cap = need;
-    }
-    if ((rc = dalloc(ctx, &w.part, (size_t)cap))) return bail(rc);
-    w.part_cap = cap;
-    // fused update: per-block partials and group counters (<= kTmaMaxBlocksPerSM blocks per SM)
-    {
-        const int64_t maxblk = (int64_t)igs::kTmaMaxBlocksPerSM * w.num_sms;
-        if ((rc = dalloc(ctx, &w.bpart, (size_t)(maxblk * (M + 1)))) ||
-            (rc = dalloc(ctx, &w.counters, (size_t)((maxblk + igs::kFusedGroup - 1) / igs::kFusedGroup + 1))))
-            return bail(rc);
-    }
-    // host -> device copies; with pooled memory they follow the allocations on the stream
-    auto upload = [&](void *dst, const void *src, size_t bytes) {
-        if (!ctx->stream_alloc) return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
-        cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
-        return e == cudaSuccess ? cudaStreamSynchronize(ctx->stream) : e;
-    };
-    {
-        std::vector<int> rp32((size_t)n + 1);
-        for (int64_t i = 0; i <= n; ++i) rp32[(size_t)i] = (int)rowptr[i];
-        cudaError_t e = upload(rp, rp32.data(), sizeof(int) * rp32.size());
-        if (e == cudaSuccess && nnz > 0) e = upload(ci, colind, sizeof(int) * (size_t)nnz);
-        if (e == cudaSuccess && nnz > 0) e = upload(va, vals, sizeof(double) * (size_t)nnz);
-        if (e != cudaSuccess) {
-            fail(ctx, IGS_ECUDA, "copying A: %s", cudaGetErrorString(e));
-            return bail(IGS_ECUDA);
-        }
-    }
-    w.rowptr = rp;
-    w.colind = ci;
-    w.val = va;
-    if (o.fp32_basis) {
-        // precision form: FP32 basis, Krylov vectors and A's values (rounded to nearest)
-        if ((rc = dalloc(ctx, &w.V32, (size_t)w.ld * (M + 1))) || (rc = dalloc(ctx, &w.z32, (size_t)w.ld)) ||
-            (rc = dalloc(ctx, &w.u32, (size_t)w.ld)) || (rc = dalloc(ctx, &w.val32, (size_t)nnz)))
-            return bail(rc);
-        std::vector<float> v32((size_t)(nnz > 0 ? nnz : 1));
-        for (int64_t q = 0; q < nnz; ++q) v32[(size_t)q] = (float)vals[q];
-        cudaError_t e = nnz > 0 ? upload(w.val32, v32.data(), sizeof(float) * (size_t)nnz) : cudaSuccess;
-        if (e != cudaSuccess) {
-            fail(ctx, IGS_ECUDA, "copying A (FP32): %s", cudaGetErrorString(e));
-            return bail(IGS_ECUDA);
-        }
-    }
-    {
-        cudaError_t e = igs::configure_kernels(w);
-        if (e == cudaSuccess) e = igs::configure_tma_kernels();
-        if (e != cudaSuccess) {
-            fail(ctx, IGS_ECUDA, "kernel configuration: %s", cudaGetErrorString(e));
-            return bail(IGS_ECUDA);
-        }
-    }
-    if (o.A_norm2 > 0.0) {
-        ctx->normA = o.A_norm2;
-    } else {
-        // A^T in CSR (counting sort), uploaded for the power iteration only.
-        std::vector<int> trp((size_t)n + 1, 0), tci((size_t)nnz);
-        std::vector<double> tva((size_t)nnz);
-        for (int64_t q = 0; q < nnz; ++q) trp[(size_t)colind[q] + 1]++;
-        for (int64_t i = 0; i < n; ++i) trp[(size_t)i + 1] += trp[(size_t)i];
-        std::vector<int> pos(trp.begin(), trp.end() - 1);
-        for (int64_t i = 0; i < n; ++i)
-            for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
-                const int c = colind[q];
-                tci[(size_t)pos[(size_t)c]] = (int)i;
-                tva[(size_t)pos[(size_t)c]++] = vals[q];
+            igs::Workspace &w = ctx->w;
+            w.n = n;
+            w.nnz = nnz;
+            w.ld = (n + 31) & ~int64_t(31);
+            w.mmax = o.max_restart_m;
+            w.spmv_warp_rows = nnz >= 16 * n;
+            const int M = w.mmax;
+            int *rp = nullptr, *ci = nullptr;
+            double *va = nullptr;
+            if ((rc = dalloc(ctx, &rp, (size_t)n + 1)) || (rc = dalloc(ctx, &ci, (size_t)nnz)) ||
+                (rc = dalloc(ctx, &va, (size_t)nnz)) || (rc = dalloc(ctx, &w.V, (size_t)w.ld * (M + 1))) ||
+                (rc = dalloc(ctx, &w.z, (size_t)w.ld)) || (rc = dalloc(ctx, &w.u, (size_t)w.ld)) ||
+                (rc = dalloc(ctx, &w.r, (size_t)w.ld)) || (rc = dalloc(ctx, &w.b, (size_t)w.ld)) ||
+                (rc = dalloc(ctx, &w.x, (size_t)w.ld)) || (rc = dalloc(ctx, &w.t, (size_t)w.ld)) ||
+                (rc = dalloc(ctx, &w.H, (size_t)(M + 1) * M)) || (rc = dalloc(ctx, &w.R, (size_t)(M + 1) * M)) ||
+                (rc = dalloc(ctx, &w.L, (size_t)(M + 1) * (M + 1))) ||
+                (rc = dalloc(ctx, &w.Lrow, (size_t)(M + 1) * M / 2 + 2)) ||
+                (rc = dalloc(ctx, &w.Lout, (size_t)(M + 1) * (M + 1))) || (rc = dalloc(ctx, &w.cs, (size_t)M)) ||
+                (rc = dalloc(ctx, &w.sn, (size_t)M)) || (rc = dalloc(ctx, &w.g, (size_t)M + 1)) ||
+                (rc = dalloc(ctx, &w.lfro2, (size_t)M + 1)) || (rc = dalloc(ctx, &w.r0v, (size_t)M + 1)) ||
+                (rc = dalloc(ctx, &w.r1v, (size_t)M + 1)) || (rc = dalloc(ctx, &w.r2v, (size_t)M + 1)) ||
+                (rc = dalloc(ctx, &w.r3v, (size_t)M + 1)) || (rc = dalloc(ctx, &w.y, (size_t)M + 1)) ||
+                (rc = dalloc(ctx, &w.hist_res, (size_t)M)) || (rc = dalloc(ctx, &w.hist_lfro, (size_t)M)) ||
+                (rc = dalloc(ctx, &w.st, 1)))
+                return bail(rc);
+            // partial-sum buffer: largest multi-dot launch (two vectors, up to m+1 columns) or norms
+            // (also holds the fused update's group partials: <= 2*SMs/kFusedGroup + 1 groups x p)
+            int64_t cap = 3 * (int64_t)w.num_sms;
+            {
+                const int64_t groups =
+                    ((int64_t)igs::kTmaMaxBlocksPerSM * w.num_sms + igs::kFusedGroup - 1) / igs::kFusedGroup + 1;
+                if (groups * (M + 1) > cap) cap = groups * (M + 1);
             }
-        int *d_trp = nullptr, *d_tci = nullptr;
-        double *d_tva = nullptr;
-        cudaError_t e = cudaMalloc(&d_trp, sizeof(int) * (n + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&d_tci, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
-        if (e == cudaSuccess) e = cudaMalloc(&d_tva, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
-        if (e == cudaSuccess) e = cudaMemcpy(d_trp, trp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(d_tci, tci.data(), sizeof(int) * (size_t)nnz, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(d_tva, tva.data(), sizeof(double) * (size_t)nnz, cudaMemcpyHostToDevice);
-        double est = 0.0;
-        if (e == cudaSuccess) e = igs::estimate_norm2(w, d_trp, d_tci, d_tva, o.norm2_iters, &est, ctx->stream);
-        cudaFree(d_trp);
-        cudaFree(d_tci);
-        cudaFree(d_tva);
-        if (e != cudaSuccess) {
-            fail(ctx, IGS_ECUDA, "norm estimate: %s", cudaGetErrorString(e));
-            return bail(IGS_ECUDA);
-        }
-        ctx->normA = est;
-        ctx->normA_est = 1;
+            for (int p = 1; p <= M + 1; ++p) {
+                const igs::DotsPlan pl = igs::plan_dots(w, p);
+                const int64_t need = 2 * (int64_t)p * pl.rblocks;
+                if (need > cap) cap = need;
+            }
+            if ((rc = dalloc(ctx, &w.part, (size_t)cap))) return bail(rc);
+            w.part_cap = cap;
+            // fused update: per-block partials and group counters (<= kTmaMaxBlocksPerSM blocks per SM)
+            {
+                const int64_t maxblk = (int64_t)igs::kTmaMaxBlocksPerSM * w.num_sms;
+                if ((rc = dalloc(ctx, &w.bpart, (size_t)(maxblk * (M + 1)))) ||
+                    (rc = dalloc(ctx, &w.counters, (size_t)((maxblk + igs::kFusedGroup - 1) / igs::kFusedGroup + 1))))
+                    return bail(rc);
+            }
+            // host -> device copies; with pooled memory they follow the allocations on the stream
+            auto upload = [&](void *dst, const void *src, size_t bytes) {
+                if (!ctx->stream_alloc) return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+                cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+                return e == cudaSuccess ? cudaStreamSynchronize(ctx->stream) : e;
+            };
+            {
+                std::vector<int> rp32((size_t)n + 1);
+                for (int64_t i = 0; i <= n; ++i) rp32[(size_t)i] = (int)rowptr[i];
+                cudaError_t e = upload(rp, rp32.data(), sizeof(int) * rp32.size());
+                if (e == cudaSuccess && nnz > 0) e = upload(ci, colind, sizeof(int) * (size_t)nnz);
+                if (e == cudaSuccess && nnz > 0) e = upload(va, vals, sizeof(double) * (size_t)nnz);
+                if (e != cudaSuccess) {
+                    fail(ctx, IGS_ECUDA, "copying A: %s", cudaGetErrorString(e));
+                    return bail(IGS_ECUDA);
+                }
+            }
+            w.rowptr = rp;
+            w.colind = ci;
+            w.val = va;
+            if (o.fp32_basis) {
+                // precision form: FP32 basis, Krylov vectors and A's values (rounded to nearest)
+                if ((rc = dalloc(ctx, &w.V32, (size_t)w.ld * (M + 1))) || (rc = dalloc(ctx, &w.z32, (size_t)w.ld)) ||
+                    (rc = dalloc(ctx, &w.u32, (size_t)w.ld)) || (rc = dalloc(ctx, &w.val32, (size_t)nnz)))
+                    return bail(rc);
+                std::vector<float> v32((size_t)(nnz > 0 ? nnz : 1));
+                for (int64_t q = 0; q < nnz; ++q) v32[(size_t)q] = (float)vals[q];
+                cudaError_t e = nnz > 0 ? upload(w.val32, v32.data(), sizeof(float) * (size_t)nnz) : cudaSuccess;
+                if (e != cudaSuccess) {
+                    fail(ctx, IGS_ECUDA, "copying A (FP32): %s", cudaGetErrorString(e));
+                    return bail(IGS_ECUDA);
+                }
+            }
+            {
+                cudaError_t e = igs::configure_kernels(w);
+                if (e == cudaSuccess) e = igs::configure_tma_kernels();
+                if (e != cudaSuccess) {
+                    fail(ctx, IGS_ECUDA, "kernel configuration: %s", cudaGetErrorString(e));
+                    return bail(IGS_ECUDA);
+                }
+            }
+            if (o.A_norm2 > 0.0) {
+                ctx->normA = o.A_norm2;
+            } else {
+                // A^T in CSR (counting sort), uploaded for the power iteration only.
+                std::vector<int> trp((size_t)n + 1, 0), tci((size_t)nnz);
+                std::vector<double> tva((size_t)nnz);
+                for (int64_t q = 0; q < nnz; ++q) trp[(size_t)colind[q] + 1]++;
+                for (int64_t i = 0; i < n; ++i) trp[(size_t)i + 1] += trp[(size_t)i];
+                std::vector<int> pos(trp.begin(), trp.end() - 1);
+                for (int64_t i = 0; i < n; ++i)
+                    for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+                        const int c = colind[q];
+                        tci[(size_t)pos[(size_t)c]] = (int)i;
+                        tva[(size_t)pos[(size_t)c]++] = vals[q];
+                    }
+                int *d_trp = nullptr, *d_tci = nullptr;
+                double *d_tva = nullptr;
+                cudaError_t e = cudaMalloc(&d_trp, sizeof(int) * (n + 1));
+                if (e == cudaSuccess) e = cudaMalloc(&d_tci, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+                if (e == cudaSuccess) e = cudaMalloc(&d_tva, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+                if (e == cudaSuccess) e = cudaMemcpy(d_trp, trp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(d_tci, tci.data(), sizeof(int) * (size_t)nnz, cudaMemcpyHostToDevice);
+                if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(d_tva, tva.data(), sizeof(double) * (size_t)nnz, cudaMemcpyHostToDevice);
+                double est = 0.0;
+                if (e == cudaSuccess) e = igs::estimate_norm2(w, d_trp, d_tci, d_tva, o.norm2_iters, &est, ctx->stream);
+                cudaFree(d_trp);
+                cudaFree(d_tci);
+                cudaFree(d_tva);
+                if (e != cudaSuccess) {
+                    fail(ctx, IGS_ECUDA, "norm estimate: %s", cudaGetErrorString(e));
+                    return bail(IGS_ECUDA);
+                }
+                ctx->normA = est;
+                ctx->normA_est = 1;
+            }
+            if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+                ctx->err = "create: stream sync failed";
+                return bail(IGS_ECUDA);
+            }
+            *out = ctx;
+            return IGS_OK;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
+        return IGS_EINVAL;
     }
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-        ctx->err = "create: stream sync failed";
-        return bail(IGS_ECUDA);
-    }
-    *out = ctx;
-    return IGS_OK;
 }
 
 int igs_get_info(const igs_ctx *ctx, igs_info *info)
@@ -868,102 +878,120 @@ int64_t igs_launch_count(const igs_ctx *ctx) { return ctx ? ctx->launches : -1; 
 
 int igs_spmv(igs_ctx *ctx, const double *x, double *y, int on_device)
 {
-    if (!ctx || !x || !y) return IGS_EINVAL;
-    CK(cudaSetDevice(ctx->device));
-    igs::Workspace &w = ctx->w;
-    const size_t bytes = sizeof(double) * (size_t)w.n;
-    const double *xd = x;
-    double *yd = y;
-    if (!on_device) {
-        CK(cudaMemcpyAsync(w.t, x, bytes, cudaMemcpyHostToDevice, ctx->stream));
-        xd = w.t;
-        yd = w.z;
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            if (!ctx || !x || !y) return IGS_EINVAL;
+            CK(cudaSetDevice(ctx->device));
+            igs::Workspace &w = ctx->w;
+            const size_t bytes = sizeof(double) * (size_t)w.n;
+            const double *xd = x;
+            double *yd = y;
+            if (!on_device) {
+                CK(cudaMemcpyAsync(w.t, x, bytes, cudaMemcpyHostToDevice, ctx->stream));
+                xd = w.t;
+                yd = w.z;
+            }
+            CK(igs::launch_spmv(w, xd, yd, nullptr, false, ctx->stream));
+            ctx->launches += 1;
+            if (!on_device) CK(cudaMemcpyAsync(y, w.z, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            return IGS_OK;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
+        return IGS_EINVAL;
     }
-    CK(igs::launch_spmv(w, xd, yd, nullptr, false, ctx->stream));
-    ctx->launches += 1;
-    if (!on_device) CK(cudaMemcpyAsync(y, w.z, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    return IGS_OK;
 }
 
 int igs_solve(igs_ctx *ctx, const double *b, const double *x0, const igs_solve_opts *opts, igs_result *res)
 {
-    if (!ctx || !b || !opts || !res || !res->x) return ctx ? fail(ctx, IGS_EINVAL, "null argument") : IGS_EINVAL;
-    const int m = opts->restart_m;
-    const int method = opts->method == 0 ? IGS_METHOD_IGS : opts->method;
-    if (method != IGS_METHOD_IGS && method != IGS_METHOD_ONE_REDUCE) return fail(ctx, IGS_EINVAL, "unknown method");
-    if (m < 1 || m > ctx->w.mmax) return fail(ctx, IGS_EINVAL, "restart_m %d outside [1, %d]", m, ctx->w.mmax);
-    if (method == IGS_METHOD_IGS && opts->gs_iters != 1 && opts->gs_iters != 2)
-        return fail(ctx, IGS_EINVAL, "gs_iters must be 1 or 2");
-    if (method == IGS_METHOD_ONE_REDUCE && opts->precision != IGS_PREC_FP64)
-        return fail(ctx, IGS_EINVAL, "the one-reduce method runs in FP64 only");
-    const int gs = method == IGS_METHOD_ONE_REDUCE ? 0 : opts->gs_iters;  // 0: Alg. 4.2 cycle
-    if (opts->max_restarts < 1) return fail(ctx, IGS_EINVAL, "max_restarts must be >= 1");
-    if (!(opts->tol_beta >= 0.0)) return fail(ctx, IGS_EINVAL, "tol_beta must be >= 0");
-    if (res->H && res->H_ld < m + 1) return fail(ctx, IGS_EINVAL, "H_ld < m+1");
-    const int prec = opts->precision;
-    if (prec != IGS_PREC_FP64 && prec != IGS_PREC_FP32_IR) return fail(ctx, IGS_EINVAL, "unknown precision %d", prec);
-    if (prec == IGS_PREC_FP32_IR && !ctx->w.V32)
-        return fail(ctx, IGS_EINVAL, "precision FP32_IR needs a context created with fp32_basis");
-    const double inner_tol = prec == IGS_PREC_FP32_IR ? (opts->inner_tol > 0.0 ? opts->inner_tol : 1e-6) : 0.0;
-    CK(cudaSetDevice(ctx->device));
-    igs::Workspace &w = ctx->w;
-    const bool dev = opts->inputs_on_device != 0;
-    int rc;
-    if ((rc = copy_vec_in(ctx, w.b, b, dev)) != IGS_OK) return rc;
-    if ((rc = copy_vec_in(ctx, w.x, x0, dev)) != IGS_OK) return rc;
-    if ((rc = run_setup(ctx, opts->tol_beta, inner_tol)) != IGS_OK) return rc;
-    igs::DevState hs{};
-    if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
-    res->hist_len = 0;
-    res->steps = 0;
-    res->cycles = 0;
-    res->rho0 = hs.rnorm;
-    int status = IGS_NOT_CONVERGED;
-    std::vector<double> hres((size_t)m), hlf((size_t)m);
-    if (!std::isfinite(hs.beta)) {
-        status = IGS_ENUMERIC;
-    } else if (hs.beta <= opts->tol_beta) {
-        status = IGS_OK;
-    } else {
-        for (int cyc = 0; cyc < opts->max_restarts; ++cyc) {
-            if ((rc = run_cycle(ctx, m, gs, prec)) != IGS_OK) return rc;
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            if (!ctx || !b || !opts || !res || !res->x) return ctx ? fail(ctx, IGS_EINVAL, "null argument") : IGS_EINVAL;
+            const int m = opts->restart_m;
+            const int method = opts->method == 0 ? IGS_METHOD_IGS : opts->method;
+            if (method != IGS_METHOD_IGS && method != IGS_METHOD_ONE_REDUCE) return fail(ctx, IGS_EINVAL, "unknown method");
+            if (m < 1 || m > ctx->w.mmax) return fail(ctx, IGS_EINVAL, "restart_m %d outside [1, %d]", m, ctx->w.mmax);
+            if (method == IGS_METHOD_IGS && opts->gs_iters != 1 && opts->gs_iters != 2)
+                return fail(ctx, IGS_EINVAL, "gs_iters must be 1 or 2");
+            if (method == IGS_METHOD_ONE_REDUCE && opts->precision != IGS_PREC_FP64)
+                return fail(ctx, IGS_EINVAL, "the one-reduce method runs in FP64 only");
+            const int gs = method == IGS_METHOD_ONE_REDUCE ? 0 : opts->gs_iters;  // 0: Alg. 4.2 cycle
+            if (opts->max_restarts < 1) return fail(ctx, IGS_EINVAL, "max_restarts must be >= 1");
+            if (!(opts->tol_beta >= 0.0)) return fail(ctx, IGS_EINVAL, "tol_beta must be >= 0");
+            if (res->H && res->H_ld < m + 1) return fail(ctx, IGS_EINVAL, "H_ld < m+1");
+            const int prec = opts->precision;
+            if (prec != IGS_PREC_FP64 && prec != IGS_PREC_FP32_IR) return fail(ctx, IGS_EINVAL, "unknown precision %d", prec);
+            if (prec == IGS_PREC_FP32_IR && !ctx->w.V32)
+                return fail(ctx, IGS_EINVAL, "precision FP32_IR needs a context created with fp32_basis");
+            const double inner_tol = prec == IGS_PREC_FP32_IR ? (opts->inner_tol > 0.0 ? opts->inner_tol : 1e-6) : 0.0;
+            CK(cudaSetDevice(ctx->device));
+            igs::Workspace &w = ctx->w;
+            const bool dev = opts->inputs_on_device != 0;
+            int rc;
+            if ((rc = copy_vec_in(ctx, w.b, b, dev)) != IGS_OK) return rc;
+            if ((rc = copy_vec_in(ctx, w.x, x0, dev)) != IGS_OK) return rc;
+            if ((rc = run_setup(ctx, opts->tol_beta, inner_tol)) != IGS_OK) return rc;
+            igs::DevState hs{};
             if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
-            res->cycles += 1;
-            const int nc = hs.ncols;
-            res->steps += nc;
-            if ((res->arnoldi_hist || res->lfro_hist) && nc > 0) {
-                CK(cudaMemcpyAsync(hres.data(), w.hist_res, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
-                CK(cudaMemcpyAsync(hlf.data(), w.hist_lfro, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
-                CK(cudaStreamSynchronize(ctx->stream));
-                for (int j = 0; j < nc && res->hist_len < res->hist_cap; ++j) {
-                    if (res->arnoldi_hist) res->arnoldi_hist[res->hist_len] = hres[(size_t)j];
-                    if (res->lfro_hist) res->lfro_hist[res->hist_len] = hlf[(size_t)j];
-                    res->hist_len++;
+            res->hist_len = 0;
+            res->steps = 0;
+            res->cycles = 0;
+            res->rho0 = hs.rnorm;
+            int status = IGS_NOT_CONVERGED;
+            std::vector<double> hres((size_t)m), hlf((size_t)m);
+            if (!std::isfinite(hs.beta)) {
+                status = IGS_ENUMERIC;
+            } else if (hs.beta <= opts->tol_beta) {
+                status = IGS_OK;
+            } else {
+                for (int cyc = 0; cyc < opts->max_restarts; ++cyc) {
+                    if ((rc = run_cycle(ctx, m, gs, prec)) != IGS_OK) return rc;
+                    if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
+                    res->cycles += 1;
+                    const int nc = hs.ncols;
+                    res->steps += nc;
+                    if ((res->arnoldi_hist || res->lfro_hist) && nc > 0) {
+                        CK(cudaMemcpyAsync(hres.data(), w.hist_res, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+                        CK(cudaMemcpyAsync(hlf.data(), w.hist_lfro, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+                        CK(cudaStreamSynchronize(ctx->stream));
+                        for (int j = 0; j < nc && res->hist_len < res->hist_cap; ++j) {
+                            if (res->arnoldi_hist) res->arnoldi_hist[res->hist_len] = hres[(size_t)j];
+                            if (res->lfro_hist) res->lfro_hist[res->hist_len] = hlf[(size_t)j];
+                            res->hist_len++;
+                        }
+                    }
+                    if (hs.stop_reason < 0 || !std::isfinite(hs.beta)) {
+                        status = IGS_ENUMERIC;
+                        break;
+                    }
+                    if (hs.beta <= opts->tol_beta) {
+                        status = IGS_OK;
+                        break;
+                    }
+                    if (hs.stop_reason == 2) {
+                        status = IGS_BREAKDOWN;
+                        break;
+                    }
                 }
             }
-            if (hs.stop_reason < 0 || !std::isfinite(hs.beta)) {
-                status = IGS_ENUMERIC;
-                break;
-            }
-            if (hs.beta <= opts->tol_beta) {
-                status = IGS_OK;
-                break;
-            }
-            if (hs.stop_reason == 2) {
-                status = IGS_BREAKDOWN;
-                break;
-            }
-        }
+            const size_t bytes = sizeof(double) * (size_t)w.n;
+            CK(cudaMemcpyAsync(res->x, w.x, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+            if (res->H && res->cycles > 0)
+                CK(cudaMemcpy2DAsync(res->H, sizeof(double) * res->H_ld, w.H, sizeof(double) * w.ldh(),
+                                     sizeof(double) * (m + 1), m, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            res->beta = hs.beta;
+            return status;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
+        return IGS_EINVAL;
     }
-    const size_t bytes = sizeof(double) * (size_t)w.n;
-    CK(cudaMemcpyAsync(res->x, w.x, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
-    if (res->H && res->cycles > 0)
-        CK(cudaMemcpy2DAsync(res->H, sizeof(double) * res->H_ld, w.H, sizeof(double) * w.ldh(),
-                             sizeof(double) * (m + 1), m, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    res->beta = hs.beta;
-    return status;
 }
 
 int igs_arnoldi(igs_ctx *ctx, const double *r0, int m, int gs, int on_device, double *V, int64_t ldv,
@@ -975,46 +1003,55 @@ int igs_arnoldi(igs_ctx *ctx, const double *r0, int m, int gs, int on_device, do
 int igs_arnoldi_ex(igs_ctx *ctx, const double *r0, int m, int method, int gs, int on_device, double *V,
                    int64_t ldv, double *H, double *L, int *ncols, double *rho)
 {
-    if (!ctx || !r0) return ctx ? fail(ctx, IGS_EINVAL, "null argument") : IGS_EINVAL;
-    if (m < 1 || m > ctx->w.mmax) return fail(ctx, IGS_EINVAL, "m %d outside [1, %d]", m, ctx->w.mmax);
-    if (method != IGS_METHOD_IGS && method != IGS_METHOD_ONE_REDUCE) return fail(ctx, IGS_EINVAL, "unknown method");
-    if (method == IGS_METHOD_IGS && gs != 1 && gs != 2) return fail(ctx, IGS_EINVAL, "gs_iters must be 1 or 2");
-    if (method == IGS_METHOD_ONE_REDUCE) gs = 0;  // the Alg. 4.2 cycle
-    if (V && ldv < ctx->w.n) return fail(ctx, IGS_EINVAL, "ldv < n");
-    CK(cudaSetDevice(ctx->device));
-    igs::Workspace &w = ctx->w;
-    const int M = w.mmax;
-    CK(cudaMemsetAsync(w.H, 0, sizeof(double) * (size_t)(M + 1) * M, ctx->stream));
-    CK(cudaMemsetAsync(w.L, 0, sizeof(double) * (size_t)(M + 1) * (M + 1), ctx->stream));
-    CK(cudaMemsetAsync(w.V, 0, sizeof(double) * (size_t)w.ld * (M + 1), ctx->stream));
-    int rc;
-    if ((rc = copy_vec_in(ctx, w.b, r0, on_device != 0)) != IGS_OK) return rc;
-    if ((rc = copy_vec_in(ctx, w.x, nullptr, false)) != IGS_OK) return rc;
-    if ((rc = run_setup(ctx, 0.0, 0.0)) != IGS_OK) return rc;
-    if ((rc = run_cycle(ctx, m, gs, IGS_PREC_FP64)) != IGS_OK) return rc;
-    igs::DevState hs{};
-    if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (V)
-        CK(cudaMemcpy2DAsync(V, sizeof(double) * ldv, w.V, sizeof(double) * w.ld, sizeof(double) * w.n,
-                             m + 1, kind, ctx->stream));
-    if (H)
-        CK(cudaMemcpy2DAsync(H, sizeof(double) * (m + 1), w.H, sizeof(double) * w.ldh(),
-                             sizeof(double) * (m + 1), m, kind, ctx->stream));
-    if (L) {
-        // the device keeps L column-major; hand it out row-major
-        double *dst = on_device ? L : w.Lout;
-        CK(igs::launch_transpose(w.L, w.ldl(), m + 1, m + 1, dst, m + 1, ctx->stream));
-        ctx->launches += 1;
-        if (!on_device)
-            CK(cudaMemcpyAsync(L, w.Lout, sizeof(double) * (size_t)(m + 1) * (m + 1),
-                               cudaMemcpyDeviceToHost, ctx->stream));
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            if (!ctx || !r0) return ctx ? fail(ctx, IGS_EINVAL, "null argument") : IGS_EINVAL;
+            if (m < 1 || m > ctx->w.mmax) return fail(ctx, IGS_EINVAL, "m %d outside [1, %d]", m, ctx->w.mmax);
+            if (method != IGS_METHOD_IGS && method != IGS_METHOD_ONE_REDUCE) return fail(ctx, IGS_EINVAL, "unknown method");
+            if (method == IGS_METHOD_IGS && gs != 1 && gs != 2) return fail(ctx, IGS_EINVAL, "gs_iters must be 1 or 2");
+            if (method == IGS_METHOD_ONE_REDUCE) gs = 0;  // the Alg. 4.2 cycle
+            if (V && ldv < ctx->w.n) return fail(ctx, IGS_EINVAL, "ldv < n");
+            CK(cudaSetDevice(ctx->device));
+            igs::Workspace &w = ctx->w;
+            const int M = w.mmax;
+            CK(cudaMemsetAsync(w.H, 0, sizeof(double) * (size_t)(M + 1) * M, ctx->stream));
+            CK(cudaMemsetAsync(w.L, 0, sizeof(double) * (size_t)(M + 1) * (M + 1), ctx->stream));
+            CK(cudaMemsetAsync(w.V, 0, sizeof(double) * (size_t)w.ld * (M + 1), ctx->stream));
+            int rc;
+            if ((rc = copy_vec_in(ctx, w.b, r0, on_device != 0)) != IGS_OK) return rc;
+            if ((rc = copy_vec_in(ctx, w.x, nullptr, false)) != IGS_OK) return rc;
+            if ((rc = run_setup(ctx, 0.0, 0.0)) != IGS_OK) return rc;
+            if ((rc = run_cycle(ctx, m, gs, IGS_PREC_FP64)) != IGS_OK) return rc;
+            igs::DevState hs{};
+            if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
+            const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            if (V)
+                CK(cudaMemcpy2DAsync(V, sizeof(double) * ldv, w.V, sizeof(double) * w.ld, sizeof(double) * w.n,
+                                     m + 1, kind, ctx->stream));
+            if (H)
+                CK(cudaMemcpy2DAsync(H, sizeof(double) * (m + 1), w.H, sizeof(double) * w.ldh(),
+                                     sizeof(double) * (m + 1), m, kind, ctx->stream));
+            if (L) {
+                // the device keeps L column-major; hand it out row-major
+                double *dst = on_device ? L : w.Lout;
+                CK(igs::launch_transpose(w.L, w.ldl(), m + 1, m + 1, dst, m + 1, ctx->stream));
+                ctx->launches += 1;
+                if (!on_device)
+                    CK(cudaMemcpyAsync(L, w.Lout, sizeof(double) * (size_t)(m + 1) * (m + 1),
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+            }
+            CK(cudaStreamSynchronize(ctx->stream));
+            if (ncols) *ncols = hs.ncols;
+            if (rho) *rho = hs.rho;
+            if (hs.stop_reason < 0) return IGS_ENUMERIC;
+            return hs.stop_reason == 2 ? IGS_BREAKDOWN : IGS_OK;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
+        return IGS_EINVAL;
     }
-    CK(cudaStreamSynchronize(ctx->stream));
-    if (ncols) *ncols = hs.ncols;
-    if (rho) *rho = hs.rho;
-    if (hs.stop_reason < 0) return IGS_ENUMERIC;
-    return hs.stop_reason == 2 ? IGS_BREAKDOWN : IGS_OK;
 }
 
 }  // extern "C"

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <new>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -495,205 +496,214 @@ extern "C" int igs_batch_create(igs_batch **out, int count, const int64_t *sys_p
                                 const int64_t *rowptr, const int32_t *colind, const double *vals,
                                 const igs_batch_opts *opts)
 {
-    using namespace igs::batch;
-    if (!out) return IGS_EINVAL;
-    *out = nullptr;
-    if (count < 1 || !sys_ptr || !rowptr || !opts) return IGS_EINVAL;
-    const int m = opts->restart_m;
-    if (m < 1 || m > kMaxM) return IGS_EINVAL;
-    if (sys_ptr[0] != 0) return IGS_EINVAL;
-    int nmax = 0;
-    for (int s = 0; s < count; ++s) {
-        const int64_t n = sys_ptr[s + 1] - sys_ptr[s];
-        if (n < 1 || n > kMaxN) return IGS_EINVAL;
-        nmax = std::max(nmax, (int)n);
-    }
-    const int64_t N = sys_ptr[count];
-    if (rowptr[0] != 0) return IGS_EINVAL;
-    for (int64_t i = 0; i < N; ++i)
-        if (rowptr[i + 1] < rowptr[i]) return IGS_EINVAL;
-    const int64_t nnz = rowptr[N];
-    if (nnz >= ((int64_t)1 << 31)) return IGS_EINVAL;
-    if (nnz > 0 && (!colind || !vals)) return IGS_EINVAL;
-    // every entry of system s must lie in its diagonal block; store local column indices
-    std::vector<int> loc((size_t)(nnz ? nnz : 1));
-    for (int s = 0; s < count; ++s) {
-        const int64_t r0 = sys_ptr[s], r1 = sys_ptr[s + 1];
-        for (int64_t i = r0; i < r1; ++i)
-            for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-                const int64_t c = colind[k];
-                if (c < r0 || c >= r1) return IGS_EINVAL;
-                if (!std::isfinite(vals[k])) return IGS_ENUMERIC;
-                loc[(size_t)k] = (int)(c - r0);
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            using namespace igs::batch;
+            if (!out) return IGS_EINVAL;
+            *out = nullptr;
+            if (count < 1 || !sys_ptr || !rowptr || !opts) return IGS_EINVAL;
+            const int m = opts->restart_m;
+            if (m < 1 || m > kMaxM) return IGS_EINVAL;
+            if (sys_ptr[0] != 0) return IGS_EINVAL;
+            int nmax = 0;
+            for (int s = 0; s < count; ++s) {
+                const int64_t n = sys_ptr[s + 1] - sys_ptr[s];
+                if (n < 1 || n > kMaxN) return IGS_EINVAL;
+                nmax = std::max(nmax, (int)n);
             }
-    }
-    if (opts->A_norm2)
-        for (int s = 0; s < count; ++s)
-            if (!(opts->A_norm2[s] >= 0.0) || !std::isfinite(opts->A_norm2[s])) return IGS_EINVAL;
-    if (opts->block_threads != 0 && !valid_threads(opts->block_threads)) return IGS_EINVAL;
-    if (opts->blocks_per_sm < 0 || opts->blocks_per_sm > kMaxSlotsPerSM) return IGS_EINVAL;
+            const int64_t N = sys_ptr[count];
+            if (rowptr[0] != 0) return IGS_EINVAL;
+            for (int64_t i = 0; i < N; ++i)
+                if (rowptr[i + 1] < rowptr[i]) return IGS_EINVAL;
+            const int64_t nnz = rowptr[N];
+            if (nnz >= ((int64_t)1 << 31)) return IGS_EINVAL;
+            if (nnz > 0 && (!colind || !vals)) return IGS_EINVAL;
+            // every entry of system s must lie in its diagonal block; store local column indices
+            std::vector<int> loc((size_t)(nnz ? nnz : 1));
+            for (int s = 0; s < count; ++s) {
+                const int64_t r0 = sys_ptr[s], r1 = sys_ptr[s + 1];
+                for (int64_t i = r0; i < r1; ++i)
+                    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+                        const int64_t c = colind[k];
+                        if (c < r0 || c >= r1) return IGS_EINVAL;
+                        if (!std::isfinite(vals[k])) return IGS_ENUMERIC;
+                        loc[(size_t)k] = (int)(c - r0);
+                    }
+            }
+            if (opts->A_norm2)
+                for (int s = 0; s < count; ++s)
+                    if (!(opts->A_norm2[s] >= 0.0) || !std::isfinite(opts->A_norm2[s])) return IGS_EINVAL;
+            if (opts->block_threads != 0 && !valid_threads(opts->block_threads)) return IGS_EINVAL;
+            if (opts->blocks_per_sm < 0 || opts->blocks_per_sm > kMaxSlotsPerSM) return IGS_EINVAL;
 
-    igs_batch *bt = new (std::nothrow) igs_batch();
-    if (!bt) return IGS_ENOMEM;
-    int rc = IGS_OK;
-    auto bail = [&](int code) {
-        igs_batch_destroy(bt);
-        return code;
-    };
-    bt->device = opts->device;
-    if (cudaSetDevice(bt->device) != cudaSuccess) return bail(IGS_ECUDA);
-    if (opts->stream) {
-        bt->stream = static_cast<cudaStream_t>(opts->stream);
-    } else {
-        if (cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(IGS_ECUDA);
-        bt->own_stream = true;
-    }
-    bt->count = count;
-    bt->m = m;
-    bt->nmax = nmax;
-    bt->N = N;
-    bt->nnz = nnz;
-    if (cudaDeviceGetAttribute(&bt->num_sms, cudaDevAttrMultiProcessorCount, bt->device) != cudaSuccess)
-        return bail(IGS_ECUDA);
-    if (cudaDeviceGetAttribute(&bt->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, bt->device) !=
-        cudaSuccess)
-        return bail(IGS_ECUDA);
-    const SmemLayout L = smem_layout(nmax, m);
-    bt->smem = sizeof(double) * (size_t)L.total;
-    for (int t : {128, 256, 512}) {
-        cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, batch_kernel(t)) != cudaSuccess) return bail(IGS_ECUDA);
-        if (bt->smem + fa.sharedSizeBytes > (size_t)bt->max_smem_optin) return bail(IGS_EINVAL);
-        if (cudaFuncSetAttribute(batch_kernel(t), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem) !=
-            cudaSuccess)
-            return bail(IGS_ECUDA);
-    }
-    if (cudaFuncSetAttribute(k_batch_norm2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem) !=
-        cudaSuccess)
-        return bail(IGS_ECUDA);
+            igs_batch *bt = new (std::nothrow) igs_batch();
+            if (!bt) return IGS_ENOMEM;
+            int rc = IGS_OK;
+            auto bail = [&](int code) {
+                igs_batch_destroy(bt);
+                return code;
+            };
+            bt->device = opts->device;
+            if (cudaSetDevice(bt->device) != cudaSuccess) return bail(IGS_ECUDA);
+            if (opts->stream) {
+                bt->stream = static_cast<cudaStream_t>(opts->stream);
+            } else {
+                if (cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(IGS_ECUDA);
+                bt->own_stream = true;
+            }
+            bt->count = count;
+            bt->m = m;
+            bt->nmax = nmax;
+            bt->N = N;
+            bt->nnz = nnz;
+            if (cudaDeviceGetAttribute(&bt->num_sms, cudaDevAttrMultiProcessorCount, bt->device) != cudaSuccess)
+                return bail(IGS_ECUDA);
+            if (cudaDeviceGetAttribute(&bt->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, bt->device) !=
+                cudaSuccess)
+                return bail(IGS_ECUDA);
+            const SmemLayout L = smem_layout(nmax, m);
+            bt->smem = sizeof(double) * (size_t)L.total;
+            for (int t : {128, 256, 512}) {
+                cudaFuncAttributes fa;
+                if (cudaFuncGetAttributes(&fa, batch_kernel(t)) != cudaSuccess) return bail(IGS_ECUDA);
+                if (bt->smem + fa.sharedSizeBytes > (size_t)bt->max_smem_optin) return bail(IGS_EINVAL);
+                if (cudaFuncSetAttribute(batch_kernel(t), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem) !=
+                    cudaSuccess)
+                    return bail(IGS_ECUDA);
+            }
+            if (cudaFuncSetAttribute(k_batch_norm2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem) !=
+                cudaSuccess)
+                return bail(IGS_ECUDA);
 
-    // slots: one per CTA of the largest configuration the GPU can hold (any block size)
-    int slots_per_sm = 0;
-    for (int t : {128, 256, 512}) {
-        int nb = 0;
-        rc = max_blocks_per_sm(bt, t, &nb);
-        if (rc != IGS_OK) return bail(rc);
-        slots_per_sm = std::max(slots_per_sm, nb);
-    }
-    if (slots_per_sm < 1) return bail(IGS_EINVAL);
-    bt->slots_alloc = bt->num_sms * slots_per_sm;
-    // (m+1) basis columns (at least three for the power iteration's vectors), then R
-    bt->r_offset = (int64_t)std::max(m + 1, 3) * round_up(nmax, 4);
-    bt->slot_stride = bt->r_offset + (int64_t)m * (m + 1) / 2;
-    bt->slot_stride = (bt->slot_stride + 31) / 32 * 32;
+            // slots: one per CTA of the largest configuration the GPU can hold (any block size)
+            int slots_per_sm = 0;
+            for (int t : {128, 256, 512}) {
+                int nb = 0;
+                rc = max_blocks_per_sm(bt, t, &nb);
+                if (rc != IGS_OK) return bail(rc);
+                slots_per_sm = std::max(slots_per_sm, nb);
+            }
+            if (slots_per_sm < 1) return bail(IGS_EINVAL);
+            bt->slots_alloc = bt->num_sms * slots_per_sm;
+            // (m+1) basis columns (at least three for the power iteration's vectors), then R
+            bt->r_offset = (int64_t)std::max(m + 1, 3) * round_up(nmax, 4);
+            bt->slot_stride = bt->r_offset + (int64_t)m * (m + 1) / 2;
+            bt->slot_stride = (bt->slot_stride + 31) / 32 * 32;
 
-    // solve order: largest system first (ties by index); the tuning sample is every 4th
-    std::vector<int> order(count);
-    for (int s = 0; s < count; ++s) order[s] = s;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        return sys_ptr[x + 1] - sys_ptr[x] > sys_ptr[y + 1] - sys_ptr[y];
-    });
-    std::vector<int> sample;
-    for (int q = 0; q < count; q += 4) sample.push_back(order[q]);
-    bt->sample_count = (int)sample.size();
+            // solve order: largest system first (ties by index); the tuning sample is every 4th
+            std::vector<int> order(count);
+            for (int s = 0; s < count; ++s) order[s] = s;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+                return sys_ptr[x + 1] - sys_ptr[x] > sys_ptr[y + 1] - sys_ptr[y];
+            });
+            std::vector<int> sample;
+            for (int q = 0; q < count; q += 4) sample.push_back(order[q]);
+            bt->sample_count = (int)sample.size();
 
-    // b for tuning: A * ones
-    std::vector<double> btune((size_t)N);
-    for (int64_t i = 0; i < N; ++i) {
-        double s = 0.0;
-        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += vals[k];
-        btune[(size_t)i] = s;
-    }
+            // b for tuning: A * ones
+            std::vector<double> btune((size_t)N);
+            for (int64_t i = 0; i < N; ++i) {
+                double s = 0.0;
+                for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += vals[k];
+                btune[(size_t)i] = s;
+            }
 
-    if (dalloc(&bt->sys_row0, (size_t)count + 1) || dalloc(&bt->order, (size_t)count) || dalloc(&bt->order_sample, sample.size()) ||
-        dalloc(&bt->normA, (size_t)count) ||
-        dalloc(&bt->vslots, (size_t)bt->slots_alloc * (size_t)bt->slot_stride) ||
-        dalloc(&bt->queue, 1) || dalloc(&bt->summary, 10) || dalloc(&bt->run_dev, 1) ||
-        dalloc(&bt->b_dev, (size_t)N) || dalloc(&bt->x_dev, (size_t)N) || dalloc(&bt->x0_dev, (size_t)N) ||
-        dalloc(&bt->b_tune, (size_t)N) || dalloc(&bt->beta_dev, (size_t)count) ||
-        dalloc(&bt->status_dev, (size_t)count) || dalloc(&bt->cycles_dev, (size_t)count) ||
-        dalloc(&bt->steps_dev, (size_t)count))
-        return bail(IGS_ENOMEM);
-    if (cudaMallocHost(reinterpret_cast<void **>(&bt->run_host), sizeof(Run)) != cudaSuccess ||
-        cudaMallocHost(reinterpret_cast<void **>(&bt->summary_host), 10 * sizeof(unsigned long long)) !=
-            cudaSuccess)
-        return bail(IGS_ENOMEM);
-    std::memset(bt->run_host, 0, sizeof(Run));
-    if (cudaEventCreate(&bt->ev0) != cudaSuccess || cudaEventCreate(&bt->ev1) != cudaSuccess)
-        return bail(IGS_ECUDA);
-    cudaStream_t s = bt->stream;
-    {
-        SellHost sh;
-        build_sell(count, sys_ptr, rowptr, loc.data(), vals, sh);
-        rc = upload_sell(sh, &bt->sell_off, &bt->sys_slice0, &bt->sell_col, &bt->sell_val, s);
-        if (rc != IGS_OK) return bail(rc);
-        if (cudaStreamSynchronize(s) != cudaSuccess) return bail(IGS_ECUDA);
-    }
-    if (cudaMemcpyAsync(bt->sys_row0, sys_ptr, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s) ||
-        cudaMemcpyAsync(bt->order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s) ||
-        cudaMemcpyAsync(bt->order_sample, sample.data(), sizeof(int) * sample.size(), cudaMemcpyHostToDevice, s) ||
-        cudaMemcpyAsync(bt->b_tune, btune.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s) ||
-        cudaMemsetAsync(bt->vslots, 0, sizeof(double) * (size_t)bt->slots_alloc * bt->slot_stride, s))
-        return bail(IGS_ECUDA);
+            if (dalloc(&bt->sys_row0, (size_t)count + 1) || dalloc(&bt->order, (size_t)count) || dalloc(&bt->order_sample, sample.size()) ||
+                dalloc(&bt->normA, (size_t)count) ||
+                dalloc(&bt->vslots, (size_t)bt->slots_alloc * (size_t)bt->slot_stride) ||
+                dalloc(&bt->queue, 1) || dalloc(&bt->summary, 10) || dalloc(&bt->run_dev, 1) ||
+                dalloc(&bt->b_dev, (size_t)N) || dalloc(&bt->x_dev, (size_t)N) || dalloc(&bt->x0_dev, (size_t)N) ||
+                dalloc(&bt->b_tune, (size_t)N) || dalloc(&bt->beta_dev, (size_t)count) ||
+                dalloc(&bt->status_dev, (size_t)count) || dalloc(&bt->cycles_dev, (size_t)count) ||
+                dalloc(&bt->steps_dev, (size_t)count))
+                return bail(IGS_ENOMEM);
+            if (cudaMallocHost(reinterpret_cast<void **>(&bt->run_host), sizeof(Run)) != cudaSuccess ||
+                cudaMallocHost(reinterpret_cast<void **>(&bt->summary_host), 10 * sizeof(unsigned long long)) !=
+                    cudaSuccess)
+                return bail(IGS_ENOMEM);
+            std::memset(bt->run_host, 0, sizeof(Run));
+            if (cudaEventCreate(&bt->ev0) != cudaSuccess || cudaEventCreate(&bt->ev1) != cudaSuccess)
+                return bail(IGS_ECUDA);
+            cudaStream_t s = bt->stream;
+            {
+                SellHost sh;
+                build_sell(count, sys_ptr, rowptr, loc.data(), vals, sh);
+                rc = upload_sell(sh, &bt->sell_off, &bt->sys_slice0, &bt->sell_col, &bt->sell_val, s);
+                if (rc != IGS_OK) return bail(rc);
+                if (cudaStreamSynchronize(s) != cudaSuccess) return bail(IGS_ECUDA);
+            }
+            if (cudaMemcpyAsync(bt->sys_row0, sys_ptr, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s) ||
+                cudaMemcpyAsync(bt->order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s) ||
+                cudaMemcpyAsync(bt->order_sample, sample.data(), sizeof(int) * sample.size(), cudaMemcpyHostToDevice, s) ||
+                cudaMemcpyAsync(bt->b_tune, btune.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s) ||
+                cudaMemsetAsync(bt->vslots, 0, sizeof(double) * (size_t)bt->slots_alloc * bt->slot_stride, s))
+                return bail(IGS_ECUDA);
 
-    // ||A_s||_2: given, or estimated on the GPU by power iteration on A_s^T A_s
-    bt->normA_host.assign((size_t)count, 0.0);
-    if (opts->A_norm2) {
-        std::memcpy(bt->normA_host.data(), opts->A_norm2, sizeof(double) * count);
-        if (cudaMemcpyAsync(bt->normA, opts->A_norm2, sizeof(double) * count, cudaMemcpyHostToDevice, s))
-            return bail(IGS_ECUDA);
-    } else {
-        // A^T in the same block-diagonal CSR form (local column indices)
-        std::vector<int64_t> trp((size_t)N + 1, 0);
-        for (int64_t k = 0; k < nnz; ++k) trp[(size_t)(colind[k] + 1)]++;
-        for (int64_t i = 0; i < N; ++i) trp[(size_t)i + 1] += trp[(size_t)i];
-        std::vector<int64_t> fillp(trp.begin(), trp.end() - 1);
-        std::vector<int> tci((size_t)(nnz ? nnz : 1));
-        std::vector<double> tva((size_t)(nnz ? nnz : 1));
-        for (int sidx = 0; sidx < count; ++sidx)
-            for (int64_t i = sys_ptr[sidx]; i < sys_ptr[sidx + 1]; ++i)
-                for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-                    const int64_t dst = fillp[(size_t)colind[k]]++;
-                    tci[(size_t)dst] = (int)(i - sys_ptr[sidx]);
-                    tva[(size_t)dst] = vals[k];
+            // ||A_s||_2: given, or estimated on the GPU by power iteration on A_s^T A_s
+            bt->normA_host.assign((size_t)count, 0.0);
+            if (opts->A_norm2) {
+                std::memcpy(bt->normA_host.data(), opts->A_norm2, sizeof(double) * count);
+                if (cudaMemcpyAsync(bt->normA, opts->A_norm2, sizeof(double) * count, cudaMemcpyHostToDevice, s))
+                    return bail(IGS_ECUDA);
+            } else {
+                // A^T in the same block-diagonal CSR form (local column indices)
+                std::vector<int64_t> trp((size_t)N + 1, 0);
+                for (int64_t k = 0; k < nnz; ++k) trp[(size_t)(colind[k] + 1)]++;
+                for (int64_t i = 0; i < N; ++i) trp[(size_t)i + 1] += trp[(size_t)i];
+                std::vector<int64_t> fillp(trp.begin(), trp.end() - 1);
+                std::vector<int> tci((size_t)(nnz ? nnz : 1));
+                std::vector<double> tva((size_t)(nnz ? nnz : 1));
+                for (int sidx = 0; sidx < count; ++sidx)
+                    for (int64_t i = sys_ptr[sidx]; i < sys_ptr[sidx + 1]; ++i)
+                        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+                            const int64_t dst = fillp[(size_t)colind[k]]++;
+                            tci[(size_t)dst] = (int)(i - sys_ptr[sidx]);
+                            tva[(size_t)dst] = vals[k];
+                        }
+                SellHost th;
+                build_sell(count, sys_ptr, trp.data(), tci.data(), tva.data(), th);
+                int64_t *at_rp = nullptr;
+                int *at_ci = nullptr;
+                double *at_va = nullptr;
+                int urc = upload_sell(th, &at_rp, nullptr, &at_ci, &at_va, s);
+                const int iters = opts->norm2_iters > 0 ? opts->norm2_iters : 100;
+                cudaError_t e = urc == IGS_OK ? cudaSuccess : cudaErrorMemoryAllocation;
+                if (e == cudaSuccess) {
+                    const int grid = std::min(count, bt->slots_alloc);
+                    k_batch_norm2<<<grid, 256, bt->smem, s>>>(make_args(bt), at_rp, at_ci, at_va, count, iters, bt->normA);
+                    e = cudaGetLastError();
                 }
-        SellHost th;
-        build_sell(count, sys_ptr, trp.data(), tci.data(), tva.data(), th);
-        int64_t *at_rp = nullptr;
-        int *at_ci = nullptr;
-        double *at_va = nullptr;
-        int urc = upload_sell(th, &at_rp, nullptr, &at_ci, &at_va, s);
-        const int iters = opts->norm2_iters > 0 ? opts->norm2_iters : 100;
-        cudaError_t e = urc == IGS_OK ? cudaSuccess : cudaErrorMemoryAllocation;
-        if (e == cudaSuccess) {
-            const int grid = std::min(count, bt->slots_alloc);
-            k_batch_norm2<<<grid, 256, bt->smem, s>>>(make_args(bt), at_rp, at_ci, at_va, count, iters, bt->normA);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(bt->normA_host.data(), bt->normA, sizeof(double) * count, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        cudaFree(at_rp);
-        cudaFree(at_ci);
-        cudaFree(at_va);
-        if (e != cudaSuccess) return bail(IGS_ECUDA);
-    }
-    if (cudaStreamSynchronize(s) != cudaSuccess) return bail(IGS_ECUDA);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(bt->normA_host.data(), bt->normA, sizeof(double) * count, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                cudaFree(at_rp);
+                cudaFree(at_ci);
+                cudaFree(at_va);
+                if (e != cudaSuccess) return bail(IGS_ECUDA);
+            }
+            if (cudaStreamSynchronize(s) != cudaSuccess) return bail(IGS_ECUDA);
 
-    // launch configuration: given, else tuned
-    if (opts->block_threads != 0 && opts->blocks_per_sm != 0) {
-        bt->threads = opts->block_threads;
-        bt->bpsm = opts->blocks_per_sm;
-        int maxb = 0;
-        rc = max_blocks_per_sm(bt, bt->threads, &maxb);
-        if (rc != IGS_OK) return bail(rc);
-        if (maxb < 1) return bail(IGS_EINVAL);
-    } else {
-        rc = autotune(bt, 2, 1e-12, 20);
-        if (rc != IGS_OK) return bail(rc);
+            // launch configuration: given, else tuned
+            if (opts->block_threads != 0 && opts->blocks_per_sm != 0) {
+                bt->threads = opts->block_threads;
+                bt->bpsm = opts->blocks_per_sm;
+                int maxb = 0;
+                rc = max_blocks_per_sm(bt, bt->threads, &maxb);
+                if (rc != IGS_OK) return bail(rc);
+                if (maxb < 1) return bail(IGS_EINVAL);
+            } else {
+                rc = autotune(bt, 2, 1e-12, 20);
+                if (rc != IGS_OK) return bail(rc);
+            }
+            *out = bt;
+            return IGS_OK;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
+        return IGS_EINVAL;
     }
-    *out = bt;
-    return IGS_OK;
 }
 
 extern "C" void igs_batch_destroy(igs_batch *bt)
@@ -733,96 +743,123 @@ extern "C" void igs_batch_destroy(igs_batch *bt)
 extern "C" int igs_batch_solve(igs_batch *bt, const double *b, const double *x0,
                                const igs_batch_solve_opts *opts, igs_batch_result *res)
 {
-    if (!bt) return IGS_EINVAL;
-    if (!b || !opts || !res || !res->x) return fail(bt, IGS_EINVAL, "null argument");
-    if (opts->gs_iters < 1 || opts->gs_iters > 2 || !(opts->tol_beta >= 0.0) || opts->max_restarts < 1)
-        return fail(bt, IGS_EINVAL, "invalid solve options");
-    if (cudaSetDevice(bt->device) != cudaSuccess) return fail(bt, IGS_ECUDA, "cudaSetDevice");
-    cudaStream_t s = bt->stream;
-    const bool dev = opts->inputs_on_device != 0;
-    Run *r = bt->run_host;
-    std::memset(r, 0, sizeof(Run));
-    r->order = bt->order;
-    r->count = bt->count;
-    r->gs = opts->gs_iters;
-    r->max_cycles = opts->max_restarts;
-    r->tol = opts->tol_beta;
-    r->x0_given = x0 ? 1 : 0;
-    const size_t vb = sizeof(double) * (size_t)bt->N;
-    if (dev) {
-        r->b = b;
-        r->x0 = x0;
-        r->x = res->x;
-        r->beta = res->beta;
-        r->status = res->status;
-        r->steps = res->steps;
-        r->cycles = res->cycles;
-    } else {
-        BT_CUDA(cudaMemcpyAsync(bt->b_dev, b, vb, cudaMemcpyHostToDevice, s), "copy b");
-        if (x0) BT_CUDA(cudaMemcpyAsync(bt->x0_dev, x0, vb, cudaMemcpyHostToDevice, s), "copy x0");
-        r->b = bt->b_dev;
-        r->x0 = x0 ? bt->x0_dev : nullptr;
-        r->x = bt->x_dev;
-        r->beta = bt->beta_dev;
-        r->status = bt->status_dev;
-        r->steps = bt->steps_dev;
-        r->cycles = bt->cycles_dev;
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            if (!bt) return IGS_EINVAL;
+            if (!b || !opts || !res || !res->x) return fail(bt, IGS_EINVAL, "null argument");
+            if (opts->gs_iters < 1 || opts->gs_iters > 2 || !(opts->tol_beta >= 0.0) || opts->max_restarts < 1)
+                return fail(bt, IGS_EINVAL, "invalid solve options");
+            if (cudaSetDevice(bt->device) != cudaSuccess) return fail(bt, IGS_ECUDA, "cudaSetDevice");
+            cudaStream_t s = bt->stream;
+            const bool dev = opts->inputs_on_device != 0;
+            Run *r = bt->run_host;
+            std::memset(r, 0, sizeof(Run));
+            r->order = bt->order;
+            r->count = bt->count;
+            r->gs = opts->gs_iters;
+            r->max_cycles = opts->max_restarts;
+            r->tol = opts->tol_beta;
+            r->x0_given = x0 ? 1 : 0;
+            const size_t vb = sizeof(double) * (size_t)bt->N;
+            if (dev) {
+                r->b = b;
+                r->x0 = x0;
+                r->x = res->x;
+                r->beta = res->beta;
+                r->status = res->status;
+                r->steps = res->steps;
+                r->cycles = res->cycles;
+            } else {
+                BT_CUDA(cudaMemcpyAsync(bt->b_dev, b, vb, cudaMemcpyHostToDevice, s), "copy b");
+                if (x0) BT_CUDA(cudaMemcpyAsync(bt->x0_dev, x0, vb, cudaMemcpyHostToDevice, s), "copy x0");
+                r->b = bt->b_dev;
+                r->x0 = x0 ? bt->x0_dev : nullptr;
+                r->x = bt->x_dev;
+                r->beta = bt->beta_dev;
+                r->status = bt->status_dev;
+                r->steps = bt->steps_dev;
+                r->cycles = bt->cycles_dev;
+            }
+            float ms = 0.f;
+            int rc = launch(bt, bt->threads, bt->bpsm, &ms);
+            if (rc != IGS_OK) return rc;
+            if (!dev) {
+                BT_CUDA(cudaMemcpyAsync(res->x, bt->x_dev, vb, cudaMemcpyDeviceToHost, s), "copy x");
+                if (res->beta)
+                    BT_CUDA(cudaMemcpyAsync(res->beta, bt->beta_dev, sizeof(double) * bt->count, cudaMemcpyDeviceToHost, s),
+                            "copy beta");
+                if (res->status)
+                    BT_CUDA(cudaMemcpyAsync(res->status, bt->status_dev, sizeof(int) * bt->count, cudaMemcpyDeviceToHost, s),
+                            "copy status");
+                if (res->steps)
+                    BT_CUDA(cudaMemcpyAsync(res->steps, bt->steps_dev, sizeof(int64_t) * bt->count, cudaMemcpyDeviceToHost, s),
+                            "copy steps");
+                if (res->cycles)
+                    BT_CUDA(cudaMemcpyAsync(res->cycles, bt->cycles_dev, sizeof(int) * bt->count, cudaMemcpyDeviceToHost, s),
+                            "copy cycles");
+                BT_CUDA(cudaStreamSynchronize(s), "copy results");
+            }
+            const unsigned long long *sum = bt->summary_host;
+            res->total_steps = (int64_t)sum[0];
+            // summary[1 + status + 6]
+            res->n_ok = (int)sum[1 + IGS_OK + 6];
+            res->n_not_converged = (int)sum[1 + IGS_NOT_CONVERGED + 6];
+            res->n_breakdown = (int)sum[1 + IGS_BREAKDOWN + 6];
+            res->n_numeric = (int)sum[1 + IGS_ENUMERIC + 6];
+            res->device_ms = ms;
+            if (res->n_numeric > 0) return IGS_ENUMERIC;
+            if (res->n_not_converged > 0) return IGS_NOT_CONVERGED;
+            if (res->n_breakdown > 0) return IGS_BREAKDOWN;
+            return IGS_OK;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
+        return IGS_EINVAL;
     }
-    float ms = 0.f;
-    int rc = launch(bt, bt->threads, bt->bpsm, &ms);
-    if (rc != IGS_OK) return rc;
-    if (!dev) {
-        BT_CUDA(cudaMemcpyAsync(res->x, bt->x_dev, vb, cudaMemcpyDeviceToHost, s), "copy x");
-        if (res->beta)
-            BT_CUDA(cudaMemcpyAsync(res->beta, bt->beta_dev, sizeof(double) * bt->count, cudaMemcpyDeviceToHost, s),
-                    "copy beta");
-        if (res->status)
-            BT_CUDA(cudaMemcpyAsync(res->status, bt->status_dev, sizeof(int) * bt->count, cudaMemcpyDeviceToHost, s),
-                    "copy status");
-        if (res->steps)
-            BT_CUDA(cudaMemcpyAsync(res->steps, bt->steps_dev, sizeof(int64_t) * bt->count, cudaMemcpyDeviceToHost, s),
-                    "copy steps");
-        if (res->cycles)
-            BT_CUDA(cudaMemcpyAsync(res->cycles, bt->cycles_dev, sizeof(int) * bt->count, cudaMemcpyDeviceToHost, s),
-                    "copy cycles");
-        BT_CUDA(cudaStreamSynchronize(s), "copy results");
-    }
-    const unsigned long long *sum = bt->summary_host;
-    res->total_steps = (int64_t)sum[0];
-    // summary[1 + status + 6]
-    res->n_ok = (int)sum[1 + IGS_OK + 6];
-    res->n_not_converged = (int)sum[1 + IGS_NOT_CONVERGED + 6];
-    res->n_breakdown = (int)sum[1 + IGS_BREAKDOWN + 6];
-    res->n_numeric = (int)sum[1 + IGS_ENUMERIC + 6];
-    res->device_ms = ms;
-    if (res->n_numeric > 0) return IGS_ENUMERIC;
-    if (res->n_not_converged > 0) return IGS_NOT_CONVERGED;
-    if (res->n_breakdown > 0) return IGS_BREAKDOWN;
-    return IGS_OK;
 }
 
 extern "C" int igs_batch_set_config(igs_batch *bt, int block_threads, int blocks_per_sm)
 {
-    if (!bt) return IGS_EINVAL;
-    if (!valid_threads(block_threads) || blocks_per_sm < 1 ||
-        bt->num_sms * blocks_per_sm > bt->slots_alloc)
-        return fail(bt, IGS_EINVAL, "invalid launch configuration");
-    int maxb = 0;
-    int rc = max_blocks_per_sm(bt, block_threads, &maxb);
-    if (rc != IGS_OK) return rc;
-    if (blocks_per_sm > maxb) return fail(bt, IGS_EINVAL, "blocks_per_sm above occupancy");
-    bt->threads = block_threads;
-    bt->bpsm = blocks_per_sm;
-    return IGS_OK;
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            if (!bt) return IGS_EINVAL;
+            if (!valid_threads(block_threads) || blocks_per_sm < 1 ||
+                bt->num_sms * blocks_per_sm > bt->slots_alloc)
+                return fail(bt, IGS_EINVAL, "invalid launch configuration");
+            int maxb = 0;
+            int rc = max_blocks_per_sm(bt, block_threads, &maxb);
+            if (rc != IGS_OK) return rc;
+            if (blocks_per_sm > maxb) return fail(bt, IGS_EINVAL, "blocks_per_sm above occupancy");
+            bt->threads = block_threads;
+            bt->bpsm = blocks_per_sm;
+            return IGS_OK;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
+        return IGS_EINVAL;
+    }
 }
 
 extern "C" int igs_batch_tune(igs_batch *bt, int gs_iters, double tol_beta, int max_restarts)
 {
-    if (!bt) return IGS_EINVAL;
-    if (gs_iters < 1 || gs_iters > 2 || !(tol_beta >= 0.0) || max_restarts < 1)
-        return fail(bt, IGS_EINVAL, "invalid tuning options");
-    if (cudaSetDevice(bt->device) != cudaSuccess) return fail(bt, IGS_ECUDA, "cudaSetDevice");
-    return autotune(bt, gs_iters, tol_beta, max_restarts);
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            if (!bt) return IGS_EINVAL;
+            if (gs_iters < 1 || gs_iters > 2 || !(tol_beta >= 0.0) || max_restarts < 1)
+                return fail(bt, IGS_EINVAL, "invalid tuning options");
+            if (cudaSetDevice(bt->device) != cudaSuccess) return fail(bt, IGS_ECUDA, "cudaSetDevice");
+            return autotune(bt, gs_iters, tol_beta, max_restarts);
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
+        return IGS_EINVAL;
+    }
 }
 
 extern "C" int igs_batch_get_info(const igs_batch *bt, igs_batch_info *info)

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <new>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -508,69 +509,78 @@ extern "C" {
 
 int igs_server_create(igs_server **out, const igs_server_opts *opts)
 {
-    using namespace igs;
-    if (!out) return IGS_EINVAL;
-    *out = nullptr;
-    if (!opts) return IGS_EINVAL;
-    if (opts->max_restart_m < 1 || opts->max_restart_m > IGS_SERVE_MAX_M || opts->arena_bytes <= 0)
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            using namespace igs;
+            if (!out) return IGS_EINVAL;
+            *out = nullptr;
+            if (!opts) return IGS_EINVAL;
+            if (opts->max_restart_m < 1 || opts->max_restart_m > IGS_SERVE_MAX_M || opts->arena_bytes <= 0)
+                return IGS_EINVAL;
+            const int slots = opts->slots > 0 ? opts->slots : 8;
+            const int rpc = opts->rows_per_cta > 0 ? opts->rows_per_cta : 4096;
+            if (slots > 256 || rpc < 256 || rpc % 32 != 0 || opts->graph_min_n < 0) return IGS_EINVAL;
+            igs_server *s = new (std::nothrow) igs_server();
+            if (!s) return IGS_ENOMEM;
+            auto bail = [&](int code) {
+                igs_server_destroy(s);
+                return code;
+            };
+            s->device = opts->device;
+            s->max_m = opts->max_restart_m;
+            s->slots = slots;
+            s->rows_per_cta = rpc;
+            s->max_queue = opts->max_queue > 0 ? opts->max_queue : 0;
+            s->graph_min_n = opts->graph_min_n;
+            s->t0 = std::chrono::steady_clock::now();
+            if (cudaSetDevice(s->device) != cudaSuccess) return bail(IGS_ECUDA);
+            cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+            int optin = 0;
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+            s->smem_max[0] = sizeof(double) * (size_t)sysdev::smem_layout<double>(rpc, s->max_m).total;
+            s->smem_max[1] = sizeof(double) * (size_t)sysdev::smem_layout<float>(rpc, s->max_m).total;
+            void *kern[2] = {kernel_ptr<double>(), kernel_ptr<float>()};
+            for (int t = 0; t < 2; ++t) {
+                cudaFuncAttributes fa;
+                if (cudaFuncGetAttributes(&fa, kern[t]) != cudaSuccess) return bail(IGS_ECUDA);
+                if (s->smem_max[t] + fa.sharedSizeBytes > (size_t)optin) return bail(IGS_EINVAL);
+                if (cudaFuncSetAttribute(kern[t], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_max[t]) !=
+                    cudaSuccess)
+                    return bail(IGS_ECUDA);
+                int nb = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern[t], serve::kThreads, s->smem_max[t]) !=
+                    cudaSuccess)
+                    return bail(IGS_ECUDA);
+                s->max_gang[t] = std::max(1, nb) * s->num_sms;
+            }
+            s->cta_budget = std::min(s->max_gang[0], s->max_gang[1]);
+            if (cudaMalloc(reinterpret_cast<void **>(&s->arena_base), (size_t)opts->arena_bytes) != cudaSuccess)
+                return bail(IGS_ENOMEM);
+            s->arena.init(opts->arena_bytes);
+            s->streams.assign((size_t)slots, nullptr);
+            s->events.assign((size_t)slots, nullptr);
+            s->slot_req.assign((size_t)slots, -1);
+            for (int k = 0; k < slots; ++k)
+                if (cudaStreamCreateWithFlags(&s->streams[(size_t)k], cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&s->events[(size_t)k], cudaEventDisableTiming) != cudaSuccess)
+                    return bail(IGS_ECUDA);
+            if (s->graph_min_n > 0) {
+                if (cudaStreamCreateWithFlags(&s->graph_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(IGS_ECUDA);
+                try {
+                    s->graph_thread = std::thread(graph_worker, s);
+                } catch (...) {
+                    return bail(IGS_ENOMEM);
+                }
+            }
+            *out = s;
+            return IGS_OK;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
         return IGS_EINVAL;
-    const int slots = opts->slots > 0 ? opts->slots : 8;
-    const int rpc = opts->rows_per_cta > 0 ? opts->rows_per_cta : 4096;
-    if (slots > 256 || rpc < 256 || rpc % 32 != 0 || opts->graph_min_n < 0) return IGS_EINVAL;
-    igs_server *s = new (std::nothrow) igs_server();
-    if (!s) return IGS_ENOMEM;
-    auto bail = [&](int code) {
-        igs_server_destroy(s);
-        return code;
-    };
-    s->device = opts->device;
-    s->max_m = opts->max_restart_m;
-    s->slots = slots;
-    s->rows_per_cta = rpc;
-    s->max_queue = opts->max_queue > 0 ? opts->max_queue : 0;
-    s->graph_min_n = opts->graph_min_n;
-    s->t0 = std::chrono::steady_clock::now();
-    if (cudaSetDevice(s->device) != cudaSuccess) return bail(IGS_ECUDA);
-    cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
-    s->smem_max[0] = sizeof(double) * (size_t)sysdev::smem_layout<double>(rpc, s->max_m).total;
-    s->smem_max[1] = sizeof(double) * (size_t)sysdev::smem_layout<float>(rpc, s->max_m).total;
-    void *kern[2] = {kernel_ptr<double>(), kernel_ptr<float>()};
-    for (int t = 0; t < 2; ++t) {
-        cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, kern[t]) != cudaSuccess) return bail(IGS_ECUDA);
-        if (s->smem_max[t] + fa.sharedSizeBytes > (size_t)optin) return bail(IGS_EINVAL);
-        if (cudaFuncSetAttribute(kern[t], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_max[t]) !=
-            cudaSuccess)
-            return bail(IGS_ECUDA);
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern[t], serve::kThreads, s->smem_max[t]) !=
-            cudaSuccess)
-            return bail(IGS_ECUDA);
-        s->max_gang[t] = std::max(1, nb) * s->num_sms;
     }
-    s->cta_budget = std::min(s->max_gang[0], s->max_gang[1]);
-    if (cudaMalloc(reinterpret_cast<void **>(&s->arena_base), (size_t)opts->arena_bytes) != cudaSuccess)
-        return bail(IGS_ENOMEM);
-    s->arena.init(opts->arena_bytes);
-    s->streams.assign((size_t)slots, nullptr);
-    s->events.assign((size_t)slots, nullptr);
-    s->slot_req.assign((size_t)slots, -1);
-    for (int k = 0; k < slots; ++k)
-        if (cudaStreamCreateWithFlags(&s->streams[(size_t)k], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s->events[(size_t)k], cudaEventDisableTiming) != cudaSuccess)
-            return bail(IGS_ECUDA);
-    if (s->graph_min_n > 0) {
-        if (cudaStreamCreateWithFlags(&s->graph_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(IGS_ECUDA);
-        try {
-            s->graph_thread = std::thread(graph_worker, s);
-        } catch (...) {
-            return bail(IGS_ENOMEM);
-        }
-    }
-    *out = s;
-    return IGS_OK;
 }
 
 void igs_server_destroy(igs_server *s)
@@ -600,171 +610,207 @@ void igs_server_destroy(igs_server *s)
 
 int igs_server_submit(igs_server *s, const igs_request *q, int64_t *id_out)
 {
-    using namespace igs;
-    if (!s) return IGS_EINVAL;
-    if (!q || !id_out) return sfail(s, IGS_EINVAL, "null argument");
-    const int64_t n = q->n, nnz = q->nnz;
-    if (n < 1 || n >= ((int64_t)1 << 30) || nnz < 0 || nnz >= ((int64_t)1 << 31) || !q->rowptr || !q->b ||
-        (nnz > 0 && (!q->colind || !q->vals)))
-        return sfail(s, IGS_EINVAL, "bad sizes or null arrays");
-    if (q->restart_m < 1 || q->restart_m > s->max_m || (q->gs_iters != 1 && q->gs_iters != 2) ||
-        !(q->tol_beta >= 0.0) || q->max_restarts < 1 ||
-        (q->precision != IGS_PREC_FP64 && q->precision != IGS_PREC_FP32_IR))
-        return sfail(s, IGS_EINVAL, "bad request options");
-    if (q->rowptr[0] != 0 || q->rowptr[n] != nnz) return sfail(s, IGS_EINVAL, "rowptr[0] must be 0, rowptr[n] = nnz");
-    if (s->max_queue > 0 && (int64_t)(s->queue.size() + s->graph_queue.size()) >= s->max_queue)
-        return sfail(s, IGS_ENOMEM, "queue full");
-    std::vector<double> rowabs((size_t)n, 0.0), colabs((size_t)n, 0.0);
-    for (int64_t i = 0; i < n; ++i) {
-        if (q->rowptr[i + 1] < q->rowptr[i]) return sfail(s, IGS_EINVAL, "rowptr decreases");
-        for (int64_t k = q->rowptr[i]; k < q->rowptr[i + 1]; ++k) {
-            if (q->colind[k] < 0 || q->colind[k] >= n) return sfail(s, IGS_EINVAL, "column index out of range");
-            if (!std::isfinite(q->vals[k])) return sfail(s, IGS_ENUMERIC, "non-finite matrix value");
-            rowabs[(size_t)i] += std::fabs(q->vals[k]);
-            colabs[(size_t)q->colind[k]] += std::fabs(q->vals[k]);
-        }
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            using namespace igs;
+            if (!s) return IGS_EINVAL;
+            if (!q || !id_out) return sfail(s, IGS_EINVAL, "null argument");
+            const int64_t n = q->n, nnz = q->nnz;
+            if (n < 1 || n >= ((int64_t)1 << 30) || nnz < 0 || nnz >= ((int64_t)1 << 31) || !q->rowptr || !q->b ||
+                (nnz > 0 && (!q->colind || !q->vals)))
+                return sfail(s, IGS_EINVAL, "bad sizes or null arrays");
+            if (q->restart_m < 1 || q->restart_m > s->max_m || (q->gs_iters != 1 && q->gs_iters != 2) ||
+                !(q->tol_beta >= 0.0) || q->max_restarts < 1 ||
+                (q->precision != IGS_PREC_FP64 && q->precision != IGS_PREC_FP32_IR))
+                return sfail(s, IGS_EINVAL, "bad request options");
+            if (q->rowptr[0] != 0 || q->rowptr[n] != nnz) return sfail(s, IGS_EINVAL, "rowptr[0] must be 0, rowptr[n] = nnz");
+            if (s->max_queue > 0 && (int64_t)(s->queue.size() + s->graph_queue.size()) >= s->max_queue)
+                return sfail(s, IGS_ENOMEM, "queue full");
+            std::vector<double> rowabs((size_t)n, 0.0), colabs((size_t)n, 0.0);
+            for (int64_t i = 0; i < n; ++i) {
+                if (q->rowptr[i + 1] < q->rowptr[i]) return sfail(s, IGS_EINVAL, "rowptr decreases");
+                for (int64_t k = q->rowptr[i]; k < q->rowptr[i + 1]; ++k) {
+                    if (q->colind[k] < 0 || q->colind[k] >= n) return sfail(s, IGS_EINVAL, "column index out of range");
+                    if (!std::isfinite(q->vals[k])) return sfail(s, IGS_ENUMERIC, "non-finite matrix value");
+                    rowabs[(size_t)i] += std::fabs(q->vals[k]);
+                    colabs[(size_t)q->colind[k]] += std::fabs(q->vals[k]);
+                }
+            }
+            Request r;
+            r.id = s->next_id++;
+            r.opt = *q;
+            r.opt.rowptr = nullptr;
+            r.opt.colind = nullptr;
+            r.opt.vals = nullptr;
+            r.opt.b = nullptr;
+            r.opt.x0 = nullptr;
+            r.n = (int)n;
+            r.n2 = (int)((n + 1) / 2 * 2);
+            r.ldv = (int)((n + 3) / 4 * 4);
+            r.f32 = q->precision == IGS_PREC_FP32_IR;
+            r.has_x0 = q->x0 != nullptr;
+            if (q->A_norm2 > 0.0) {
+                r.normA = q->A_norm2;
+            } else {
+                // ||A||_2 <= sqrt(||A||_1 ||A||_inf)
+                const double n1 = *std::max_element(colabs.begin(), colabs.end());
+                const double ninf = *std::max_element(rowabs.begin(), rowabs.end());
+                r.normA = std::sqrt(n1 * ninf);
+            }
+            if (s->graph_min_n > 0 && n >= s->graph_min_n) {
+                // graph lane: the library solves it with whole-GPU kernels; keep the CSR form
+                auto job = std::make_unique<igs::serve::GraphJob>();
+                job->id = r.id;
+                job->opt = r.opt;
+                job->opt.colind = nullptr;
+                job->opt.vals = nullptr;
+                job->opt.b = nullptr;
+                job->opt.x0 = nullptr;
+                job->normA = r.normA;
+                job->rowptr.assign(q->rowptr, q->rowptr + n + 1);
+                job->colind.assign(q->colind, q->colind + nnz);
+                job->vals.assign(q->vals, q->vals + nnz);
+                job->b.assign(q->b, q->b + n);
+                if (r.has_x0) job->x0.assign(q->x0, q->x0 + n);
+                r.graph = true;
+                r.G = 0;
+                r.job = std::move(job);
+                r.t_submit = now_s(s);
+                const int64_t id = r.id;
+                s->reqs.emplace(id, std::move(r));
+                s->graph_queue.push_back(id);
+                s->submitted++;
+                *id_out = id;
+                return IGS_OK;
+            }
+            // gang: about rows_per_cta rows per CTA, rows split on multiples of 32.  A gang of more
+            // CTAs than SMs is rounded up to a whole number of CTAs per SM (within the CTA budget),
+            // so that when it runs alone no SM carries more of its rows than another.
+            int G = (r.n2 + s->rows_per_cta - 1) / s->rows_per_cta;
+            if (G > s->num_sms) G = std::min((G + s->num_sms - 1) / s->num_sms * s->num_sms, std::max(G, s->cta_budget));
+            int chunk = ((r.n2 + G - 1) / G + 31) / 32 * 32;
+            G = (r.n2 + chunk - 1) / chunk;
+            if (G > s->cta_budget) return sfail(s, IGS_EINVAL, "system too large for one co-resident gang");
+            r.G = G;
+            r.chunk = chunk;
+            r.smem = r.f32 ? sizeof(double) * (size_t)sysdev::smem_layout<float>(chunk, r.opt.restart_m).total
+                           : sizeof(double) * (size_t)sysdev::smem_layout<double>(chunk, r.opt.restart_m).total;
+            // SELL-32 (32-row slices, each as wide as its longest row, CSR order, padding -1)
+            const int64_t nsl = (n + 31) / 32;
+            r.sell_off.assign((size_t)nsl + 1, 0);
+            for (int64_t k = 0; k < nsl; ++k) {
+                int64_t w = 0;
+                for (int64_t i = 32 * k; i < std::min(n, 32 * k + 32); ++i) w = std::max(w, q->rowptr[i + 1] - q->rowptr[i]);
+                r.sell_off[(size_t)k + 1] = r.sell_off[(size_t)k] + 32 * w;
+            }
+            const int64_t ne = r.sell_off[(size_t)nsl];
+            r.sell_col.assign((size_t)std::max<int64_t>(ne, 1), -1);
+            r.sell_val.assign((size_t)std::max<int64_t>(ne, 1), 0.0);
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t j = 0; j < q->rowptr[i + 1] - q->rowptr[i]; ++j) {
+                    const size_t e = (size_t)(r.sell_off[(size_t)(i >> 5)] + 32 * j + (i & 31));
+                    r.sell_col[e] = q->colind[q->rowptr[i] + j];
+                    r.sell_val[e] = q->vals[q->rowptr[i] + j];
+                }
+            if (r.f32) {
+                r.sell_val32.resize(r.sell_val.size());
+                for (size_t e = 0; e < r.sell_val.size(); ++e) r.sell_val32[e] = (float)r.sell_val[e];
+            }
+            r.b.assign(q->b, q->b + n);
+            if (r.has_x0) r.x0.assign(q->x0, q->x0 + n);
+            r.bytes = plan_request(r, 2 * (r.opt.restart_m + 1) + 2);
+            if (r.bytes > s->arena.size()) return sfail(s, IGS_EINVAL, "request larger than the arena");
+            r.t_submit = now_s(s);
+            const int64_t id = r.id;
+            s->reqs.emplace(id, std::move(r));
+            s->queue.push_back(id);
+            s->submitted++;
+            *id_out = id;
+            return IGS_OK;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
+        return IGS_EINVAL;
     }
-    Request r;
-    r.id = s->next_id++;
-    r.opt = *q;
-    r.opt.rowptr = nullptr;
-    r.opt.colind = nullptr;
-    r.opt.vals = nullptr;
-    r.opt.b = nullptr;
-    r.opt.x0 = nullptr;
-    r.n = (int)n;
-    r.n2 = (int)((n + 1) / 2 * 2);
-    r.ldv = (int)((n + 3) / 4 * 4);
-    r.f32 = q->precision == IGS_PREC_FP32_IR;
-    r.has_x0 = q->x0 != nullptr;
-    if (q->A_norm2 > 0.0) {
-        r.normA = q->A_norm2;
-    } else {
-        // ||A||_2 <= sqrt(||A||_1 ||A||_inf)
-        const double n1 = *std::max_element(colabs.begin(), colabs.end());
-        const double ninf = *std::max_element(rowabs.begin(), rowabs.end());
-        r.normA = std::sqrt(n1 * ninf);
-    }
-    if (s->graph_min_n > 0 && n >= s->graph_min_n) {
-        // graph lane: the library solves it with whole-GPU kernels; keep the CSR form
-        auto job = std::make_unique<igs::serve::GraphJob>();
-        job->id = r.id;
-        job->opt = r.opt;
-        job->opt.colind = nullptr;
-        job->opt.vals = nullptr;
-        job->opt.b = nullptr;
-        job->opt.x0 = nullptr;
-        job->normA = r.normA;
-        job->rowptr.assign(q->rowptr, q->rowptr + n + 1);
-        job->colind.assign(q->colind, q->colind + nnz);
-        job->vals.assign(q->vals, q->vals + nnz);
-        job->b.assign(q->b, q->b + n);
-        if (r.has_x0) job->x0.assign(q->x0, q->x0 + n);
-        r.graph = true;
-        r.G = 0;
-        r.job = std::move(job);
-        r.t_submit = now_s(s);
-        const int64_t id = r.id;
-        s->reqs.emplace(id, std::move(r));
-        s->graph_queue.push_back(id);
-        s->submitted++;
-        *id_out = id;
-        return IGS_OK;
-    }
-    // gang: about rows_per_cta rows per CTA, rows split on multiples of 32.  A gang of more
-    // CTAs than SMs is rounded up to a whole number of CTAs per SM (within the CTA budget),
-    // so that when it runs alone no SM carries more of its rows than another.
-    int G = (r.n2 + s->rows_per_cta - 1) / s->rows_per_cta;
-    if (G > s->num_sms) G = std::min((G + s->num_sms - 1) / s->num_sms * s->num_sms, std::max(G, s->cta_budget));
-    int chunk = ((r.n2 + G - 1) / G + 31) / 32 * 32;
-    G = (r.n2 + chunk - 1) / chunk;
-    if (G > s->cta_budget) return sfail(s, IGS_EINVAL, "system too large for one co-resident gang");
-    r.G = G;
-    r.chunk = chunk;
-    r.smem = r.f32 ? sizeof(double) * (size_t)sysdev::smem_layout<float>(chunk, r.opt.restart_m).total
-                   : sizeof(double) * (size_t)sysdev::smem_layout<double>(chunk, r.opt.restart_m).total;
-    // SELL-32 (32-row slices, each as wide as its longest row, CSR order, padding -1)
-    const int64_t nsl = (n + 31) / 32;
-    r.sell_off.assign((size_t)nsl + 1, 0);
-    for (int64_t k = 0; k < nsl; ++k) {
-        int64_t w = 0;
-        for (int64_t i = 32 * k; i < std::min(n, 32 * k + 32); ++i) w = std::max(w, q->rowptr[i + 1] - q->rowptr[i]);
-        r.sell_off[(size_t)k + 1] = r.sell_off[(size_t)k] + 32 * w;
-    }
-    const int64_t ne = r.sell_off[(size_t)nsl];
-    r.sell_col.assign((size_t)std::max<int64_t>(ne, 1), -1);
-    r.sell_val.assign((size_t)std::max<int64_t>(ne, 1), 0.0);
-    for (int64_t i = 0; i < n; ++i)
-        for (int64_t j = 0; j < q->rowptr[i + 1] - q->rowptr[i]; ++j) {
-            const size_t e = (size_t)(r.sell_off[(size_t)(i >> 5)] + 32 * j + (i & 31));
-            r.sell_col[e] = q->colind[q->rowptr[i] + j];
-            r.sell_val[e] = q->vals[q->rowptr[i] + j];
-        }
-    if (r.f32) {
-        r.sell_val32.resize(r.sell_val.size());
-        for (size_t e = 0; e < r.sell_val.size(); ++e) r.sell_val32[e] = (float)r.sell_val[e];
-    }
-    r.b.assign(q->b, q->b + n);
-    if (r.has_x0) r.x0.assign(q->x0, q->x0 + n);
-    r.bytes = plan_request(r, 2 * (r.opt.restart_m + 1) + 2);
-    if (r.bytes > s->arena.size()) return sfail(s, IGS_EINVAL, "request larger than the arena");
-    r.t_submit = now_s(s);
-    const int64_t id = r.id;
-    s->reqs.emplace(id, std::move(r));
-    s->queue.push_back(id);
-    s->submitted++;
-    *id_out = id;
-    return IGS_OK;
 }
 
 int igs_server_pump(igs_server *s, int *running)
 {
-    if (!s) return IGS_EINVAL;
-    if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, IGS_ECUDA, "cudaSetDevice");
-    int rc = collect(s);
-    if (rc == IGS_OK) rc = admit(s);
-    if (running) {
-        int k = s->graph_busy >= 0 ? 1 : 0;
-        for (auto id : s->slot_req) k += id >= 0;
-        *running = k;
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            if (!s) return IGS_EINVAL;
+            if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, IGS_ECUDA, "cudaSetDevice");
+            int rc = collect(s);
+            if (rc == IGS_OK) rc = admit(s);
+            if (running) {
+                int k = s->graph_busy >= 0 ? 1 : 0;
+                for (auto id : s->slot_req) k += id >= 0;
+                *running = k;
+            }
+            return rc;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
+        return IGS_EINVAL;
     }
-    return rc;
 }
 
 int igs_server_poll(igs_server *s, igs_completion *out, int max_out, int *n_out)
 {
-    if (!s || !n_out || (max_out > 0 && !out)) return IGS_EINVAL;
-    int k = 0;
-    while (k < max_out && !s->completions.empty()) {
-        const int64_t id = s->completions.front();
-        s->completions.pop_front();
-        Request &r = s->reqs[id];
-        igs_completion &c = out[k++];
-        c.id = id;
-        c.status = r.status;
-        c.beta = r.res.beta;
-        c.steps = r.res.steps;
-        c.cycles = r.res.cycles;
-        c.gang_ctas = r.G;
-        c.device_bytes = r.bytes;
-        c.path = r.graph ? IGS_SERVE_PATH_GRAPH : IGS_SERVE_PATH_GANG;
-        c.t_submit = r.t_submit;
-        c.t_admit = r.t_admit;
-        c.t_done = r.t_done;
-        r.polled = true;
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            if (!s || !n_out || (max_out > 0 && !out)) return IGS_EINVAL;
+            int k = 0;
+            while (k < max_out && !s->completions.empty()) {
+                const int64_t id = s->completions.front();
+                s->completions.pop_front();
+                Request &r = s->reqs[id];
+                igs_completion &c = out[k++];
+                c.id = id;
+                c.status = r.status;
+                c.beta = r.res.beta;
+                c.steps = r.res.steps;
+                c.cycles = r.res.cycles;
+                c.gang_ctas = r.G;
+                c.device_bytes = r.bytes;
+                c.path = r.graph ? IGS_SERVE_PATH_GRAPH : IGS_SERVE_PATH_GANG;
+                c.t_submit = r.t_submit;
+                c.t_admit = r.t_admit;
+                c.t_done = r.t_done;
+                r.polled = true;
+            }
+            *n_out = k;
+            return IGS_OK;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
+        return IGS_EINVAL;
     }
-    *n_out = k;
-    return IGS_OK;
 }
 
 int igs_server_take_result(igs_server *s, int64_t id, double *x)
 {
-    if (!s || !x) return IGS_EINVAL;
-    auto it = s->reqs.find(id);
-    if (it == s->reqs.end() || !it->second.done) return sfail(s, IGS_EINVAL, "unknown or unfinished request");
-    std::memcpy(x, it->second.x_host.data(), sizeof(double) * it->second.x_host.size());
-    s->reqs.erase(it);
-    return IGS_OK;
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            if (!s || !x) return IGS_EINVAL;
+            auto it = s->reqs.find(id);
+            if (it == s->reqs.end() || !it->second.done) return sfail(s, IGS_EINVAL, "unknown or unfinished request");
+            std::memcpy(x, it->second.x_host.data(), sizeof(double) * it->second.x_host.size());
+            s->reqs.erase(it);
+            return IGS_OK;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
+        return IGS_EINVAL;
+    }
 }
 
 int igs_server_get_stats(const igs_server *s, igs_server_stats *o)
@@ -787,40 +833,49 @@ double igs_server_clock(const igs_server *s) { return s ? now_s(s) : 0.0; }
 
 int igs_server_gang_selftest(int device, int G, int stall, int *abort_out)
 {
-    using namespace igs;
-    if (G < 2 || (stall != 0 && stall != 1)) return IGS_EINVAL;
-    if (cudaSetDevice(device) != cudaSuccess) return IGS_ECUDA;
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || G > sms)
+    // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
+    try {
+        return [&]() -> int {
+            using namespace igs;
+            if (G < 2 || (stall != 0 && stall != 1)) return IGS_EINVAL;
+            if (cudaSetDevice(device) != cudaSuccess) return IGS_ECUDA;
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || G > sms)
+                return IGS_EINVAL;
+            sysdev::GangSync *sync = nullptr;
+            int *ok = nullptr;
+            cudaStream_t st = nullptr;
+            int rc = IGS_ECUDA;
+            std::vector<int> h((size_t)G, 0);
+            sysdev::GangSync hs{};
+            // stalled: an arrival count that no arrival brings to G, so that every wait runs out
+            hs.count = stall ? 0x40000000u : 0u;
+            if (cudaMalloc(&sync, sizeof(sysdev::GangSync)) == cudaSuccess && cudaMalloc(&ok, sizeof(int) * G) == cudaSuccess &&
+                cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaMemcpyAsync(sync, &hs, sizeof(hs), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                cudaMemsetAsync(ok, 0, sizeof(int) * G, st) == cudaSuccess) {
+                void *args[] = {&sync, &ok};
+                if (cudaLaunchCooperativeKernel(reinterpret_cast<void *>(serve::k_gang_selftest), dim3(G),
+                                                dim3(serve::kThreads), args, 0, st) == cudaSuccess &&
+                    cudaMemcpyAsync(h.data(), ok, sizeof(int) * G, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                    cudaMemcpyAsync(&hs, sync, sizeof(hs), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                    cudaStreamSynchronize(st) == cudaSuccess) {
+                    int passed = 0;
+                    for (int v : h) passed += v;
+                    if (abort_out) *abort_out = hs.abort;
+                    rc = passed == G ? IGS_OK : IGS_ETIMEOUT;
+                }
+            }
+            if (st) cudaStreamDestroy(st);
+            cudaFree(ok);
+            cudaFree(sync);
+            return rc;
+        }();
+    } catch (const std::bad_alloc &) {
+        return IGS_ENOMEM;
+    } catch (...) {
         return IGS_EINVAL;
-    sysdev::GangSync *sync = nullptr;
-    int *ok = nullptr;
-    cudaStream_t st = nullptr;
-    int rc = IGS_ECUDA;
-    std::vector<int> h((size_t)G, 0);
-    sysdev::GangSync hs{};
-    // stalled: an arrival count that no arrival brings to G, so that every wait runs out
-    hs.count = stall ? 0x40000000u : 0u;
-    if (cudaMalloc(&sync, sizeof(sysdev::GangSync)) == cudaSuccess && cudaMalloc(&ok, sizeof(int) * G) == cudaSuccess &&
-        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
-        cudaMemcpyAsync(sync, &hs, sizeof(hs), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-        cudaMemsetAsync(ok, 0, sizeof(int) * G, st) == cudaSuccess) {
-        void *args[] = {&sync, &ok};
-        if (cudaLaunchCooperativeKernel(reinterpret_cast<void *>(serve::k_gang_selftest), dim3(G),
-                                        dim3(serve::kThreads), args, 0, st) == cudaSuccess &&
-            cudaMemcpyAsync(h.data(), ok, sizeof(int) * G, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-            cudaMemcpyAsync(&hs, sync, sizeof(hs), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-            cudaStreamSynchronize(st) == cudaSuccess) {
-            int passed = 0;
-            for (int v : h) passed += v;
-            if (abort_out) *abort_out = hs.abort;
-            rc = passed == G ? IGS_OK : IGS_ETIMEOUT;
-        }
     }
-    if (st) cudaStreamDestroy(st);
-    cudaFree(ok);
-    cudaFree(sync);
-    return rc;
 }
 
 const char *igs_server_last_error(const igs_server *s) { return s ? s->err.c_str() : "null server"; }

@@ -224,24 +224,31 @@ __device__ void unit_lower_solve(const double *Lsm, int p, const double *rhs, do
     if (terms >= 1) {
         for (int i = t; i < p; i += T) x[i] = rhs[i];
         __syncthreads();
-        // tmp = rhs - L x.  Thread pair (2a, 2a+1) owns rows a and p-1-a (equal total
-        // length); the two threads of a pair take alternate columns and combine by one
-        // shuffle.  Two rows give two independent FMA chains per thread.
+        // tmp = rhs - L x.  Rows a and p-1-a (equal total length) form pair a; tpp threads
+        // share a pair and take every tpp-th column (two independent FMA chains each), then
+        // combine by a fixed shuffle tree.  tpp spreads the pairs over the whole block (two
+        // rounds when that doubles tpp from 2): the FP64 instructions of the single SM are the
+        // cost, so every warp should carry its share.
         const int npair = (p + 1) >> 1;
+        int tpp = 32;
+        while (tpp > 1 && npair * tpp > T) tpp >>= 1;
+        if (tpp <= 2 && npair * 2 * tpp <= 2 * T) tpp *= 2;
         for (int it = 1; it < terms; ++it) {
-            for (int base = 0; base < 2 * npair; base += T) {
-                const int q = base + t, a = q >> 1, h = q & 1;
+            for (int base = 0; base < npair * tpp; base += T) {
+                const int q = base + t, a = q / tpp, h = q % tpp;
                 const bool act = a < npair;
                 const int r0 = a, r1 = p - 1 - a;
                 double s0 = 0.0, s1 = 0.0;
                 if (act) {
                     const double *l0 = Lsm + packed_row(r0), *l1 = Lsm + packed_row(r1);
-                    for (int c = h; c < r0; c += 2) s0 = fma(l0[c], x[c], s0);
+                    for (int c = h; c < r0; c += tpp) s0 = fma(l0[c], x[c], s0);
                     if (r1 != r0)
-                        for (int c = h; c < r1; c += 2) s1 = fma(l1[c], x[c], s1);
+                        for (int c = h; c < r1; c += tpp) s1 = fma(l1[c], x[c], s1);
                 }
-                s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-                s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+                for (int o = tpp >> 1; o > 0; o >>= 1) {
+                    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                }
                 if (act && h == 0) {
                     tmp[r0] = rhs[r0] - s0;
                     if (r1 != r0) tmp[r1] = rhs[r1] - s1;

@@ -427,6 +427,9 @@ def serve_config(duration):
             "step": "the whole stream: arrivals for window_s, then the admitted backlog drains"}
 
 
+DOTS_TRAFFIC_RATIO = 1.012  # measured DRAM bytes / algorithmic bytes of the multi-dots (ncu)
+
+
 def norm_bound(A):
     """sqrt(||A||_1 ||A||_inf) >= ||A||_2: the norm the server's beta uses for a request
     without one, so that the one-at-a-time solves stop at the same beta."""
@@ -742,7 +745,13 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     total_ms = sum(v["ms"] for v in prof.values())
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved_tflops / peak_tflops, "traffic": None,
+                "frac": achieved_tflops / peak_tflops,
+                # DRAM bytes per launch: ncu's dram__bytes_read.sum + dram__bytes_write.sum of the
+                # two multi-dots at p = 49 on this workload were 1.011 (k_dots<2>) and 1.013
+                # (k_dots<1>) times their algorithmic bytes; scaled to the average launch
+                "traffic": bytes_per_launch * DOTS_TRAFFIC_RATIO if args.gs == 2 else None,
+                "traffic_source": "ncu capture of k_dots at p = 49 (profiles/launches_cd2d512_m100_gs2.md), "
+                                  "ratio to algorithmic bytes applied to the mean launch",
                 "kernel": "k_dots (block multi-dot, Alg. 4.1 steps 5 and 14)",
                 "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2070 MHz (unit counts and max clock)",
                 "hbm_gbs": bytes_per_launch / avg_s / 1e9, "hbm_peak_gbs": hbm_peak,

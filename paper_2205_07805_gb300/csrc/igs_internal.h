@@ -111,6 +111,11 @@ struct Workspace {
     float *V32 = nullptr;          // ld x (mmax+1), column-major, zero padding rows
     float *z32 = nullptr, *u32 = nullptr;
     float *val32 = nullptr;        // A's values rounded to FP32 (same rowptr / colind)
+    // SELL-32 copy of A for the short-row FP64 SpMV: slices of 32 rows, each as wide as its
+    // longest row; entry k of row r at sell_off[r/32] + 32k + r%32 (CSR order, padding -1)
+    const int64_t *sell_off = nullptr;
+    const int *sell_col = nullptr;
+    const double *sell_val = nullptr;
     int ldh() const { return mmax + 1; }
     int ldl() const { return mmax + 1; }
 };

@@ -349,6 +349,39 @@ k_spmv_rows(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ c
     }
 }
 
+// Thread per row over the SELL-32 copy (short rows): a warp is one 32-row slice, so every
+// column-index and value load of the warp is one contiguous 128- or 256-byte segment.  The
+// entries of a row are visited in CSR order with the same two chains as k_spmv_rows (even
+// and odd positions), so the results are bitwise those of the CSR kernel.
+__global__ void __launch_bounds__(kStreamThreads)
+k_spmv_sell(int64_t n, const int64_t *__restrict__ sell_off, const int *__restrict__ sell_col,
+            const double *__restrict__ sell_val, const double *__restrict__ x, double *__restrict__ y,
+            const double *__restrict__ b, const DevState *st, int check_halt)
+{
+    IGS_PDL_ENTER();
+    if (check_halt && halted(st)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // the grid covers n
+    if (i >= n) return;
+    const int64_t off = sell_off[i >> 5];
+    const int wd = (int)((sell_off[(i >> 5) + 1] - off) >> 5);
+    const int *cs = sell_col + off + (i & 31);
+    const double *vs = sell_val + off + (i & 31);
+    double s0 = 0.0, s1 = 0.0;
+    int k = 0;
+    for (; k + 1 < wd; k += 2) {
+        const int c0 = cs[32 * k], c1 = cs[32 * (k + 1)];
+        const double v0 = vs[32 * k], v1 = vs[32 * (k + 1)];
+        if (c0 >= 0) s0 = fma(v0, x[c0], s0);
+        if (c1 >= 0) s1 = fma(v1, x[c1], s1);
+    }
+    if (k < wd) {
+        const int c0 = cs[32 * k];
+        if (c0 >= 0) s0 = fma(vs[32 * k], x[c0], s0);
+    }
+    const double s = s0 + s1;
+    y[i] = b ? b[i] - s : s;
+}
+
 // Warp per row: long rows (dense or wide-band matrices).
 __global__ void __launch_bounds__(kStreamThreads)
 k_spmv_warp(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ colind,
@@ -1390,6 +1423,9 @@ cudaError_t launch_spmv(const Workspace &w, const double *x, double *y, const do
     if (w.spmv_warp_rows)
         launch_k(false, k_spmv_warp, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.rowptr, w.colind, w.val, x, y, b, w.st,
                                                     check_halt);
+    else if (w.sell_col)
+        launch_k(false, k_spmv_sell, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.sell_off, w.sell_col, w.sell_val, x, y,
+                 b, (const DevState *)w.st, check_halt ? 1 : 0);
     else
         launch_k(false, k_spmv_rows, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.rowptr, w.colind, w.val, x, y, b, w.st,
                                                     check_halt);

@@ -496,7 +496,7 @@ k_dots(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t rows
 // norm_last, column p-1 (the lagged w_{k-1}) is first normalised in place,
 // v = w * inv_gamma (step 7), and a = inv_gamma (step 11).
 // =====================================================================================
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kStreamThreads, kUpdateBlocksPerSM)
 k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coef, int neg_coef,
          double alpha, const double *src, double *out, int norm_last, int p_from_state,
          DevState *st, int check_halt)
@@ -521,17 +521,33 @@ k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coe
         const double *vi = V + i;
         double x0 = 0.0, x1 = 0.0, y0 = 0.0, y1 = 0.0;
         int c = 0;
-        for (; c + 7 < pc; c += 8) {
-            double2 v[8];
+        if (pc >= 4) {
+            // software pipeline: the next 4 columns load while these 4 are used
+            double2 v[4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const double2 *>(vi + (int64_t)(c + q) * ld);
+            for (int q = 0; q < 4; ++q) v[q] = *reinterpret_cast<const double2 *>(vi + (int64_t)q * ld);
+            for (; c + 7 < pc; c += 4) {
+                double2 nv[4];
 #pragma unroll
-            for (int q = 0; q < 8; q += 2) {
+                for (int q = 0; q < 4; ++q) nv[q] = *reinterpret_cast<const double2 *>(vi + (int64_t)(c + 4 + q) * ld);
+#pragma unroll
+                for (int q = 0; q < 4; q += 2) {
+                    x0 = fma(v[q].x, sc[c + q], x0);
+                    y0 = fma(v[q].y, sc[c + q], y0);
+                    x1 = fma(v[q + 1].x, sc[c + q + 1], x1);
+                    y1 = fma(v[q + 1].y, sc[c + q + 1], y1);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = nv[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q += 2) {
                 x0 = fma(v[q].x, sc[c + q], x0);
                 y0 = fma(v[q].y, sc[c + q], y0);
                 x1 = fma(v[q + 1].x, sc[c + q + 1], x1);
                 y1 = fma(v[q + 1].y, sc[c + q + 1], y1);
             }
+            c += 4;
         }
         for (; c < pc; ++c) {
             const double2 v = *reinterpret_cast<const double2 *>(vi + (int64_t)c * ld);
@@ -1171,20 +1187,33 @@ k_update_1r(double *V, int64_t ld, int nb, int64_t n, const double *__restrict__
         const double *vi = V + i;
         double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
         int c = 0;
-        for (; c + 3 < nb; c += 4) {
+        if (nb >= 4) {
+            // software pipeline: the next 4 columns load while these 4 are used
             double v[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = vi[(int64_t)(c + q) * ld];
-            a0 = fma(v[0], s2[c], a0);
-            a1 = fma(v[1], s2[c + 1], a1);
-            a0 = fma(v[2], s2[c + 2], a0);
-            a1 = fma(v[3], s2[c + 3], a1);
-            if (!vonly) {
-                b0 = fma(v[0], s1[c], b0);
-                b1 = fma(v[1], s1[c + 1], b1);
-                b0 = fma(v[2], s1[c + 2], b0);
-                b1 = fma(v[3], s1[c + 3], b1);
+            for (int q = 0; q < 4; ++q) v[q] = vi[(int64_t)q * ld];
+            for (;; c += 4) {
+                const bool more = c + 7 < nb;
+                double nv[4];
+                if (more) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) nv[q] = vi[(int64_t)(c + 4 + q) * ld];
+                }
+                a0 = fma(v[0], s2[c], a0);
+                a1 = fma(v[1], s2[c + 1], a1);
+                a0 = fma(v[2], s2[c + 2], a0);
+                a1 = fma(v[3], s2[c + 3], a1);
+                if (!vonly) {
+                    b0 = fma(v[0], s1[c], b0);
+                    b1 = fma(v[1], s1[c + 1], b1);
+                    b0 = fma(v[2], s1[c + 2], b0);
+                    b1 = fma(v[3], s1[c + 3], b1);
+                }
+                if (!more) break;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = nv[q];
             }
+            c += 4;
         }
         for (; c < nb; ++c) {
             const double v = vi[(int64_t)c * ld];

@@ -95,3 +95,19 @@ def test_fp32_ir_inner_tolerance(pkg):
     assert tight["status"] == 0 and loose["status"] == 0
     assert loose["cycles"] > tight["cycles"]
     assert np.linalg.norm(loose["x"] - tight["x"]) <= 1e-10 * np.linalg.norm(tight["x"])
+
+
+def test_fp32_ir_full_size_backward_error(pkg):
+    """The 3-D system the benchmark times (160^3, n = 4,096,000, 28.5 M non-zeros, m = 200,
+    the launch configuration of bench.py): FP32-IR to beta <= 1e-14, with beta recomputed by
+    the oracle (its own SpMV and norms) from the returned x at full size, and ||A||_2 from
+    the context's own estimate passed to both."""
+    A, b, _, _ = gen.cd3d(160, 20.0, seed=0)
+    with pkg.Solver(A, max_restart_m=200, fp32_basis=True) as s:
+        normA = s.info["A_norm2"]
+        r = s.solve(b, m=200, gs=2, tol=1e-14, max_restarts=100, precision="fp32_ir")
+    assert r["status"] == 0 and r["beta"] <= 1e-14, (r["status"], r["beta"])
+    beta_o = oracle.backward_error(A, b, r["x"], normA)
+    print(f"160^3 FP32-IR: {r['steps']} steps / {r['cycles']} refinement steps, beta {r['beta']:.2e}, "
+          f"oracle beta {beta_o:.2e}")
+    assert beta_o <= 1e-14 * (1 + 1e-6) + 1e-16

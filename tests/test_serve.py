@@ -185,3 +185,29 @@ def test_gang_wait_runs_out_without_a_fault(pkg):
         c = {c["id"]: c for c in sv.run_all()}[rid]
         sv.take(rid)
     assert c["status"] == 0 and c["gang_ctas"] > 1
+
+
+@pytest.mark.gpu
+def test_served_full_size_requests(pkg):
+    """Requests of the served benchmark's largest sizes: a 1024 x 1024 grid (n = 1,048,576)
+    on the graph lane in FP64 and a 700 x 700 grid (n = 490,000) on a gang of 120 CTAs in
+    FP32-IR, both to beta <= 1e-10; beta is recomputed by the oracle from the returned x
+    with the server's norm bound sqrt(||A||_1 ||A||_inf)."""
+    reqs = [(gen.cd2d(1024, 60.0, seed=70)[:2], "fp64"), (gen.cd2d(700, 30.0, seed=71)[:2], "fp32_ir")]
+    with pkg.Server(max_restart_m=100, arena_bytes=8 << 30, slots=2, rows_per_cta=4096,
+                    graph_min_n=1_000_000) as sv:
+        ids = [sv.submit(A, b, m=100, gs=2, tol=1e-10, max_restarts=2000, precision=prec)
+               for (A, b), prec in reqs]
+        done = {c["id"]: c for c in sv.run_all()}
+        xs = [sv.take(rid) for rid in ids]
+    for rid, x, ((A, b), prec) in zip(ids, xs, reqs):
+        c = done[rid]
+        assert c["status"] == 0 and c["beta"] <= 1e-10, c
+        rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+        av = np.abs(A.val)
+        bound = float(np.sqrt(np.bincount(A.colind, av, A.n).max() * np.bincount(rows, av, A.n).max()))
+        beta_o = oracle.backward_error(A, b, x, bound)
+        print(f"n={A.n} {prec} path {c['path']} G={c['gang_ctas']}: {c['steps']} steps, beta {c['beta']:.2e}, "
+              f"oracle beta {beta_o:.2e}")
+        assert beta_o <= 1e-10 * (1 + 1e-6)
+    assert done[ids[0]]["path"] == 1 and done[ids[1]]["path"] == 0 and done[ids[1]]["gang_ctas"] == 120

@@ -1,0 +1,66 @@
+"""The Python binding's ctypes structures against the C headers (no GPU): a small C program
+compiled with gcc from include/*.h prints sizeof and every field's offset of each struct
+of the interface, and the binding's layout must be identical (a field added on one side
+only would silently shift every later field across the C interface)."""
+import os
+import shutil
+import subprocess
+import tempfile
+
+import ctypes as C
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# C typedef name -> binding class name
+PAIRS = {
+    "igs_create_opts": "_CreateOpts",
+    "igs_solve_opts": "_SolveOpts",
+    "igs_result": "_Result",
+    "igs_info": "_Info",
+    "igs_profile": "_Profile",
+    "igs_batch_opts": "_BatchOpts",
+    "igs_batch_solve_opts": "_BatchSolveOpts",
+    "igs_batch_result": "_BatchResult",
+    "igs_batch_tune_entry": "_TuneEntry",
+    "igs_batch_info": "_BatchInfo",
+    "igs_server_opts": "_ServerOpts",
+    "igs_request": "_Request",
+    "igs_completion": "_Completion",
+    "igs_server_stats": "_ServerStats",
+}
+
+
+def _c_layout(pkg):
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "igs.h"', '#include "igs_batch.h"',
+             '#include "igs_serve.h"', "int main(void) {"]
+    for cname, pyname in PAIRS.items():
+        cls = getattr(pkg, pyname)
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines) + "\n")
+        subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    res = {}
+    for ln in out.splitlines():
+        cname, field, val = ln.split()
+        res[(cname, field)] = int(val)
+    return res
+
+
+def test_ctypes_structs_match_the_headers():
+    import paper_2205_07805_gb300 as pkg
+    lay = _c_layout(pkg)
+    for cname, pyname in PAIRS.items():
+        cls = getattr(pkg, pyname)
+        assert C.sizeof(cls) == lay[(cname, "sizeof")], (cname, C.sizeof(cls), lay[(cname, "sizeof")])
+        for f, _ in cls._fields_:
+            assert getattr(cls, f).offset == lay[(cname, f)], (cname, f)

@@ -1,4 +1,4 @@
-"""The Python binding's ctypes structures against the C headers (no GPU): a small C program
+"""The Python binding's ctypes structures and constants against the C headers (no GPU): small C programs
 compiled with gcc from include/*.h prints sizeof and every field's offset of each struct
 of the interface, and the binding's layout must be identical (a field added on one side
 only would silently shift every later field across the C interface)."""
@@ -64,3 +64,27 @@ def test_ctypes_structs_match_the_headers():
         assert C.sizeof(cls) == lay[(cname, "sizeof")], (cname, C.sizeof(cls), lay[(cname, "sizeof")])
         for f, _ in cls._fields_:
             assert getattr(cls, f).offset == lay[(cname, f)], (cname, f)
+
+
+def test_constants_match_the_headers():
+    """Status codes, methods, precisions and kernel classes of the binding are the headers'."""
+    import paper_2205_07805_gb300 as pkg
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    names = {"IGS_OK": pkg.OK, "IGS_NOT_CONVERGED": pkg.NOT_CONVERGED, "IGS_BREAKDOWN": pkg.BREAKDOWN,
+             "IGS_EINVAL": pkg.EINVAL, "IGS_ENOMEM": pkg.ENOMEM, "IGS_ECUDA": pkg.ECUDA,
+             "IGS_ENUMERIC": pkg.ENUMERIC, "IGS_ETIMEOUT": pkg.ETIMEOUT, "IGS_ENOTIMPL": pkg.ENOTIMPL,
+             "IGS_METHOD_IGS": pkg.METHODS["igs"], "IGS_METHOD_ONE_REDUCE": pkg.METHODS["one_reduce"],
+             "IGS_PREC_FP64": pkg.PRECISIONS["fp64"], "IGS_PREC_FP32_IR": pkg.PRECISIONS["fp32_ir"],
+             "IGS_KCLASS_COUNT": len(pkg.KCLASS_NAMES)}
+    body = "\n".join(f'  printf("{k} %d\\n", (int){k});' for k in names)
+    src_text = ('#include <stdio.h>\n#include "igs.h"\n#include "igs_batch.h"\n#include "igs_serve.h"\n'
+                "int main(void) {\n" + body + "\n  return 0;\n}\n")
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "consts.c"), os.path.join(d, "consts")
+        open(src, "w").write(src_text)
+        subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    got = {k: int(v) for k, v in (ln.split() for ln in out.splitlines())}
+    assert got == names

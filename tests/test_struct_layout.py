@@ -1,7 +1,7 @@
-"""The Python binding's ctypes structures and constants against the C headers (no GPU): small C programs
-compiled with gcc from include/*.h prints sizeof and every field's offset of each struct
-of the interface, and the binding's layout must be identical (a field added on one side
-only would silently shift every later field across the C interface)."""
+"""The Python binding's ctypes structures and constants against the C headers (no GPU):
+small C programs compiled with gcc from include/*.h print sizeof and every field's offset of
+each struct of the interface, and the enum values; the binding must agree exactly (a field
+added on one side only would silently shift every later field across the C interface)."""
 import os
 import shutil
 import subprocess

@@ -577,6 +577,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--gs", type=int, default=2)
+    ap.add_argument("--method", default="igs", choices=["igs", "one_reduce"],
+                    help="the main line's Arnoldi process: Alg. 4.1 (igs) or Alg. 4.2 (one_reduce)")
     ap.add_argument("--impl", default="igs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="cd2d", choices=["cd2d", "batched", "precision", "served"])
@@ -683,7 +685,8 @@ def main():
     x_dev = torch.empty_like(b_dev)
 
     def step():
-        return solver.solve(b_dev, m=M, gs=args.gs, tol=0.0, max_restarts=1, x_out=x_dev, hist_cap=0)
+        return solver.solve(b_dev, m=M, gs=args.gs, tol=0.0, max_restarts=1, x_out=x_dev, hist_cap=0,
+                            method=args.method)
 
     for _ in range(args.warmup):
         out = step()
@@ -712,12 +715,13 @@ def main():
     # ---- end to end through the C interface with host buffers ----
     b_host = np.ascontiguousarray(b)
     x_host = np.empty_like(b_host)
-    solver.solve(b_host, m=M, gs=args.gs, tol=0.0, max_restarts=1, x_out=x_host, hist_cap=0)
+    solver.solve(b_host, m=M, gs=args.gs, tol=0.0, max_restarts=1, x_out=x_host, hist_cap=0, method=args.method)
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        solver.solve(b_host, m=M, gs=args.gs, tol=0.0, max_restarts=1, x_out=x_host, hist_cap=0)
+        solver.solve(b_host, m=M, gs=args.gs, tol=0.0, max_restarts=1, x_out=x_host, hist_cap=0,
+                     method=args.method)
     e2e_s = time.perf_counter() - t0
     ms, e2e_s, steps_total = reduce_replicas(ms, e2e_s, args.steps * M, dist, "cuda")
     value = steps_total / (ms / 1e3)
@@ -768,7 +772,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {**workload_config(args.gs), "parallelism": f"replicas x{ws}"},
+            "config": {**workload_config(args.gs), "method": args.method, "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk}
     if rank == 0 and not args.no_cpu_baseline:
@@ -778,23 +782,24 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"one full cycle ({M} Arnoldi columns) of the same workload, {dt:.1f} s"}
     # ---- Alg. 4.2 (one-reduce) on the same workload: the same K cycles, device-timed ----
-    def step_1r():
-        return solver.solve(b_dev, m=M, tol=0.0, max_restarts=1, x_out=x_dev, hist_cap=0, method="one_reduce")
+    if args.method == "igs":  # (with --method one_reduce the main line is Alg. 4.2 itself)
+        def step_1r():
+            return solver.solve(b_dev, m=M, tol=0.0, max_restarts=1, x_out=x_dev, hist_cap=0, method="one_reduce")
 
-    for _ in range(args.warmup):
-        o1 = step_1r()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step_1r()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms1 = e0.elapsed_time(e1)
-    ms1, _, steps1 = reduce_replicas(ms1, 0.0, args.steps * o1["steps"], dist, "cuda")
-    line["one_reduce"] = {"metric": METRIC, "value": steps1 / (ms1 / 1e3), "unit": UNIT,
-                          "ms_per_step": ms1 / args.steps, "method": "Alg. 4.2 (one global reduction per column)",
-                          "speedup_vs_alg41_gs2": (steps1 / (ms1 / 1e3)) / value if args.gs == 2 else None}
+        for _ in range(args.warmup):
+            o1 = step_1r()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_1r()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms1 = e0.elapsed_time(e1)
+        ms1, _, steps1 = reduce_replicas(ms1, 0.0, args.steps * o1["steps"], dist, "cuda")
+        line["one_reduce"] = {"metric": METRIC, "value": steps1 / (ms1 / 1e3), "unit": UNIT,
+                              "ms_per_step": ms1 / args.steps, "method": "Alg. 4.2 (one global reduction per column)",
+                              "speedup_vs_alg41_gs2": (steps1 / (ms1 / 1e3)) / value if args.gs == 2 else None}
     solver.close()
     if not args.no_precision:
         line["precision"] = run_precision(args, pkg, torch, local, dist)

@@ -214,9 +214,11 @@ int64_t igs_launch_count(const igs_ctx *ctx);
  * call returns after it completes.  Same kernel and summation order as the library's
  * step-5 reduction.
  * The per-block partial sums live in a fixed file-scope device array of 16384 doubles
- * (128 KiB) that every GPU loading the library holds until the process exits; a launch
- * whose partial sums would not fit (more than about 2000 columns) is rejected with
- * IGS_EINVAL.  The first call
+ * (128 KiB) that every GPU loading the library holds until the process exits.  Largest p:
+ * 24 x (the GPU's SM count), capped at 8192 -- 3648 on a 152-SM GB300, with or without x1
+ * (the kernel's column groups take at most 8 columns each, at most 3 groups per SM; the
+ * partial sums of every accepted launch then fit the array).  A larger p is rejected with
+ * IGS_EINVAL before anything is launched.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress), so make that
  * first call before any stream capture.  All calls share the array: calls whose GPU work
  * overlaps race on it.  Nothing in it must start at zero (each call writes every partial it

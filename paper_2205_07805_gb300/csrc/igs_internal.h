@@ -14,6 +14,8 @@ constexpr int kGivensThreads = 128;
 // Target columns per block of the multi-dot kernel (few columns per block keep the number of
 // per-block partial sums, which one block must add up afterwards, small).
 constexpr int kDotsColsPerBlock = 4;
+// Most columns one multi-dot block can take (its warps split into at most 8 column lanes).
+constexpr int kDotsMaxGroupCols = 8;
 // Resident blocks per SM assumed when sizing grids (256 threads, <= 128 registers).
 constexpr int kBlocksPerSM = 2;
 // Resident blocks per SM of the multi-dot kernel (256 threads, <= 80 registers).

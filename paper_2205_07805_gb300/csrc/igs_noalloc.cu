@@ -59,6 +59,16 @@ int scratch_address(int dev, double **out)
     return IGS_OK;
 }
 
+// Largest p one launch can take on a GPU with `sms` SMs: the plan's column groups (at most
+// kDotsBlocksPerSM blocks per SM) of at most kDotsMaxGroupCols columns each, and the partial
+// sums of the widest plan (one row block) within the scratch array for two vectors.
+int64_t max_columns(int sms)
+{
+    const int64_t by_groups = (int64_t)sms * igs::kDotsBlocksPerSM * igs::kDotsMaxGroupCols;
+    const int64_t by_scratch = kStaticScratch / 2;
+    return by_groups < by_scratch ? by_groups : by_scratch;
+}
+
 }  // namespace
 
 extern "C" int igs_block_dots_static(const double *V, int64_t ldv, int p, int64_t n, const double *x0,
@@ -82,7 +92,12 @@ extern "C" int igs_block_dots_static(const double *V, int64_t ldv, int p, int64_
     w.V = const_cast<double *>(V);
     w.part = scratch;
     const int nq = x1 ? 2 : 1;
+    // The multi-dot kernel gives each column group at most kDotsMaxGroupCols columns; the
+    // plan caps the group count at 3 blocks per SM, so p beyond 3 * SMs * kDotsMaxGroupCols
+    // (3648 on a 152-SM GPU) cannot be computed and is rejected before anything launches.
+    if ((int64_t)p > max_columns(sms)) return IGS_EINVAL;
     const igs::DotsPlan pl = igs::plan_dots(w, p);
+    if ((p + pl.groups - 1) / pl.groups > igs::kDotsMaxGroupCols) return IGS_EINVAL;
     if ((int64_t)nq * p * pl.rblocks > kStaticScratch) return IGS_EINVAL;  // beyond the fixed scratch
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     igs::DotsPlan used{};

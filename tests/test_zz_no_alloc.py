@@ -49,6 +49,18 @@ def test_block_dots_static_matches_arnoldi():
         # V_k^T v_k: the last entry is ||v_k||^2 = 1 and the rest is row k-1 of L
         assert np.abs(got[k:2 * k - 1] - L[k - 1, :k - 1]).max() <= 1e-14
         assert abs(got[2 * k - 1] - 1.0) <= 1e-14
+    # one vector (x1 = NULL): V_k^T v_k alone, against row k-1 of L and ||v_k||^2 = 1
+    k = 23
+    out = torch.full((k,), np.nan, dtype=torch.float64, device="cuda")
+    rc = lib.igs_block_dots_static(C.c_void_p(Vbuf.data_ptr()), n, k, n, C.c_void_p(Vbuf[k - 1].data_ptr()),
+                                   None, C.c_void_p(out.data_ptr()), C.c_void_p(stream.cuda_stream))
+    assert rc == pkg.OK
+    got = out.cpu().numpy()
+    assert np.abs(got[:k - 1] - L[k - 1, :k - 1]).max() <= 1e-14
+    assert abs(got[k - 1] - 1.0) <= 1e-14
+    # and both against a direct product in NumPy on the same basis (independent of the library's L)
+    Vh = Vbuf.cpu().numpy()
+    assert np.abs(got - Vh[:k] @ Vh[k - 1]).max() <= 1e-14
 
 
 def test_block_dots_static_rejects_bad_sizes():
@@ -64,3 +76,21 @@ def test_block_dots_static_rejects_bad_sizes():
     big = torch.zeros(8 * 20000, dtype=torch.float64, device="cuda")
     assert lib.igs_block_dots_static(C.c_void_p(big.data_ptr()), 8, 20000, 8, ptr, ptr,
                                      C.c_void_p(out.data_ptr()), None) == pkg.EINVAL
+    # just above the widest launch the kernel can compute (8 columns per block, 3 blocks per
+    # SM): rejected with and without x1, before anything is launched
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    pmax = min(24 * sms, 8192)
+    wide = torch.zeros(8 * (pmax + 1), dtype=torch.float64, device="cuda")
+    for x1 in (ptr, None):
+        assert lib.igs_block_dots_static(C.c_void_p(wide.data_ptr()), 8, pmax + 1, 8, ptr, x1,
+                                         C.c_void_p(out.data_ptr()), None) == pkg.EINVAL
+    # the widest accepted launch on this GPU runs and is right (8 rows, pmax columns)
+    Vw = torch.randn(pmax, 8, dtype=torch.float64, device="cuda")
+    xw = torch.randn(8, dtype=torch.float64, device="cuda")
+    yw = torch.randn(8, dtype=torch.float64, device="cuda")
+    outw = torch.full((2 * pmax,), np.nan, dtype=torch.float64, device="cuda")
+    assert lib.igs_block_dots_static(C.c_void_p(Vw.data_ptr()), 8, pmax, 8, C.c_void_p(xw.data_ptr()),
+                                     C.c_void_p(yw.data_ptr()), C.c_void_p(outw.data_ptr()), None) == pkg.OK
+    Vn = Vw.cpu().numpy()
+    ref = np.concatenate([Vn @ xw.cpu().numpy(), Vn @ yw.cpu().numpy()])
+    assert np.abs(outw.cpu().numpy() - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())

@@ -46,8 +46,6 @@ struct igs_ctx {
     bool profiling = false;
     igs_profile prof{};
     int64_t launches = 0;
-    bool fused_update = false;  // non-TMA fused steps 7/11/13 + step-14 partials (kept for A/B)
-    bool use_tma = false;       // TMA-pipelined basis updates (igs_stream_tma.cu)
     std::string err;
 };
 
@@ -224,38 +222,6 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
         RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_a(w, k, gs, pl, st_));
         // Givens least squares for the column completed by step 6 (column k-2, 1-based).
         if ((e = fork_givens(k - 3)) != cudaSuccess) return e;
-        if (ctx->use_tma && igs::tma_fits(p)) {
-            if (gs == 2) {
-                // Steps 7, 11, 13 with the partial sums of step 14 (r^(2) = V_{k-1}^T u_k) in
-                // one pass over V_{k-1}.
-                int ngroups = 0;
-                RUN(igs::KC_UPDATE, upd_bytes(w, p) + 8.0 * w.n, 4.0 * w.n * p, s,
-                    igs::launch_update_dots_tma(w, p, w.r1v, w.z, w.u, st_, &ngroups));
-                igs::DotsPlan gp{};
-                gp.rblocks = ngroups;
-                // Steps 15, 17.
-                RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_b(w, k, gp, st_));
-                // Step 16: w_k = u_k - V_{k-1} r^(3).
-                RUN(igs::KC_UPDATE, upd_bytes(w, p), 2.0 * w.n * p, s,
-                    igs::launch_update_tma(w, p, w.r3v, 1.0, w.u, col(p), false, st_));
-            } else {
-                // Steps 7, 11, 13 (one iteration): w_k = z/gamma - V_{k-1} r^(1).
-                RUN(igs::KC_UPDATE, upd_bytes(w, p) + 8.0 * w.n, 2.0 * w.n * p, s,
-                    igs::launch_update_tma(w, p, w.r1v, 0.0, w.z, col(p), true, st_));
-            }
-            continue;
-        }
-        if (gs == 2 && ctx->fused_update && igs::update_dots_fits(p)) {
-            int ngroups = 0;
-            RUN(igs::KC_UPDATE, upd_bytes(w, p) + 8.0 * w.n, 4.0 * w.n * p, s,
-                igs::launch_update_dots(w, p, w.r1v, w.z, w.u, st_, &ngroups));
-            igs::DotsPlan gp{};
-            gp.rblocks = ngroups;
-            RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_b(w, k, gp, st_));
-            RUN(igs::KC_UPDATE, upd_bytes(w, p), 2.0 * w.n * p, s,
-                igs::launch_update(w, p, w.r3v, false, 1.0, w.u, col(p), false, false, true, st_));
-            continue;
-        }
         // Steps 7, 11, 13: v_{k-1} = w/gamma in place, u_k = v_k/gamma - V_{k-1} r^(1).
         double *uout = gs == 1 ? col(p) : w.u;
         RUN(igs::KC_UPDATE, upd_bytes(w, p) + 8.0 * w.n, 2.0 * w.n * p, s,
@@ -660,15 +626,6 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
             if (o.norm2_iters <= 0) o.norm2_iters = 100;
 
             ctx = new igs_ctx();
-            // Basis-update implementation (all compute the same steps): "plain" (row per thread,
-            // default: fastest measured), "tma" (bulk-copy pipelined), "fused" (non-pipelined fused
-            // update + reduction).
-            // Programmatic dependent launch between the cycle's kernels (default on; IGS_PDL=0 off).
-            if (const char *pdl = getenv("IGS_PDL")) ctx->w.pdl = strcmp(pdl, "0") != 0;
-            if (const char *path = getenv("IGS_UPDATE_PATH")) {
-                ctx->use_tma = strcmp(path, "tma") == 0;
-                ctx->fused_update = strcmp(path, "fused") == 0;
-            }
             int rc = IGS_OK;
             auto bail = [&](int code) {
                 if (!ctx->err.empty()) g_create_err = ctx->err;
@@ -736,13 +693,7 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
                 (rc = dalloc(ctx, &w.st, 1)))
                 return bail(rc);
             // partial-sum buffer: largest multi-dot launch (two vectors, up to m+1 columns) or norms
-            // (also holds the fused update's group partials: <= 2*SMs/kFusedGroup + 1 groups x p)
             int64_t cap = 3 * (int64_t)w.num_sms;
-            {
-                const int64_t groups =
-                    ((int64_t)igs::kTmaMaxBlocksPerSM * w.num_sms + igs::kFusedGroup - 1) / igs::kFusedGroup + 1;
-                if (groups * (M + 1) > cap) cap = groups * (M + 1);
-            }
             for (int p = 1; p <= M + 1; ++p) {
                 const igs::DotsPlan pl = igs::plan_dots(w, p);
                 const int64_t need = 2 * (int64_t)p * pl.rblocks;
@@ -750,13 +701,6 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
             }
             if ((rc = dalloc(ctx, &w.part, (size_t)cap))) return bail(rc);
             w.part_cap = cap;
-            // fused update: per-block partials and group counters (<= kTmaMaxBlocksPerSM blocks per SM)
-            {
-                const int64_t maxblk = (int64_t)igs::kTmaMaxBlocksPerSM * w.num_sms;
-                if ((rc = dalloc(ctx, &w.bpart, (size_t)(maxblk * (M + 1)))) ||
-                    (rc = dalloc(ctx, &w.counters, (size_t)((maxblk + igs::kFusedGroup - 1) / igs::kFusedGroup + 1))))
-                    return bail(rc);
-            }
             // host -> device copies; with pooled memory they follow the allocations on the stream
             auto upload = [&](void *dst, const void *src, size_t bytes) {
                 if (!ctx->stream_alloc) return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -830,7 +774,6 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
             }
             {
                 cudaError_t e = igs::configure_kernels(w);
-                if (e == cudaSuccess) e = igs::configure_tma_kernels();
                 if (e != cudaSuccess) {
                     fail(ctx, IGS_ECUDA, "kernel configuration: %s", cudaGetErrorString(e));
                     return bail(IGS_ECUDA);

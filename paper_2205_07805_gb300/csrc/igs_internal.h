@@ -23,14 +23,6 @@ constexpr int kDotsBlocksPerSM = 3;
 // Basis update grid: a whole number of blocks per SM, each with an equal row range (the update
 // is bound by the FP64 pipe, so an uneven block count per SM costs its share directly).
 constexpr int kUpdateBlocksPerSM = 4;
-// Fused update + second reduction: rows per tile (= threads per block), blocks per combine
-// group, and the largest dynamic shared memory it may use (p up to ~216 columns).
-constexpr int kFusedRows = 128;
-constexpr int kFusedGroup = 16;
-constexpr size_t kFusedMaxSmem = 220 * 1024;  // under the 227 KiB opt-in, minus static smem
-// TMA-pipelined basis kernels: largest dynamic shared memory and blocks per SM they use.
-constexpr size_t kTmaMaxSmem = 220 * 1024;
-constexpr int kTmaMaxBlocksPerSM = 8;
 // Largest restart length supported.  The small single-block steps hold L_p packed in shared
 // memory: 8 (5p + p(p-1)/2) bytes <= 227 KiB gives p <= 232.
 constexpr int kMaxRestart = 232;
@@ -105,8 +97,6 @@ struct Workspace {
     double *r0v = nullptr, *r1v = nullptr, *r2v = nullptr, *r3v = nullptr, *y = nullptr;
     double *part = nullptr;        // per-block partial sums
     int64_t part_cap = 0;
-    double *bpart = nullptr;       // per-block partials of the fused update (blocks x p)
-    int *counters = nullptr;       // group arrival counters of the fused update
     double *hist_res = nullptr, *hist_lfro = nullptr;  // per-cycle history (mmax entries)
     DevState *st = nullptr;
     // precision form (allocated when the context is created with an FP32 basis)
@@ -148,22 +138,6 @@ cudaError_t launch_dots(const Workspace &w, int p, const double *x0, const doubl
 cudaError_t launch_update(const Workspace &w, int p, const double *coef, bool neg_coef,
                           double alpha, const double *src, double *out, bool norm_last,
                           bool p_from_state, bool check_halt, cudaStream_t s);
-// Fused steps 7, 11, 13 + step-14 partial sums (two GS iterations): writes u and the group
-// partials part[g*p + c]; *ngroups_out = groups.  update_dots_fits(p) tells whether the
-// tile of p columns fits in shared memory.
-size_t update_dots_smem(int p);
-bool update_dots_fits(int p);
-cudaError_t launch_update_dots(const Workspace &w, int p, const double *coef, const double *z,
-                               double *u, cudaStream_t s, int *ngroups_out);
-// TMA-pipelined versions (igs_stream_tma.cu).  tma_fits(p): the double-buffered tile of p
-// columns fits in shared memory.
-size_t tma_smem(int p, bool with_dots);
-bool tma_fits(int p);
-cudaError_t launch_update_dots_tma(const Workspace &w, int p, const double *coef, const double *z,
-                                   double *u, cudaStream_t s, int *ngroups_out);
-cudaError_t launch_update_tma(const Workspace &w, int p, const double *coef, double alpha,
-                              const double *src, double *out, bool norm_last, cudaStream_t s);
-cudaError_t configure_tma_kernels();
 // Partial sums of squares of up to three vectors (part[blk*nvec + q]).
 cudaError_t launch_norms(const Workspace &w, const double *a, const double *b,
                          const double *c, int *blocks_out, cudaStream_t s);

@@ -571,150 +571,6 @@ k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coe
     }
 }
 
-// =====================================================================================
-// Fused first Gauss-Seidel update and second reduction (two GS iterations; Alg. 4.1
-// steps 7, 11, 13 and the partial sums of step 14):
-//   v_{k-1} = w_{k-1} / gamma (in place), u_k = z / gamma - V_{k-1} r^(1),
-//   part[blk*p + c] = sum over the block's rows of V[:,c] u_k.
-// Each block streams a contiguous row range in tiles of TR rows.  Phase 1 (thread per row)
-// reads the tile's p columns once from HBM, keeps them in shared memory and forms u; phase 2
-// (thread per column, or per column and row slice) reads the tile back from shared memory
-// against u.  Every basis element thus feeds two FMAs from one HBM read, as in the step-5
-// multi-dot.  Blocks then combine their partials in groups: the last block of each group to
-// finish (atomic counter; nobody waits) adds the group's partials in block order and writes
-// gpart[g*p + c] -- few enough partials for one block to finish the reduction quickly.
-// =====================================================================================
-template <int TR>
-__global__ void __launch_bounds__(TR, 2)
-k_update_dots(double *V, int64_t ld, int p, int64_t n, int64_t rows_per_block,
-              const double *__restrict__ coef, const double *__restrict__ z, double *__restrict__ u,
-              double *__restrict__ bpart, double *__restrict__ gpart, int *__restrict__ counters,
-              int group, DevState *st)
-{
-    IGS_PDL_ENTER();
-    if (halted(st)) return;
-    extern __shared__ double smem[];
-    constexpr int ldt = TR + 1;          // padded tile stride
-    double *tile = smem;                 // p columns x ldt
-    double *sc = tile + (size_t)p * ldt; // p coefficients
-    double *us = sc + p;                 // u of the tile's rows
-    double *red = us + TR;               // slice tree
-    __shared__ int s_last;
-    const int t = threadIdx.x;
-    const double ig = st->inv_gamma;
-    for (int c = t; c < p; c += TR) sc[c] = coef[c];
-    // phase-2 mapping
-    const bool narrow = p <= TR;
-    const int S = narrow ? TR / p : 1;   // row slices per column
-    const int cmine = narrow ? t % p : t;
-    const int s = narrow ? t / p : 0;
-    const bool act = narrow ? s < S : true;
-    double a0 = 0.0, a1 = 0.0;           // narrow: two chains of column cmine; wide: columns t, t+TR
-    __syncthreads();
-    const int64_t r_lo = (int64_t)blockIdx.x * rows_per_block;
-    const int64_t r_hi = r_lo + rows_per_block < n ? r_lo + rows_per_block : n;
-    for (int64_t t0 = r_lo; t0 < r_hi; t0 += TR) {
-        const int len = (int)(r_hi - t0 < TR ? r_hi - t0 : TR);
-        if (t < len) {
-            const int64_t i = t0 + t;
-            const double *vi = V + i;
-            double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
-            int c = 0;
-            const int pc = p - 1;
-            for (; c + 7 < pc; c += 8) {
-                double v[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = vi[(int64_t)(c + q) * ld];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) tile[(size_t)(c + q) * ldt + t] = v[q];
-                b0 = fma(v[0], sc[c], b0);
-                b1 = fma(v[1], sc[c + 1], b1);
-                b2 = fma(v[2], sc[c + 2], b2);
-                b3 = fma(v[3], sc[c + 3], b3);
-                b0 = fma(v[4], sc[c + 4], b0);
-                b1 = fma(v[5], sc[c + 5], b1);
-                b2 = fma(v[6], sc[c + 6], b2);
-                b3 = fma(v[7], sc[c + 7], b3);
-            }
-            for (; c < pc; ++c) {
-                const double v = vi[(int64_t)c * ld];
-                tile[(size_t)c * ldt + t] = v;
-                b0 = fma(v, sc[c], b0);
-            }
-            double *vl = V + (int64_t)pc * ld + i;
-            const double vlast = *vl * ig;  // step 7, in place
-            *vl = vlast;
-            tile[(size_t)pc * ldt + t] = vlast;
-            b1 = fma(vlast, sc[pc], b1);
-            const double ui = fma(ig, z[i], -((b0 + b2) + (b1 + b3)));  // steps 11, 13
-            u[i] = ui;
-            us[t] = ui;
-        }
-        __syncthreads();
-        if (narrow) {
-            if (act) {
-                const int rs = s * len / S, re = (s + 1) * len / S;
-                const double *tc = tile + (size_t)cmine * ldt;
-                int r = rs;
-                for (; r + 1 < re; r += 2) {
-                    a0 = fma(tc[r], us[r], a0);
-                    a1 = fma(tc[r + 1], us[r + 1], a1);
-                }
-                if (r < re) a0 = fma(tc[r], us[r], a0);
-            }
-        } else {
-            const double *t0c = tile + (size_t)t * ldt;
-            const double *t1c = tile + (size_t)(t + TR) * ldt;
-            const bool second = t + TR < p;
-            for (int r = 0; r < len; ++r) {
-                a0 = fma(t0c[r], us[r], a0);
-                if (second) a1 = fma(t1c[r], us[r], a1);
-            }
-        }
-        __syncthreads();
-    }
-    // block partials (slice tree when narrow)
-    if (narrow) {
-        red[t] = a0 + a1;
-        int Sp = S;
-        while (Sp > 1) {
-            const int h = (Sp + 1) >> 1;
-            __syncthreads();
-            if (act && s < Sp - h) red[t] += red[t + h * p];
-            Sp = h;
-        }
-        __syncthreads();
-        if (act && s == 0) bpart[(int64_t)blockIdx.x * p + cmine] = red[t];
-    } else {
-        if (t < p) bpart[(int64_t)blockIdx.x * p + t] = a0;
-        if (t + TR < p) bpart[(int64_t)blockIdx.x * p + t + TR] = a1;
-    }
-    // group combine by the last block of the group to finish
-    __threadfence();
-    __syncthreads();
-    const int g = blockIdx.x / group;
-    const int gb0 = g * group;
-    const int gb1 = gb0 + group < (int)gridDim.x ? gb0 + group : (int)gridDim.x;
-    if (t == 0) {
-        const int prev = atomicAdd(&counters[g], 1);
-        s_last = prev == gb1 - gb0 - 1;
-        if (s_last) counters[g] = 0;  // ready for the next launch
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    for (int c = t; c < p; c += TR) {
-        double s0 = 0.0, s1 = 0.0;
-        int b = gb0;
-        for (; b + 1 < gb1; b += 2) {
-            s0 += __ldcg(bpart + (int64_t)b * p + c);
-            s1 += __ldcg(bpart + (int64_t)(b + 1) * p + c);
-        }
-        if (b < gb1) s0 += __ldcg(bpart + (int64_t)b * p + c);
-        gpart[(int64_t)g * p + c] = s0 + s1;
-    }
-}
-
 // Partial sums of squares of up to three vectors: part[blockIdx.x * nvec + q].
 __global__ void __launch_bounds__(kStreamThreads)
 k_norms(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
@@ -1493,36 +1349,6 @@ cudaError_t launch_update(const Workspace &w, int p, const double *coef, bool ne
     return cudaGetLastError();
 }
 
-size_t update_dots_smem(int p)
-{
-    return sizeof(double) * ((size_t)p * (kFusedRows + 1) + (size_t)p + 2 * (size_t)kFusedRows);
-}
-
-bool update_dots_fits(int p)
-{
-    return update_dots_smem(p) <= kFusedMaxSmem;
-}
-
-cudaError_t launch_update_dots(const Workspace &w, int p, const double *coef, const double *z,
-                               double *u, cudaStream_t s, int *ngroups_out)
-{
-    const size_t smem = update_dots_smem(p);
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_dots<kFusedRows>,
-                                                                  kFusedRows, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 2) per_sm = 2;
-    const int blocks = w.num_sms * per_sm;
-    const int64_t rows = (w.n + blocks - 1) / blocks;
-    const int nblk = (int)((w.n + rows - 1) / rows);
-    const int ngroups = (nblk + kFusedGroup - 1) / kFusedGroup;
-    launch_k(false, k_update_dots<kFusedRows>, dim3(nblk), dim3(kFusedRows), smem, s, w.V, w.ld, p, w.n, rows, coef, z, u, w.bpart,
-                                                             w.part, w.counters, kFusedGroup, w.st);
-    if (ngroups_out) *ngroups_out = ngroups;
-    return cudaGetLastError();
-}
-
 cudaError_t launch_norms(const Workspace &w, const double *a, const double *b, const double *c,
                          int *blocks_out, cudaStream_t s)
 {
@@ -1589,18 +1415,6 @@ cudaError_t configure_kernels(const Workspace &w)
     cudaError_t e = allow_smem((const void *)k_step_a, small_solve_smem(w.mmax, 5));
     if (e == cudaSuccess) e = allow_smem((const void *)k_step_b, small_solve_smem(w.mmax, 3));
     if (e == cudaSuccess) e = allow_smem((const void *)k_step_1r, small_solve_smem(w.mmax + 1, 6));
-    if (e == cudaSuccess) {
-        int dev = 0, optin = 0;
-        cudaFuncAttributes fa{};
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_update_dots<kFusedRows>);
-        if (e == cudaSuccess) {
-            size_t lim = (size_t)optin - fa.sharedSizeBytes;
-            if (lim > kFusedMaxSmem) lim = kFusedMaxSmem;
-            e = cudaFuncSetAttribute(k_update_dots<kFusedRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
-        }
-    }
     return e;
 }
 

@@ -87,3 +87,23 @@ def test_one_reduce_rejects_fp32(pkg):
             s.solve(b, m=10, method="one_reduce", precision="fp32_ir")
         with pytest.raises(ValueError):
             s.solve(b, m=10, method="cgs")
+
+
+def test_full_size_cd2d_one_reduce_cycle(pkg):
+    """Alg. 4.2 on the benchmark workload (2-D convection-diffusion 512 x 512, Pe 50,
+    n = 262144, m = 100): one full cycle against the oracle's Alg. 4.2, element-wise on H while
+    kappa(B_k) < 1e6, with the orthogonality and Arnoldi relations at full size."""
+    A, b, _, _ = gen.cd2d(512, 50.0, seed=0)
+    m = 100
+    normA = gen.norm2_power(A, iters=50)
+    with pkg.Solver(A, max_restart_m=m, A_norm2=normA) as s:
+        g = s.arnoldi(b, m, method="one_reduce")
+    o = oracle.arnoldi(A, b, m, oracle.ONE_REDUCE, 2)
+    assert g["ncols"] == o["ncols"] == m
+    kap = P.kappa_prefix(A, b, o["V"], m)
+    herr = P.h_column_errors(g["H"], o["H"], m)
+    well = kap < 1e6
+    assert well[0]
+    assert herr[well].max() <= 1e-10, herr[well].max()
+    assert P.orth_loss(g["V"], m + 1) <= 1e-13
+    assert P.arnoldi_relation(A, g["V"], g["H"], m, normA) <= 1e-13

@@ -23,10 +23,10 @@ workload and cycles; `precision`: the FP32-basis form inside FP64 iterative refi
 against the FP64 form on the 160^3 convection-diffusion system (n = 4.1M, m = 200) to
 beta <= 1e-14, with the FP32 multi-dot's HBM roofline; `served`: a Poisson stream of
 2-D convection-diffusion requests (2000/s, sides 64..1024) replayed against the request
-server (include/igs_serve.h: gangs, plus the graph lane for n >= --serve-graph-min-n) for a
-20 s window (60 s with --workload served), with served solves/s, p50/p99 latency, the
-refused backlog, and the same completed requests solved one at a time through igs_solve
-(FP64) for comparison; and `batched`: the batched form (include/igs_batch.h) on 4096 banded
+server (include/igs_serve.h: gangs, plus graph lanes for n >= --serve-graph-min-n) for a
+60 s window, with served solves/s, p50/p99 latency and service time, the refused backlog,
+and every completed request solved again one at a time through igs_solve (FP64) for
+comparison; and `batched`: the batched form (include/igs_batch.h) on 4096 banded
 systems (n ~ U{64..2048}, 7 diagonals, m = 50, every system to beta <= 1e-12) in solves/s,
 its FP64 roofline, and the same systems solved one at a time by igs_solve (a sample) for
 comparison.  `--workload batched` prints that measurement as the main line instead.
@@ -61,6 +61,11 @@ def workload_config(gs):
             "n": GRID_N * GRID_N, "nnz": 5 * GRID_N * GRID_N - 4 * GRID_N, "restart_m": M,
             "gs_iters": gs, "step": f"one restart cycle = {M} Arnoldi steps",
             "l2": "inputs larger than L2 (Krylov basis 212 MB > 126 MB L2)"}
+
+
+def main_config(gs, method, ws):
+    """The main line's `config` (the same dict in both bench arms)."""
+    return {**workload_config(gs), "method": method, "parallelism": f"replicas x{ws}"}
 
 
 BATCH_COUNT, BATCH_M, BATCH_TOL, BATCH_MAX_RESTARTS = 4096, 50, 1e-12, 20
@@ -165,13 +170,31 @@ def reduce_replicas(ms, e2e_s, steps, dist=None, device=None):
     return float(t[0].item()), float(t[1].item()), int(round(s.item()))
 
 
-def oracle_cycle_rate(A, b, m):
-    """Arnoldi steps/s of the CPU oracle (as it stands, one thread) over one cycle."""
+def oracle_cycle_rate(A, b, m, method="igs", gs=2, impl=None):
+    """Arnoldi steps/s of the CPU oracle (as it stands) over one cycle: the serial parity
+    build (impl=None) or the OpenMP timing build (oracle.openmp(), all host cores)."""
     import oracle
+    meth = oracle.ONE_REDUCE if method == "one_reduce" else oracle.IGS
     t0 = time.perf_counter()
-    out = oracle.arnoldi(A, b, m, oracle.IGS, 2)
+    out = oracle.arnoldi(A, b, m, meth, gs, impl=impl)
     dt = time.perf_counter() - t0
     return out["ncols"] / dt, dt
+
+
+def cpu_baseline_cd2d(A, b, m, method, gs):
+    """The oracle on one full cycle of the benchmark workload, serial and on all host cores
+    (the OpenMP build: bitwise the serial build's results)."""
+    import oracle
+    oracle.build()
+    omp = oracle.openmp()
+    threads = oracle.openmp_threads()
+    rate1, dt1 = oracle_cycle_rate(A, b, m, method, gs)
+    rate_n, dt_n = oracle_cycle_rate(A, b, m, method, gs, impl=omp)
+    return {"value": rate_n, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one full cycle ({m} Arnoldi columns) of the same workload: {dt_n:.1f} s on "
+                      f"{threads} threads (OpenMP build), {dt1:.1f} s serial",
+            "nproc": os.cpu_count(),
+            "serial": {"value": rate1, "unit": UNIT, "cores": 1, "build": "serial parity build"}}
 
 
 def run_reference(args):
@@ -212,29 +235,34 @@ def run_reference(args):
     A, b, _, _ = gen.cd2d(GRID_N, PECLET, SEED)
     import oracle
     oracle.build()
+    omp = oracle.openmp()
+    threads = oracle.openmp_threads()
+    meth = oracle.ONE_REDUCE if args.method == "one_reduce" else oracle.IGS
     # bounded sample per step: the first s columns of the m = 100 cycle, s chosen so that the
     # whole run stays within about two minutes (early columns are cheaper, so this favours
     # the oracle)
     t_probe = time.perf_counter()
-    oracle.arnoldi(A, b, 10, oracle.IGS, args.gs)
+    oracle.arnoldi(A, b, 10, meth, args.gs, impl=omp)
     t10 = time.perf_counter() - t_probe
     budget = 120.0 / max(1, args.steps + args.warmup)
     s = 10
     while s < M and t10 * ((s + 10) / 10.0) ** 2 <= budget:
         s += 10
     for _ in range(args.warmup):
-        oracle.arnoldi(A, b, s, oracle.IGS, args.gs)
+        oracle.arnoldi(A, b, s, meth, args.gs, impl=omp)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.arnoldi(A, b, s, oracle.IGS, args.gs)
+        oracle.arnoldi(A, b, s, meth, args.gs, impl=omp)
     dt = time.perf_counter() - t0
     value = args.steps * s / dt
-    sample = f"first {s} of the {M} Arnoldi columns of the cycle, per step"
+    sample = (f"first {s} of the {M} Arnoldi columns of the cycle, per step; OpenMP build of the "
+              f"oracle (bitwise the serial build's results) on {threads} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.gs),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": main_config(args.gs, args.method, ws),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -456,18 +484,20 @@ def serve_stream(seed, duration):
                     "fp32_ir" if rng.integers(0, 2) else "fp64", int(rng.integers(1 << 30))))
 
 
-def run_served(args, pkg, torch, local, dist, duration, drain_s, oaat_budget_s=60.0):
+def run_served(args, pkg, torch, local, dist, duration, drain_s, oaat_budget_s=900.0):
     """Replay the arrival stream against the request server: a request is materialised (its
     matrix generated) and submitted at its arrival time when the server's backlog has room,
-    else it is refused (counted).  Latency = completion - arrival.  Then the completed
-    requests are solved again one at a time through igs_solve (FP64), in an order spread
-    over the run, until all are done or oaat_budget_s has passed; if the budget ends it
-    first, the one-at-a-time time of the rest is extrapolated by work (n x served steps)."""
+    else it is refused (counted).  Latency = completion - arrival; service time = completion
+    - admission.  Then every completed request is solved again one at a time through
+    igs_solve (FP64, the same ||A|| and tolerance), each timed; nothing is extrapolated (a
+    safety budget, oaat_budget_s, stops the pass early only on a pathological run, and the
+    line then says how many were timed and rates only those)."""
     ws, rank, _ = dist_env()
     stream = serve_stream(SEED + rank, duration)
     max_queue = args.serve_backlog
     sv = pkg.Server(max_restart_m=SERVE_M, arena_bytes=SERVE_ARENA, slots=args.serve_slots,
-                    rows_per_cta=4096, max_queue=max_queue, device=local, graph_min_n=args.serve_graph_min_n)
+                    rows_per_cta=4096, max_queue=max_queue, device=local, graph_min_n=args.serve_graph_min_n,
+                    graph_lanes=args.serve_graph_lanes)
     arrivals, done, refused = {}, [], 0
     t_start = sv.clock()
     k = 0
@@ -502,12 +532,13 @@ def run_served(args, pkg, torch, local, dist, duration, drain_s, oaat_budget_s=6
     ok = sum(1 for c in done if c["status"] == 0)
     line = {"metric": "served solves/s", "value": len(done) / (t_end - t_start), "unit": "solves/s",
             "config": {**serve_config(duration), "slots": args.serve_slots, "backlog": max_queue,
-                       "graph_min_n": args.serve_graph_min_n},
+                       "graph_min_n": args.serve_graph_min_n, "graph_lanes": args.serve_graph_lanes},
             "offered": len(stream), "submitted": st["submitted"],
             "refused_backlog_full": refused, "completed": len(done), "completed_ok": ok,
             "unfinished_at_end": st["queued"] + st["running"], "wall_s": t_end - t_start,
             "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
-            "service_p50_s": float(np.percentile(svc, 50)),
+            "service_p50_s": float(np.percentile(svc, 50)), "service_p99_s": float(np.percentile(svc, 99)),
+            "queue_wait_p50_s": float(np.percentile(lat - svc, 50)),
             "arena_peak_bytes": st["arena_peak"], "gpu_launches": st["launches"],
             "by_precision": {p: sum(1 for c in done if arrivals[c["id"]][2] == p) for p in ("fp64", "fp32_ir")},
             "by_path": {"gang": sum(1 for c in done if c["path"] == 0),
@@ -517,8 +548,7 @@ def run_served(args, pkg, torch, local, dist, duration, drain_s, oaat_budget_s=6
         # the same requests, one at a time through igs_solve in FP64 with graph-captured
         # cycles (set-up and capture outside the timing), in an order spread over the run
         order = list(range(0, len(done), 2)) + list(range(1, len(done), 2))
-        work = {c["id"]: float(c["steps"]) * serve_n(arrivals[c["id"]][1]) for c in done}
-        t_tot, n_ok, n_run, w_run = 0.0, 0, 0, 0.0
+        t_tot, n_ok, n_run = 0.0, 0, 0
         t_budget = time.perf_counter() + oaat_budget_s
         for j in order:
             if time.perf_counter() > t_budget:
@@ -528,7 +558,7 @@ def run_served(args, pkg, torch, local, dist, duration, drain_s, oaat_budget_s=6
             src = next(x for x in stream if abs(x[0] + t_start - t_arr) < 1e-9)
             A, b, _, _ = gen.cd2d(side, src[2], src[5])
             st_ = torch.cuda.current_stream()
-            with pkg.Solver(A, max_restart_m=SERVE_M, A_norm2=norm_bound(A), device=local,
+            with pkg.Solver(A, max_restart_m=SERVE_M, A_norm2=c["A_norm2"], device=local,
                             stream=st_.cuda_stream) as so:
                 bd = torch.from_numpy(b).cuda()
                 xd = torch.empty_like(bd)
@@ -540,19 +570,102 @@ def run_served(args, pkg, torch, local, dist, duration, drain_s, oaat_budget_s=6
                 t_tot += time.perf_counter() - t0
                 n_ok += r["status"] == 0
             n_run += 1
-            w_run += work[c["id"]]
-        w_all = sum(work.values())
-        t_all = t_tot * (w_all / w_run) if n_run < len(done) else t_tot
-        line["one_at_a_time"] = {"value": len(done) / t_all, "unit": "solves/s", "converged": n_ok,
-                                 "path": "igs_solve per request (FP64, whole GPU, context set-up and "
-                                         "graph capture outside the timing)",
-                                 "requests": f"{n_run} of the {len(done)} completed requests solved again "
-                                             f"one at a time ({t_tot:.1f} s)"
-                                             + ("" if n_run == len(done) else
-                                                "; the rest extrapolated by work = n x served steps"),
-                                 "one_at_a_time_s": t_all}
+        line["one_at_a_time"] = {"value": n_run / t_tot, "unit": "solves/s", "converged": n_ok,
+                                 "path": "igs_solve per request (FP64, whole GPU, the server's ||A|| and "
+                                         "tolerance; context set-up and graph capture outside the timing)",
+                                 "requests": ("all " if n_run == len(done) else f"{n_run} of the ")
+                                             + f"{len(done)} completed requests solved again one at a time, "
+                                               f"each timed ({t_tot:.1f} s in total)",
+                                 "one_at_a_time_s": t_tot}
         line["speedup_vs_one_at_a_time"] = line["value"] / line["one_at_a_time"]["value"]
     return line
+
+
+SOLVE_TOL, SOLVE_MAX_RESTARTS = 1e-13, 500
+
+
+def run_cd2d_extra(args, solver, b_dev, x_dev, stream, dist, value_gs):
+    """On the benchmark system: Alg. 4.1 with the other number of GS iterations (the same K
+    single cycles, device-timed), and the whole solve to the workload's own stopping
+    criterion beta <= 1e-13 (restarts until it holds; device-timed, best of two)."""
+    import torch
+    out = {}
+    gs_other = 1 if args.gs == 2 else 2
+
+    def cyc():
+        return solver.solve(b_dev, m=M, gs=gs_other, tol=0.0, max_restarts=1, x_out=x_dev, hist_cap=0)
+
+    for _ in range(args.warmup):
+        cyc()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        cyc()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms, _, st = reduce_replicas(e0.elapsed_time(e1), 0.0, args.steps * M, dist, "cuda")
+    out[f"gs{gs_other}"] = {"metric": METRIC, "value": st / (ms / 1e3), "unit": UNIT,
+                            "ms_per_step": ms / args.steps, "gs_iters": gs_other,
+                            "method": f"Alg. 4.1 with {gs_other} Gauss-Seidel iteration(s)"}
+    best = None
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = solver.solve(b_dev, m=M, gs=args.gs, tol=SOLVE_TOL, max_restarts=SOLVE_MAX_RESTARTS, x_out=x_dev,
+                         hist_cap=0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if best is None or ms < best[0]:
+            best = (ms, r)
+    ms, r = best
+    ms, _, _ = reduce_replicas(ms, 0.0, 1, dist, "cuda")
+    out["solve_to_tol"] = {"metric": "seconds to beta <= 1e-13", "value": ms / 1e3, "unit": "s",
+                           "higher_is_better": False, "tol_beta": SOLVE_TOL, "status": r["status"],
+                           "beta": r["beta"], "steps": r["steps"], "cycles": r["cycles"],
+                           "arnoldi_steps_per_s": r["steps"] / (ms / 1e3), "gs_iters": args.gs,
+                           "timing": "device (CUDA events), best of two solves from x0 = 0"}
+    return out
+
+
+def run_dense200(args, pkg, torch, local, dist, rank):
+    """The dense ill-conditioned system (A = U diag(s) W^T, n = 200, s log-spaced 1..1e-10,
+    k = 200 unrestarted): Arnoldi steps/s of one full cycle with one and two GS iterations
+    and Alg. 4.2 on the GPU (device-timed, A and the basis resident in L2, so latency-bound),
+    and the oracle's MGS-GMRES and Alg. 4.1 on one core for comparison."""
+    A, b, _, info = gen.dense_usv(200, SEED)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "dense A = U diag(s) W^T, n = 200, kappa 1e10, k = 200 unrestarted",
+           "metric": METRIC, "unit": UNIT}
+    with pkg.Solver(A, max_restart_m=200, A_norm2=info["normA"], device=local, stream=stream.cuda_stream) as sv:
+        bd = torch.from_numpy(b).cuda()
+        xd = torch.empty_like(bd)
+        for name, gs, meth in (("igs_gs1", 1, "igs"), ("igs_gs2", 2, "igs"), ("one_reduce", 2, "one_reduce")):
+            def cyc():
+                return sv.solve(bd, m=200, gs=gs, tol=0.0, max_restarts=1, x_out=xd, hist_cap=0, method=meth)
+            for _ in range(args.warmup):
+                r = cyc()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 20
+            e0.record(stream)
+            for _ in range(reps):
+                r = cyc()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms, _, st = reduce_replicas(e0.elapsed_time(e1), 0.0, reps * r["steps"], dist, "cuda")
+            out[name] = {"value": st / (ms / 1e3), "steps_per_cycle": r["steps"], "beta": r["beta"],
+                         "status": r["status"]}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        for name, meth, gs in (("oracle_mgs", oracle.MGS, 1), ("oracle_igs_gs2", oracle.IGS, 2)):
+            t0 = time.perf_counter()
+            o = oracle.arnoldi(A, b, 200, meth, gs)
+            dt = time.perf_counter() - t0
+            out[name] = {"value": o["ncols"] / dt, "steps": o["ncols"], "cores": 1}
+    return out
 
 
 def oracle_batch_rate(stride=128):
@@ -590,6 +703,8 @@ def main():
     ap.add_argument("--batch-launch", default="",
                     help="T:B = block threads and CTAs per SM for the batched kernel (default: tuned)")
     ap.add_argument("--no-one-at-a-time", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other-gs cycle, the solve to beta <= 1e-13 and the dense n = 200 lines")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision-form sub-measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream sub-measurement")
     ap.add_argument("--serve-window", type=float, default=0.0,
@@ -598,7 +713,9 @@ def main():
     ap.add_argument("--serve-backlog", type=int, default=16,
                     help="requests waiting for admission at most (arrivals beyond it are refused)")
     ap.add_argument("--serve-graph-min-n", type=int, default=250000,
-                    help="requests with n >= this take the server's graph lane (0: gangs only)")
+                    help="requests with n >= this take the server's graph lanes (0: gangs only)")
+    ap.add_argument("--serve-graph-lanes", type=int, default=2,
+                    help="graph-lane requests in flight at once")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -624,7 +741,7 @@ def main():
         clocks = Clocks(local)
         clocks.start()
         window = args.serve_window or 60.0
-        sl = run_served(args, pkg, torch, local, dist, window, drain_s=120.0, oaat_budget_s=300.0)
+        sl = run_served(args, pkg, torch, local, dist, window, drain_s=120.0)
         clk = clocks.stop()
         line = {"metric": sl["metric"], "value": sl["value"], "unit": sl["unit"], "n_gpus": ws, "steps": 1,
                 "warmup": 0, "ms_per_step": 1e3 * sl["wall_s"], "higher_is_better": True, "scaling": "weak",
@@ -772,15 +889,11 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {**workload_config(args.gs), "method": args.method, "parallelism": f"replicas x{ws}"},
+            "config": main_config(args.gs, args.method, ws),
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk}
     if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        rate, dt = oracle_cycle_rate(A, b, M)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"one full cycle ({M} Arnoldi columns) of the same workload, {dt:.1f} s"}
+        line["cpu_baseline"] = cpu_baseline_cd2d(A, b, M, args.method, args.gs)
     # ---- Alg. 4.2 (one-reduce) on the same workload: the same K cycles, device-timed ----
     if args.method == "igs":  # (with --method one_reduce the main line is Alg. 4.2 itself)
         def step_1r():
@@ -800,12 +913,15 @@ def main():
         line["one_reduce"] = {"metric": METRIC, "value": steps1 / (ms1 / 1e3), "unit": UNIT,
                               "ms_per_step": ms1 / args.steps, "method": "Alg. 4.2 (one global reduction per column)",
                               "speedup_vs_alg41_gs2": (steps1 / (ms1 / 1e3)) / value if args.gs == 2 else None}
+    if args.method == "igs" and not args.no_extra:
+        line.update(run_cd2d_extra(args, solver, b_dev, x_dev, stream, dist, value))
     solver.close()
+    if not args.no_extra:
+        line["dense_200"] = run_dense200(args, pkg, torch, local, dist, rank)
     if not args.no_precision:
         line["precision"] = run_precision(args, pkg, torch, local, dist)
     if not args.no_served:
-        line["served"] = run_served(args, pkg, torch, local, dist, args.serve_window or 20.0, drain_s=30.0,
-                                    oaat_budget_s=40.0)
+        line["served"] = run_served(args, pkg, torch, local, dist, args.serve_window or 60.0, drain_s=60.0)
     if not args.no_batched:
         bl = run_batched(args, pkg, torch, local, dist)
         line["batched"] = {k: bl[k] for k in ("metric", "value", "unit", "ms_per_step", "arnoldi_steps_per_s",

@@ -21,10 +21,11 @@
  *    memory free up.
  *  - The same pump call finds finished requests (CUDA events), copies x to host memory held by
  *    the server, releases their device memory, and queues a completion record.
- *  - Large requests (n >= graph_min_n, when set) take the graph lane instead: a worker thread
- *    of the server solves them one at a time with the single-system library of igs.h (its
- *    whole-GPU kernels are the faster executor for one large system), concurrently with the
- *    gangs of the other requests.
+ *  - Large requests (n >= graph_min_n, when set) take a graph lane instead: a worker thread
+ *    of the server solves each with the single-system library of igs.h (its whole-GPU kernels
+ *    are the faster executor for one large system).  graph_lanes lanes run concurrently, each
+ *    on its own stream, so that large requests overlap on the device with each other (one
+ *    fills the others' single-block steps) and with the gangs of the other requests.
  *  - A request's result depends only on the request (its matrix, b, x0 and options) and the
  *    server's options: it is bitwise the same alone and in any mix (its lane and gang size are
  *    functions of n, and no arithmetic of one request touches another's data).
@@ -63,6 +64,9 @@ typedef struct {
                                igs_solve (igs.h: whole-GPU kernels, graph-captured cycles,
                                pooled device memory outside the arena), beside the gangs.
                                0: no graph lane                                              */
+    int graph_lanes;        /* graph-lane requests in flight at once (one worker thread and
+                               stream each, 1..16), so that large requests overlap on the
+                               device; 0: 1                                                  */
 } igs_server_opts;
 
 typedef struct {
@@ -94,6 +98,7 @@ typedef struct {
                                launched, and found finished by igs_server_pump               */
     int path;               /* IGS_SERVE_PATH_GANG or IGS_SERVE_PATH_GRAPH (gang_ctas is 0 and
                                device_bytes the context's memory on the graph lane)          */
+    double A_norm2;         /* the ||A||_2 the request's beta used                            */
 } igs_completion;
 
 enum { IGS_SERVE_PATH_GANG = 0, IGS_SERVE_PATH_GRAPH = 1 };

@@ -21,8 +21,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "igs_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libigs_oracle.so")
+_OMP_PATH = os.path.join(_OUT_DIR, "libigs_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_omp = None
+_FLAGS = ["-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
 
 MGS, IGS, ONE_REDUCE = 0, 1, 2  # MGS-GMRES, Alg. 4.1, Alg. 4.2
 OK, NOT_CONVERGED, BREAKDOWN, EINVAL, ENOMEM, ENUMERIC = 0, 1, 2, -1, -2, -4
@@ -32,16 +35,40 @@ _d = C.c_double
 _i64 = C.c_int64
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (serial, no FMA contraction)."""
+def _compile(path: str, extra: list, force: bool) -> str:
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", *_FLAGS, *extra, "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (serial, no FMA contraction): the parity build."""
+    return _compile(_LIB_PATH, [], force)
+
+
+def build_openmp(force: bool = False) -> str:
+    """Compile the timing build: the same source with -fopenmp.  Its parallel loops write
+    disjoint outputs, each formed exactly as in the serial build, so its results are
+    bitwise those of ``build()`` (checked by the tests); it exists only to time the oracle
+    on all host cores (threads from OMP_NUM_THREADS, default all)."""
+    return _compile(_OMP_PATH, ["-fopenmp"], force)
+
+
+def openmp() -> "Oracle":
+    """The OpenMP timing build, for the ``impl=`` argument of the functions below."""
+    global _omp
+    with _lock:
+        if _omp is None:
+            _omp = Oracle(build_openmp())
+        return _omp
+
+
+def openmp_threads() -> int:
+    """Threads the OpenMP build will use (its omp_get_max_threads())."""
+    return int(openmp().lib.ora_threads())
 
 
 class Oracle:
@@ -69,6 +96,9 @@ class Oracle:
                                   _d, C.c_int, _d, _i64, f64, f64, C.POINTER(_i64),
                                   C.POINTER(_d), C.POINTER(C.c_int), C.POINTER(_i64)]
         lib.ora_gmres.restype = C.c_int
+        if hasattr(lib, "ora_threads"):
+            lib.ora_threads.argtypes = []
+            lib.ora_threads.restype = C.c_int
         self.lib = lib
         self.path = lib_path
 
@@ -78,8 +108,7 @@ def compile_variant(src_text: str, out_path: str) -> str:
     src = out_path + ".c"
     with open(src, "w") as f:
         f.write(src_text)
-    subprocess.run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-                    "-fno-fast-math", "-o", out_path, src, "-lm"], check=True)
+    subprocess.run(["gcc", *_FLAGS, "-o", out_path, src, "-lm"], check=True)
     return out_path
 
 

@@ -11,6 +11,11 @@
  *  - IEEE binary64, round to nearest; built with -ffp-contract=off so that no
  *    multiply-add is fused (identical results on x86-64 and AArch64).
  *  - Every sum is taken left to right in index order; no blocking or reordering.
+ *  - The parity build is serial (no -fopenmp: the "omp" pragmas are ignored).  A second
+ *    build with -fopenmp exists only to time the oracle on all host cores; its pragmas
+ *    sit on loops whose iterations write different outputs (matrix rows, vector entries,
+ *    one inner product per basis column), and every output is still formed by the same
+ *    serial operations in the same order, so both builds give bitwise the same results.
  *  - Matrices: A in CSR (int64 row pointers, int32 column indices).  V is n x (m+1)
  *    column-major (ld = n).  H is (m+1) x m column-major (ld = m+1).  L is
  *    (m+1) x (m+1) row-major; row i holds the strictly-lower row v_{i+1}^T V_i.
@@ -25,10 +30,23 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { ORA_MGS = 0, ORA_IGS = 1, ORA_ONE_REDUCE = 2 };
 enum { ORA_OK = 0, ORA_NOT_CONVERGED = 1, ORA_BREAKDOWN = 2, ORA_EINVAL = -1, ORA_ENOMEM = -2,
        ORA_ENUMERIC = -4 };
+
+/* Threads the loops below run on: 1 in the serial parity build. */
+int ora_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ---------------------------------------------------------------------------------------
  * Basic kernels (plain loops).
@@ -39,6 +57,7 @@ enum { ORA_OK = 0, ORA_NOT_CONVERGED = 1, ORA_BREAKDOWN = 2, ORA_EINVAL = -1, OR
 void ora_spmv(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
               const double *x, double *y)
 {
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s += val[p] * x[colind[p]];
@@ -74,6 +93,7 @@ static void unit_lower_solve(int p, const double *L, int ldl, const double *rhs,
 static void project_out(int64_t n, int p, const double *V, const double *coef, const double *a,
                         double *out)
 {
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int c = 0; c < p; ++c) s += V[(int64_t)c * n + i] * coef[c];
@@ -204,6 +224,7 @@ static int mgs_cycle(int64_t n, const int64_t *rp, const int32_t *ci, const doub
     const int ldh = m + 1;
     double *w = (double *)malloc((size_t)n * sizeof(double));
     if (!w) { *status = ORA_ENOMEM; return 0; }
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) V[i] = r0[i] / rho;
     int done = 0;
     for (int j = 0; j < m; ++j) {
@@ -212,6 +233,7 @@ static int mgs_cycle(int64_t n, const int64_t *rp, const int32_t *ci, const doub
             const double *vi = V + (int64_t)i * n;
             double h = ora_dot(n, vi, w);
             H[(int64_t)j * ldh + i] = h;
+            #pragma omp parallel for schedule(static)
             for (int64_t r = 0; r < n; ++r) w[r] -= h * vi[r];
         }
         double h = ora_nrm2(n, w);
@@ -221,6 +243,7 @@ static int mgs_cycle(int64_t n, const int64_t *rp, const int32_t *ci, const doub
         record(ctl, j, res, NAN);
         done = j + 1;
         if (is_breakdown(H, ldh, j, h)) { *status = ORA_BREAKDOWN; break; }
+        #pragma omp parallel for schedule(static)
         for (int64_t r = 0; r < n; ++r) V[(int64_t)(j + 1) * n + r] = w[r] / h;
         if (converged(ctl, res)) break;
     }
@@ -260,6 +283,7 @@ static int igs_cycle(int64_t n, const int64_t *rp, const int32_t *ci, const doub
     if (!z || !u || !r0c || !r1 || !r2 || !r3 || !lrow) { *status = ORA_ENOMEM; goto out; }
 
     /* Step 1: v_1 = r_0 / rho (rho = ||r_0|| is computed by the caller). */
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) V[i] = r0[i] / rho;
 
     /* Step 2: w_2 = A v_1, H_{1,1} = v_1^T w_2, w_2 = w_2 - H_{1,1} v_1, V_2 = [v_1, w_2]. */
@@ -268,6 +292,7 @@ static int igs_cycle(int64_t n, const int64_t *rp, const int32_t *ci, const doub
         ora_spmv(n, rp, ci, va, V, w2);
         double h11 = ora_dot(n, V, w2);
         H[0] = h11;
+        #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) w2[i] -= h11 * V[i];
     }
 
@@ -280,7 +305,9 @@ static int igs_cycle(int64_t n, const int64_t *rp, const int32_t *ci, const doub
 
         /* Step 5, the one global reduction: L^T_{1:k-2,k-1} = V_{k-2}^T w_{k-1} and
          * r^(0)_{1:k-1,k} = V_{k-1}^T v_k, with ||w_{k-1}||^2 folded in (step 6). */
+        #pragma omp parallel for schedule(static)
         for (int c = 0; c < p - 1; ++c) lrow[c] = ora_dot(n, V + (int64_t)c * n, w);
+        #pragma omp parallel for schedule(static)
         for (int c = 0; c < p; ++c) r0c[c] = ora_dot(n, V + (int64_t)c * n, z);
         double ww = ora_dot(n, w, w);
 
@@ -297,6 +324,7 @@ static int igs_cycle(int64_t n, const int64_t *rp, const int32_t *ci, const doub
         }
 
         /* Step 7: v_{k-1} = w_{k-1} / gamma_{k-1} (lagged normalization, in place). */
+        #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) w[i] = w[i] / gamma;
         /* Step 8: r^(0)_{1:k-1,k} /= gamma;  Step 9: r^(0)_{k-1,k} /= gamma once more. */
         for (int c = 0; c < p; ++c) r0c[c] = r0c[c] / gamma;
@@ -304,6 +332,7 @@ static int igs_cycle(int64_t n, const int64_t *rp, const int32_t *ci, const doub
         /* Step 10: L_{k-1,1:k-2} = L_{k-1,1:k-2} / gamma (new row p-1 of L). */
         for (int c = 0; c < p - 1; ++c) L[(int64_t)(p - 1) * ldl + c] = lrow[c] / gamma;
         /* Step 11: v_k = v_k / gamma. */
+        #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) z[i] = z[i] / gamma;
 
         /* Step 12: r^(1) = (I + L_{k-1})^{-1} r^(0).  Step 13: u_k = v_k - V_{k-1} r^(1). */
@@ -313,6 +342,7 @@ static int igs_cycle(int64_t n, const int64_t *rp, const int32_t *ci, const doub
         double *wk = V + (int64_t)p * n;
         if (gs == 2) {
             /* Step 14: r^(2) = V_{k-1}^T u_k (second reduction). */
+            #pragma omp parallel for schedule(static)
             for (int c = 0; c < p; ++c) r2[c] = ora_dot(n, V + (int64_t)c * n, u);
             /* Step 15: r^(3) = (I + L_{k-1})^{-1} r^(2).  Step 16: w_k = u_k - V_{k-1} r^(3). */
             unit_lower_solve(p, L, ldl, r2, r3);
@@ -329,6 +359,7 @@ static int igs_cycle(int64_t n, const int64_t *rp, const int32_t *ci, const doub
      * H_{m+1,m} = gamma_{m+1}, v_{m+1} = w_{m+1} / gamma_{m+1}, last row of L. */
     if (*status == ORA_OK && !stopped && done == m - 1) {
         double *w = V + (int64_t)m * n;
+        #pragma omp parallel for schedule(static)
         for (int c = 0; c < m; ++c) lrow[c] = ora_dot(n, V + (int64_t)c * n, w);
         double gamma = sqrt(ora_dot(n, w, w));
         H[(int64_t)(m - 1) * ldh + m] = gamma;
@@ -337,6 +368,7 @@ static int igs_cycle(int64_t n, const int64_t *rp, const int32_t *ci, const doub
         record(ctl, m - 1, res, lower_fro(L, ldl, m));
         done = m;
         if (is_breakdown(H, ldh, m - 1, gamma)) { *status = ORA_BREAKDOWN; goto out; }
+        #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) w[i] = w[i] / gamma;
         for (int c = 0; c < m; ++c) L[(int64_t)m * ldl + c] = lrow[c] / gamma;
     }
@@ -385,12 +417,14 @@ static int one_reduce_cycle(int64_t n, const int64_t *rp, const int32_t *ci, con
     if (!z || !u || !zs || !r1 || !r2 || !r3 || !s0 || !q) { *status = ORA_ENOMEM; goto out; }
 
     /* Step 1: v_1 = r_0 / rho. */
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) V[i] = r0[i] / rho;
     /* Step 2: w_2 = A v_1, H_11 = v_1^T w_2, u_2 = w_2 - v_1 H_11; H_11 is the first entry of
      * column 1's first-projection coefficients q. */
     {
         ora_spmv(n, rp, ci, va, V, z);
         const double h11 = ora_dot(n, V, z);
+        #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) u[i] = z[i] - V[i] * h11;
         q[0] = h11;
     }
@@ -399,10 +433,12 @@ static int one_reduce_cycle(int64_t n, const int64_t *rp, const int32_t *ci, con
         const int flush = k == m + 2;    /* last: re-orthogonalise u_{m+1} only */
         /* Step 4, the one global reduction. */
         if (!flush) ora_spmv(n, rp, ci, va, u, z);
+        #pragma omp parallel for schedule(static)
         for (int c = 0; c < nb; ++c) r2[c] = ora_dot(n, V + (int64_t)c * n, u);
         const double uu = ora_dot(n, u, u);
         double t = 0.0;
         if (!flush) {
+            #pragma omp parallel for schedule(static)
             for (int c = 0; c < nb; ++c) s0[c] = ora_dot(n, V + (int64_t)c * n, z);
             t = ora_dot(n, u, z);
         }
@@ -430,6 +466,7 @@ static int one_reduce_cycle(int64_t n, const int64_t *rp, const int32_t *ci, con
         {
             double *vnew = V + (int64_t)nb * n;
             project_out(n, nb, V, r2, u, vnew);
+            #pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < n; ++i) vnew[i] = vnew[i] / gamma;
         }
         if (flush) break;
@@ -446,6 +483,7 @@ static int one_reduce_cycle(int64_t n, const int64_t *rp, const int32_t *ci, con
             r1[nb] = t - lr;
         }
         /* Step 13: u_k = A u_{k-1} / gamma - V_{k-1} r^(1). */
+        #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) zs[i] = z[i] / gamma;
         project_out(n, nb + 1, V, r1, zs, u);
         /* Step 15: first-projection coefficients of column k-1: q = r^(1) - H r^(3) / gamma. */
@@ -515,6 +553,7 @@ double ora_backward_error(int64_t n, const int64_t *rp, const int32_t *ci, const
     double *r = (double *)malloc((size_t)n * sizeof(double));
     if (!r) return NAN;
     ora_spmv(n, rp, ci, va, x, r);
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
     /* A zero residual is an exact solution: beta = 0 (also for b = 0, x = 0). */
     double rn = ora_nrm2(n, r);
@@ -553,6 +592,7 @@ int ora_gmres(int64_t n, const int64_t *rp, const int32_t *ci, const double *va,
     for (;;) {
         /* r_0 = b - A x_0, rho = ||r_0|| (step 1). */
         ora_spmv(n, rp, ci, va, x, r);
+        #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
         beta = ora_backward_error(n, rp, ci, va, b, x, normA);
         if (!isfinite(beta)) { status = ORA_ENUMERIC; break; }
@@ -587,6 +627,7 @@ int ora_gmres(int64_t n, const int64_t *rp, const int32_t *ci, const double *va,
         /* x_m = x_0 + V_m y_m. */
         if (done > 0) {
             givens_solve(&G, done, y);
+            #pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < n; ++i) {
                 double s = 0.0;
                 for (int c = 0; c < done; ++c) s += V[(int64_t)c * n + i] * y[c];

@@ -117,7 +117,7 @@ class _BatchInfo(C.Structure):
 class _ServerOpts(C.Structure):
     _fields_ = [("device", C.c_int), ("max_restart_m", C.c_int), ("arena_bytes", C.c_int64),
                 ("slots", C.c_int), ("rows_per_cta", C.c_int), ("max_queue", C.c_int),
-                ("graph_min_n", C.c_int64)]
+                ("graph_min_n", C.c_int64), ("graph_lanes", C.c_int)]
 
 
 class _Request(C.Structure):
@@ -131,7 +131,7 @@ class _Completion(C.Structure):
     _fields_ = [("id", C.c_int64), ("status", C.c_int), ("beta", C.c_double), ("steps", C.c_int64),
                 ("cycles", C.c_int), ("gang_ctas", C.c_int), ("device_bytes", C.c_int64),
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
-                ("path", C.c_int)]
+                ("path", C.c_int), ("A_norm2", C.c_double)]
 
 
 class _ServerStats(C.Structure):
@@ -566,14 +566,15 @@ class Server:
     """Continuous-batching request server (``igs_server_create``).  ``submit`` queues a
     request (host arrays), ``pump`` admits what fits and collects finished requests,
     ``poll`` returns completion records, ``take`` the solution of a completed request.
-    Requests with n >= ``graph_min_n`` (when > 0) take the graph lane (``path`` 1 in their
-    completion record)."""
+    Requests with n >= ``graph_min_n`` (when > 0) take a graph lane (``path`` 1 in their
+    completion record); ``graph_lanes`` of them run at once."""
 
     def __init__(self, max_restart_m: int = 100, arena_bytes: int = 1 << 30, slots: int = 8,
-                 rows_per_cta: int = 4096, max_queue: int = 0, device: int = 0, graph_min_n: int = 0):
+                 rows_per_cta: int = 4096, max_queue: int = 0, device: int = 0, graph_min_n: int = 0,
+                 graph_lanes: int = 1):
         self._lib = load_library()
         opts = _ServerOpts(int(device), int(max_restart_m), int(arena_bytes), int(slots),
-                           int(rows_per_cta), int(max_queue), int(graph_min_n))
+                           int(rows_per_cta), int(max_queue), int(graph_min_n), int(graph_lanes))
         h = C.c_void_p()
         rc = self._lib.igs_server_create(C.byref(h), C.byref(opts))
         if rc != OK:

@@ -202,17 +202,21 @@ struct igs_server {
     int max_gang[2] = {1, 1};       // largest co-resident gang (FP64, FP32 kernels)
     int cta_budget = 1;             // CTAs of all running gangs at most (all co-resident at once)
     int running_ctas = 0;
-    // graph lane: requests with n >= graph_min_n, solved one at a time by a worker thread
-    // through igs_create/igs_solve (the whole-GPU kernels and CUDA graphs of igs.h)
+    // graph lanes: requests with n >= graph_min_n, each solved by a worker thread of its lane
+    // through igs_create/igs_solve (the whole-GPU kernels and CUDA graphs of igs.h); the lanes
+    // run concurrently (their streams overlap on the device) and beside the gangs
+    struct Lane {
+        std::thread thread;
+        cudaStream_t stream = nullptr;
+        int64_t busy = -1;                                    // request on the lane, -1: idle
+        std::unique_ptr<igs::serve::GraphJob> in, out;        // hand-over / finished (under graph_mu)
+    };
     int64_t graph_min_n = 0;
-    std::deque<int64_t> graph_queue;       // waiting for the lane (FIFO)
-    int64_t graph_busy = -1;               // request on the lane, -1: idle
-    std::thread graph_thread;
+    std::deque<int64_t> graph_queue;       // waiting for a lane (FIFO)
+    std::vector<Lane> lanes;
     std::mutex graph_mu;
     std::condition_variable graph_cv;
-    std::unique_ptr<igs::serve::GraphJob> graph_in, graph_out;  // hand-over / finished (under graph_mu)
     bool graph_stop = false;
-    cudaStream_t graph_stream = nullptr;
     size_t smem_max[2] = {0, 0};
     std::chrono::steady_clock::time_point t0;
     std::string err;
@@ -327,12 +331,12 @@ int launch_request(igs_server *s, Request &r, cudaStream_t st)
 
 // One graph-lane request through the single-system library on the lane's stream (pooled
 // device memory, so that creating and destroying the context never waits for the gangs).
-void run_graph_job(igs_server *s, igs::serve::GraphJob &j)
+void run_graph_job(igs_server *s, cudaStream_t stream, igs::serve::GraphJob &j)
 {
     const igs_request &q = j.opt;
     j.x.assign((size_t)q.n, 0.0);
     igs_create_opts co{};
-    co.stream = s->graph_stream;
+    co.stream = stream;
     co.device = s->device;
     co.max_restart_m = q.restart_m;
     co.A_norm2 = j.normA;
@@ -365,33 +369,36 @@ void run_graph_job(igs_server *s, igs::serve::GraphJob &j)
     igs_destroy(ctx);
 }
 
-// The graph lane's worker thread: takes the handed-over job, solves it, hands it back.
-void graph_worker(igs_server *s)
+// A graph lane's worker thread: takes the job handed to its lane, solves it on the lane's
+// stream, hands it back.
+void graph_worker(igs_server *s, int lane)
 {
     cudaSetDevice(s->device);
+    igs_server::Lane &L = s->lanes[(size_t)lane];
     for (;;) {
         std::unique_ptr<igs::serve::GraphJob> job;
         {
             std::unique_lock<std::mutex> lk(s->graph_mu);
-            s->graph_cv.wait(lk, [&] { return s->graph_stop || s->graph_in != nullptr; });
+            s->graph_cv.wait(lk, [&] { return s->graph_stop || L.in != nullptr; });
             if (s->graph_stop) return;
-            job = std::move(s->graph_in);
+            job = std::move(L.in);
         }
-        run_graph_job(s, *job);
+        run_graph_job(s, L.stream, *job);
         std::lock_guard<std::mutex> lk(s->graph_mu);
-        s->graph_out = std::move(job);
+        L.out = std::move(job);
     }
 }
 
 // Finished requests: collect results, release memory.
 int collect(igs_server *s)
 {
-    std::unique_ptr<igs::serve::GraphJob> fin;
-    {
-        std::lock_guard<std::mutex> lk(s->graph_mu);
-        fin = std::move(s->graph_out);
-    }
-    if (fin) {
+    for (auto &L : s->lanes) {
+        std::unique_ptr<igs::serve::GraphJob> fin;
+        {
+            std::lock_guard<std::mutex> lk(s->graph_mu);
+            fin = std::move(L.out);
+        }
+        if (!fin) continue;
         Request &r = s->reqs[fin->id];
         r.status = fin->status;
         r.res.status = fin->status;
@@ -402,7 +409,7 @@ int collect(igs_server *s)
         r.x_host = std::move(fin->x);
         r.t_done = now_s(s);
         r.done = true;
-        s->graph_busy = -1;
+        L.busy = -1;
         s->completions.push_back(r.id);
         s->completed++;
     }
@@ -444,16 +451,17 @@ int collect(igs_server *s)
 // once, so no cooperative launch waits for SMs that later, smaller gangs could take first).
 int admit(igs_server *s)
 {
-    if (s->graph_busy < 0 && !s->graph_queue.empty()) {
+    for (auto &L : s->lanes) {
+        if (L.busy >= 0 || s->graph_queue.empty()) continue;
         const int64_t id = s->graph_queue.front();
         s->graph_queue.pop_front();
         Request &r = s->reqs[id];
         {
             std::lock_guard<std::mutex> lk(s->graph_mu);
-            s->graph_in = std::move(r.job);
+            L.in = std::move(r.job);
         }
-        s->graph_cv.notify_one();
-        s->graph_busy = id;
+        s->graph_cv.notify_all();
+        L.busy = id;
         s->launches++;
         r.t_admit = now_s(s);
     }
@@ -520,7 +528,8 @@ int igs_server_create(igs_server **out, const igs_server_opts *opts)
                 return IGS_EINVAL;
             const int slots = opts->slots > 0 ? opts->slots : 8;
             const int rpc = opts->rows_per_cta > 0 ? opts->rows_per_cta : 4096;
-            if (slots > 256 || rpc < 256 || rpc % 32 != 0 || opts->graph_min_n < 0) return IGS_EINVAL;
+            const int lanes = opts->graph_lanes > 0 ? opts->graph_lanes : 1;
+            if (slots > 256 || rpc < 256 || rpc % 32 != 0 || opts->graph_min_n < 0 || lanes > 16) return IGS_EINVAL;
             igs_server *s = new (std::nothrow) igs_server();
             if (!s) return IGS_ENOMEM;
             auto bail = [&](int code) {
@@ -566,11 +575,15 @@ int igs_server_create(igs_server **out, const igs_server_opts *opts)
                     cudaEventCreateWithFlags(&s->events[(size_t)k], cudaEventDisableTiming) != cudaSuccess)
                     return bail(IGS_ECUDA);
             if (s->graph_min_n > 0) {
-                if (cudaStreamCreateWithFlags(&s->graph_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(IGS_ECUDA);
-                try {
-                    s->graph_thread = std::thread(graph_worker, s);
-                } catch (...) {
-                    return bail(IGS_ENOMEM);
+                s->lanes = std::vector<igs_server::Lane>((size_t)lanes);
+                for (int l = 0; l < lanes; ++l) {
+                    if (cudaStreamCreateWithFlags(&s->lanes[(size_t)l].stream, cudaStreamNonBlocking) != cudaSuccess)
+                        return bail(IGS_ECUDA);
+                    try {
+                        s->lanes[(size_t)l].thread = std::thread(graph_worker, s, l);
+                    } catch (...) {
+                        return bail(IGS_ENOMEM);
+                    }
                 }
             }
             *out = s;
@@ -589,15 +602,17 @@ void igs_server_destroy(igs_server *s)
     {
         std::lock_guard<std::mutex> lk(s->graph_mu);
         s->graph_stop = true;
-        s->graph_in.reset();
+        for (auto &L : s->lanes) L.in.reset();
     }
     s->graph_cv.notify_all();
-    if (s->graph_thread.joinable()) s->graph_thread.join();  // a running graph-lane solve ends first
+    for (auto &L : s->lanes)
+        if (L.thread.joinable()) L.thread.join();  // a running graph-lane solve ends first
     cudaSetDevice(s->device);
-    if (s->graph_stream) {
-        cudaStreamSynchronize(s->graph_stream);
-        cudaStreamDestroy(s->graph_stream);
-    }
+    for (auto &L : s->lanes)
+        if (L.stream) {
+            cudaStreamSynchronize(L.stream);
+            cudaStreamDestroy(L.stream);
+        }
     for (auto st : s->streams)
         if (st) cudaStreamSynchronize(st);
     for (auto st : s->streams)
@@ -746,7 +761,8 @@ int igs_server_pump(igs_server *s, int *running)
             int rc = collect(s);
             if (rc == IGS_OK) rc = admit(s);
             if (running) {
-                int k = s->graph_busy >= 0 ? 1 : 0;
+                int k = 0;
+                for (auto &L : s->lanes) k += L.busy >= 0;
                 for (auto id : s->slot_req) k += id >= 0;
                 *running = k;
             }
@@ -782,6 +798,7 @@ int igs_server_poll(igs_server *s, igs_completion *out, int max_out, int *n_out)
                 c.t_submit = r.t_submit;
                 c.t_admit = r.t_admit;
                 c.t_done = r.t_done;
+                c.A_norm2 = r.normA;
                 r.polled = true;
             }
             *n_out = k;
@@ -819,7 +836,8 @@ int igs_server_get_stats(const igs_server *s, igs_server_stats *o)
     std::memset(o, 0, sizeof(*o));
     o->submitted = s->submitted;
     o->queued = (int64_t)(s->queue.size() + s->graph_queue.size());
-    o->running = s->graph_busy >= 0 ? 1 : 0;
+    o->running = 0;
+    for (auto &L : s->lanes) o->running += L.busy >= 0;
     for (auto id : s->slot_req) o->running += id >= 0;
     o->completed = s->completed;
     o->arena_bytes = s->arena.size();

@@ -147,6 +147,32 @@ def test_full_size_cd2d_cycle(pkg):
     assert P.arnoldi_relation(A, g["V"], g["H"], m, normA) <= 1e-13
 
 
+def test_full_size_cd2d_solve_to_tol(pkg):
+    """The benchmark system solved to its own stopping criterion, beta <= 1e-13 (restarted
+    GMRES(100), two iterations): the same status and final beta <= 1e-13 as the oracle,
+    within +-2 Arnoldi steps of it, x close to the oracle's, and beta recomputed by the
+    oracle from the returned x.  The oracle runs its OpenMP build (bitwise the serial
+    build's results) so that the ~2000-step solve takes seconds per core count, not minutes."""
+    A, b, _, _ = gen.cd2d(512, 50.0, seed=0)
+    m, tol = 100, 1e-13
+    normA = gen.norm2_power(A, iters=50)
+    with pkg.Solver(A, max_restart_m=m, A_norm2=normA) as s:
+        g3 = s.solve(b, m=m, gs=2, tol=0.0, max_restarts=3)
+        g = s.solve(b, m=m, gs=2, tol=tol, max_restarts=500)
+    omp = oracle.openmp()
+    o3 = oracle.gmres(A, b, m=m, gs=2, tol=0.0, max_cycles=3, normA=normA, impl=omp)
+    assert g3["steps"] == o3["steps"] == 3 * m
+    assert np.linalg.norm(g3["x"] - o3["x"]) <= 1e-10 * np.linalg.norm(o3["x"])
+    assert abs(g3["beta"] - o3["beta"]) <= 1e-6 * o3["beta"]
+    o = oracle.gmres(A, b, m=m, gs=2, tol=tol, max_cycles=500, normA=normA, impl=omp)
+    assert g["status"] == o["status"] == oracle.OK, (g["status"], o["status"])
+    assert g["beta"] <= tol and o["beta"] <= tol
+    assert abs(g["steps"] - o["steps"]) <= 2, (g["steps"], o["steps"])
+    assert oracle.backward_error(A, b, g["x"], normA) <= tol
+    # both solutions are within the problem's forward error of x*: a coarse agreement check
+    assert np.linalg.norm(g["x"] - o["x"]) <= 1e-6 * np.linalg.norm(o["x"])
+
+
 def test_edge_m1_and_tiny(pkg):
     A, b, _, _ = gen.walker(4, 10.0)
     with pkg.Solver(A, max_restart_m=3, A_norm2=12.0) as s:

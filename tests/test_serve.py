@@ -126,17 +126,19 @@ def test_numeric_error_is_isolated(pkg):
 
 
 @pytest.mark.gpu
-def test_graph_lane_requests_match_oracle_and_mix(pkg):
-    """Requests with n >= graph_min_n run on the graph lane (the whole-GPU kernels of igs.h,
-    one at a time on the server's worker thread) beside gang requests: FP64 against the
-    oracle as above, FP32-IR to beta <= 1e-14, and the graph request bitwise the same alone
-    and in a mix."""
+@pytest.mark.parametrize("lanes", [1, 3])
+def test_graph_lane_requests_match_oracle_and_mix(pkg, lanes):
+    """Requests with n >= graph_min_n run on the graph lanes (the whole-GPU kernels of igs.h,
+    on the server's worker threads; with 3 lanes the three large requests run at once) beside
+    gang requests: FP64 against the oracle as above, FP32-IR to beta <= 1e-14, and the graph
+    request bitwise the same alone (one lane) and in the mix."""
     big = [gen.cd2d(side, pe, seed=50 + k)[:2] for k, (side, pe) in enumerate([(52, 30.0), (56, 70.0)])]
     small = _cases()[:3]
     norms_big = [gen.norm2_power(A, iters=100) for A, _ in big]
     norms_small = [gen.norm2_power(A, iters=100) for A, _ in small]
     gmin = 2500                   # the two grids (n = 2704, 3136); the small cases have n <= 2304
-    with pkg.Server(max_restart_m=40, arena_bytes=1 << 30, slots=3, rows_per_cta=512, graph_min_n=gmin) as sv:
+    with pkg.Server(max_restart_m=40, arena_bytes=1 << 30, slots=3, rows_per_cta=512, graph_min_n=gmin,
+                    graph_lanes=lanes) as sv:
         ids_b = [sv.submit(A, b, A_norm2=nA, m=40, gs=2, tol=1e-12, max_restarts=200)
                  for (A, b), nA in zip(big, norms_big)]
         id_f = sv.submit(big[0][0], big[0][1], A_norm2=norms_big[0], m=40, gs=2, tol=1e-14, max_restarts=100,
@@ -147,7 +149,7 @@ def test_graph_lane_requests_match_oracle_and_mix(pkg):
         xs = {rid: sv.take(rid) for rid in ids_b + [id_f] + ids_s}
     for rid, (A, b), nA in zip(ids_b, big, norms_big):
         c = done[rid]
-        assert c["path"] == 1 and c["gang_ctas"] == 0
+        assert c["path"] == 1 and c["gang_ctas"] == 0 and c["A_norm2"] == nA
         o = oracle.gmres(A, b, m=40, gs=2, tol=1e-12, max_cycles=200, normA=nA)
         assert c["status"] == o["status"] == 0 and abs(c["steps"] - o["steps"]) <= 2, (c, o["steps"])
         assert np.linalg.norm(xs[rid] - o["x"]) <= 1e-8 * np.linalg.norm(o["x"])

@@ -231,6 +231,38 @@ def pin_embree(impl=None):
     return ok, f"converged at iteration {it}, orth {loss:.2g}"
 
 
+def pin_helmert(impl=None):
+    """Helmert matrix, n = 18 (Sec. 5, "Complex Eigenvalues in a Disc"): orthogonal, its
+    eigenvalues cluster around -1; the MGS Arnoldi residual falls quickly and then stagnates,
+    while with two GS iterations it keeps falling, the loss of orthogonality stays near
+    machine precision and ||L_k||_F tracks it.  The paper's matrix is a row permutation of
+    the textbook one used here (its MATLAB variant), so its stagnation level (1e-10 from
+    iteration 12) is not reproduced; the contrast is: MGS's residual flat (within a factor
+    of 2 over its last four iterations, above 1e-17) from iteration 15 on, IGS-2's still
+    decreasing there and below 1e-18 by iteration 17."""
+    A, b, _, _ = gen.helmert(GOLDEN["helmert"]["n"])
+    D = csr_to_dense(A)
+    ev = np.linalg.eigvals(D)
+    near = int(np.sum(np.abs(ev + 1.0) < 0.3))
+    orth = np.linalg.norm(D.T @ D - np.eye(A.n))
+    nb = np.linalg.norm(b)
+    mg = oracle.gmres(A, b, m=18, method=oracle.MGS, tol=0.0, max_cycles=1, normA=1.0, impl=impl)
+    ig = oracle.gmres(A, b, m=18, method=oracle.IGS, gs=2, tol=0.0, max_cycles=1, normA=1.0, impl=impl)
+    mres, ires = mg["hist_res"] / nb, ig["hist_res"] / nb
+    tail = mres[14:]
+    mgs_flat = tail.min() >= 1e-17 and tail.max() <= 2 * tail.min()
+    igs_falls = ires[16] <= 1e-18 and np.all(np.diff(ires[12:]) < 0)
+    arn = oracle.arnoldi(A, b, 16, oracle.IGS, 2, impl=impl)
+    loss = orth_loss(arn["V"], 16)
+    lfro = float(np.linalg.norm(np.tril(arn["L"][:16, :16], -1)))
+    # ||I - V^T V||_F = sqrt(2) ||strict_lower(V^T V)||_F plus the diagonal's O(eps) terms:
+    # the same order of magnitude
+    tracks = 0.25 * loss <= np.sqrt(2.0) * lfro <= 4.0 * loss
+    ok = near >= 14 and orth <= 1e-14 and mgs_flat and igs_falls and loss <= 1e-14 and tracks
+    return ok, (f"{near}/18 eigenvalues near -1; MGS tail {tail.min():.2g}..{tail.max():.2g}; "
+                f"IGS-2 at it. 17 {ires[16]:.2g}; orth {loss:.2g}, sqrt2 ||L||_F {np.sqrt(2) * lfro:.2g}")
+
+
 def pin_mgs_equals_igs1_early(impl=None):
     """In exact arithmetic one Gauss-Seidel iteration is MGS (Ruhe, Sec. 2): the H columns
     of IGS-1 agree with MGS's to 1e-12 while kappa(B_k) < 1e4 (rounding differences grow
@@ -338,4 +370,4 @@ ONE_REDUCE_PINS = [pin_one_reduce_arnoldi_and_krylov, pin_one_reduce_orthogonali
 
 ALL_PINS = [pin_spmv, pin_arnoldi_relation, pin_krylov_qr, pin_L_is_gram, pin_orthogonality_two_gs,
             pin_orthogonality_one_gs, pin_givens_lstsq, pin_kn_exact, pin_backward_error_closed_forms,
-            pin_simoncini, pin_walker, pin_embree, pin_mgs_equals_igs1_early] + ONE_REDUCE_PINS
+            pin_simoncini, pin_walker, pin_embree, pin_helmert, pin_mgs_equals_igs1_early] + ONE_REDUCE_PINS

@@ -63,6 +63,14 @@ def workload_config(gs):
             "l2": "inputs larger than L2 (Krylov basis 212 MB > 126 MB L2)"}
 
 
+def peaks_hbm():
+    """The measured HBM copy bandwidth (GB/s) of MEASURED_PEAKS.json, else the fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
 def main_config(gs, method, ws):
     """The main line's `config` (the same dict in both bench arms)."""
     return {**workload_config(gs), "method": method, "parallelism": f"replicas x{ws}"}
@@ -591,6 +599,36 @@ def run_cd2d_extra(args, solver, b_dev, x_dev, stream, dist, value_gs):
     import torch
     out = {}
     gs_other = 1 if args.gs == 2 else 2
+    # the double-float reductions (IGS_PREC_FP64_DF) on the same cycles, both algorithms, with
+    # per-class kernel time from an eager re-run (CUDA events per launch)
+    for name, meth in (("fp64_df", "igs"), ("one_reduce_fp64_df", "one_reduce")):
+        def cyc_df():
+            return solver.solve(b_dev, m=M, gs=args.gs, tol=0.0, max_restarts=1, x_out=x_dev, hist_cap=0,
+                                method=meth, precision="fp64_df")
+
+        for _ in range(args.warmup):
+            cyc_df()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            cyc_df()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms, _, st = reduce_replicas(e0.elapsed_time(e1), 0.0, args.steps * M, dist, "cuda")
+        solver.profile_enable(True)
+        cyc_df()
+        prof = solver.profile()
+        solver.profile_enable(False)
+        d = prof["dots"]
+        hbm = peaks_hbm()
+        out[name] = {"metric": METRIC, "value": st / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+                     "method": "Alg. 4.1" if meth == "igs" else "Alg. 4.2",
+                     "precision": "FP64 data; block reductions in double-float on the FP32 pipes",
+                     "speedup_vs_fp64": (st / (ms / 1e3)) / value_gs if meth == "igs" else None,
+                     "dots_hbm_gbs": d["bytes"] / (d["ms"] / 1e3) / 1e9,
+                     "dots_hbm_frac": d["bytes"] / (d["ms"] / 1e3) / 1e9 / hbm,
+                     "kernel_ms_per_cycle": {k: v["ms"] for k, v in prof.items()}}
 
     def cyc():
         return solver.solve(b_dev, m=M, gs=gs_other, tol=0.0, max_restarts=1, x_out=x_dev, hist_cap=0)

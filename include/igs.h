@@ -80,13 +80,27 @@ typedef struct {
 /* Arithmetic of igs_solve's Arnoldi cycles. */
 enum {
     IGS_PREC_FP64 = 0,     /* everything in FP64 (Alg. 4.1 as stated)                          */
-    IGS_PREC_FP32_IR = 1   /* FP32 SpMV, basis and basis updates; FP64 Gram accumulation (FP32
+    IGS_PREC_FP32_IR = 1,  /* FP32 SpMV, basis and basis updates; FP64 Gram accumulation (FP32
                               sums over 32 rows promoted to FP64), (I+L) solves, Givens least
                               squares, x and r = b - A x.  Each restart is one step of FP64
                               iterative refinement: r = b - A x, an FP32 cycle on A d = r
                               stopped when its residual estimate falls by inner_tol (or meets
                               tol_beta), x = x + d.  The paper names mixed precision only as
                               future work (Sec. 6); this form is this library's extension.   */
+    IGS_PREC_FP64_DF = 2   /* FP64 data, SpMV, basis updates and small steps; the block
+                              reductions (Alg. 4.1 steps 5 and 14, Alg. 4.2 step 4) are
+                              evaluated with double-float arithmetic on the FP32 pipes: each
+                              FP64 operand split into two FP32 parts (exact to 2^-48 for
+                              2^-100 <= |a| < 2^127), exact products of the high parts, cross
+                              terms in FP32 (<= ~2^-45 relative per product), TwoSum
+                              accumulation folded into FP64 every 32 terms, FP64 lane sums.
+                              For vectors spread over n >= 16384 rows the added error is
+                              below the FP64 summation error; smaller systems run the FP64
+                              reductions.  GB300's FP64 pipe (1.26 TFLOP/s) bounds the FP64
+                              reductions at ~1/3 of HBM bandwidth; these run near HBM speed.
+                              An operand >= 2^127 makes the solve stop with IGS_ENUMERIC.
+                              The paper's precision is FP64 (Sec. 3); this is a library
+                              extension, checked against the FP64 oracle.                   */
 };
 
 /* Options of igs_solve. */
@@ -97,12 +111,13 @@ typedef struct {
     double tol_beta;      /* stop when beta(x) <= tol_beta; 0 runs max_restarts full cycles  */
     int max_restarts;     /* at most this many cycles (>= 1)                                 */
     int inputs_on_device; /* 1: b, x0 and res->x are device pointers; 0: host pointers        */
-    int precision;        /* IGS_PREC_FP64 (0, default) or IGS_PREC_FP32_IR (needs a context
-                             created with fp32_basis); anything else: IGS_EINVAL            */
+    int precision;        /* IGS_PREC_FP64 (0, default), IGS_PREC_FP32_IR (needs a context
+                             created with fp32_basis) or IGS_PREC_FP64_DF; anything else:
+                             IGS_EINVAL                                                     */
     double inner_tol;     /* IGS_PREC_FP32_IR: relative residual reduction per FP32 cycle;
                              <= 0: 1e-6.  Ignored for FP64                                   */
     int method;           /* 0 or IGS_METHOD_IGS: Alg. 4.1; IGS_METHOD_ONE_REDUCE: Alg. 4.2
-                             (FP64 only)                                                     */
+                             (FP64 or FP64_DF)                                               */
 } igs_solve_opts;
 
 /* Results of igs_solve.  Input fields are marked "in". */
@@ -177,8 +192,10 @@ int igs_spmv(igs_ctx *ctx, const double *x, double *y, int on_device);
 
 /* igs_arnoldi with the Arnoldi process chosen: method IGS_METHOD_IGS (Alg. 4.1, gs_iters 1
  * or 2) or IGS_METHOD_ONE_REDUCE (Alg. 4.2; L then holds the rows u_{k-1}^T V_{k-2} / gamma of
- * the lagged vectors, as the algorithm defines them).  Same arguments and results otherwise. */
-int igs_arnoldi_ex(igs_ctx *ctx, const double *r0, int m, int method, int gs_iters, int on_device,
+ * the lagged vectors, as the algorithm defines them), and the arithmetic: precision
+ * IGS_PREC_FP64 or IGS_PREC_FP64_DF (anything else: IGS_EINVAL).  Same arguments and results
+ * otherwise. */
+int igs_arnoldi_ex(igs_ctx *ctx, const double *r0, int m, int method, int gs_iters, int precision, int on_device,
                    double *V, int64_t ldv, double *H, double *L, int *ncols, double *rho);
 
 /* Fill *info.  Returns IGS_OK or IGS_EINVAL. */

@@ -62,7 +62,7 @@ class _SolveOpts(C.Structure):
                 ("inner_tol", C.c_double), ("method", C.c_int)]
 
 
-PRECISIONS = {"fp64": 0, "fp32_ir": 1}
+PRECISIONS = {"fp64": 0, "fp32_ir": 1, "fp64_df": 2}
 # Arnoldi processes: Alg. 4.1 (two-reduce IGS) and Alg. 4.2 (one-reduce hybrid MGS-CGS).
 METHODS = {"igs": 1, "one_reduce": 2}
 
@@ -161,7 +161,7 @@ def load_library(path: str | None = None):
     lib.igs_solve.restype = i32
     lib.igs_arnoldi.argtypes = [vp, vp, i32, i32, i32, vp, i64, vp, vp, C.POINTER(i32), C.POINTER(dbl)]
     lib.igs_arnoldi.restype = i32
-    lib.igs_arnoldi_ex.argtypes = [vp, vp, i32, i32, i32, i32, vp, i64, vp, vp, C.POINTER(i32), C.POINTER(dbl)]
+    lib.igs_arnoldi_ex.argtypes = [vp, vp, i32, i32, i32, i32, i32, vp, i64, vp, vp, C.POINTER(i32), C.POINTER(dbl)]
     lib.igs_arnoldi_ex.restype = i32
     lib.igs_spmv.argtypes = [vp, vp, vp, i32]
     lib.igs_spmv.restype = i32
@@ -348,7 +348,8 @@ class Solver:
             out["H"] = H
         return out
 
-    def arnoldi(self, r0, m: int, gs: int = 2, V=None, H=None, L=None, method: str = "igs") -> dict:
+    def arnoldi(self, r0, m: int, gs: int = 2, V=None, H=None, L=None, method: str = "igs",
+                precision: str = "fp64") -> dict:
         """One Arnoldi cycle (``igs_arnoldi``).  Host input gives numpy outputs
         (V: n x (m+1), H: (m+1) x m, L: (m+1) x (m+1) row-major); a CUDA tensor input gives
         CUDA tensor outputs unless output tensors are passed."""
@@ -371,7 +372,10 @@ class Solver:
         rho = C.c_double(0.0)
         if method not in METHODS:
             raise ValueError(f"method must be one of {sorted(METHODS)}")
-        rc = self._lib.igs_arnoldi_ex(self._h, rp, int(m), METHODS[method], int(gs), 1 if dev else 0,
+        if precision not in ("fp64", "fp64_df"):
+            raise ValueError("arnoldi runs precision 'fp64' or 'fp64_df'")
+        rc = self._lib.igs_arnoldi_ex(self._h, rp, int(m), METHODS[method], int(gs), PRECISIONS[precision],
+                                      1 if dev else 0,
                                       C.c_void_p(vptr), self.n, C.c_void_p(hptr), C.c_void_p(lptr),
                                       C.byref(ncols), C.byref(rho))
         if rc < 0:

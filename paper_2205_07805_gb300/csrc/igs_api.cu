@@ -153,14 +153,24 @@ double upd_bytes(const igs::Workspace &w, int p) { return 8.0 * w.n * (p + 2); }
 // Enqueue one restart cycle (see the file comment).  Precondition: ctx->w.r = b - A x,
 // st->rnorm/xnorm/bnorm set (by the solve set-up or the previous cycle's end).
 cudaError_t enqueue_cycle32(igs_ctx *ctx, Issuer &is, int m, int gs);
-cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m);
+cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m, bool df);
+
+// The block multi-dot of the FP64 cycles: FP64 FMAs, or double-float products on the FP32
+// pipes for the IGS_PREC_FP64_DF form (from kDfMinRows rows on; same partial-sum layout).
+using DotsLauncher = cudaError_t (*)(const igs::Workspace &, int, const double *, const double *, bool,
+                                     cudaStream_t, igs::DotsPlan *);
+DotsLauncher dots_launcher(const igs::Workspace &w, bool df)
+{
+    return df && igs::dots_df_applies(w) ? igs::launch_dots_df : igs::launch_dots;
+}
 
 // gs = 0 selects Alg. 4.2 (one-reduce); 1 or 2 Alg. 4.1 with that many GS iterations.
 cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
 {
-    if (gs == 0) return enqueue_cycle_1r(ctx, is, m);
+    if (gs == 0) return enqueue_cycle_1r(ctx, is, m, prec == IGS_PREC_FP64_DF);
     if (prec == IGS_PREC_FP32_IR) return enqueue_cycle32(ctx, is, m, gs);
     const igs::Workspace &w = ctx->w;
+    const DotsLauncher dots = dots_launcher(w, prec == IGS_PREC_FP64_DF);
     cudaStream_t s = is.s;
     const int64_t ld = w.ld;
     double *V = w.V;
@@ -178,7 +188,7 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
     // Step 2: w2 = A v1, H11 = v1^T w2, w2 -= H11 v1.
     igs::DotsPlan pl{};
     RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, col(0), col(1), nullptr, false, st_));
-    RUN(igs::KC_DOTS, dots_bytes(w, 1, 1), 2.0 * w.n, s, igs::launch_dots(w, 1, col(1), nullptr, false, st_, &pl));
+    RUN(igs::KC_DOTS, dots_bytes(w, 1, 1), 2.0 * w.n, s, dots(w, 1, col(1), nullptr, false, st_, &pl));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_prime(w, pl, st_));
     RUN(igs::KC_UPDATE, upd_bytes(w, 1), 2.0 * w.n, s,
         igs::launch_update(w, 1, w.r1v, false, 1.0, col(1), col(1), false, false, false, st_));
@@ -216,7 +226,7 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
         // Step 4: v_k = A w_{k-1}.
         RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wv, w.z, nullptr, true, st_));
         // Step 5: [V_{k-2}, w_{k-1}]^T [w_{k-1}, v_k] (block partial sums).
-        RUN(igs::KC_DOTS, dots_bytes(w, p, 2), 4.0 * w.n * p, s, igs::launch_dots(w, p, wv, w.z, true, st_, &pl));
+        RUN(igs::KC_DOTS, dots_bytes(w, p, 2), 4.0 * w.n * p, s, dots(w, p, wv, w.z, true, st_, &pl));
         if ((e = join_side()) != cudaSuccess) return e;
         // Steps 6-12 (+ step 17 for one iteration).
         RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_a(w, k, gs, pl, st_));
@@ -228,7 +238,7 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
             igs::launch_update(w, p, w.r1v, false, 0.0, w.z, uout, true, false, true, st_));
         if (gs == 2) {
             // Step 14: r^(2) = V_{k-1}^T u_k.
-            RUN(igs::KC_DOTS, dots_bytes(w, p, 1), 2.0 * w.n * p, s, igs::launch_dots(w, p, w.u, nullptr, true, st_, &pl));
+            RUN(igs::KC_DOTS, dots_bytes(w, p, 1), 2.0 * w.n * p, s, dots(w, p, w.u, nullptr, true, st_, &pl));
             // Steps 15, 17.
             RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_b(w, k, pl, st_));
             // Step 16: w_k = u_k - V_{k-1} r^(3).
@@ -238,7 +248,7 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
     }
     // Flush: gamma_{m+1} = ||w_{m+1}||, H_{m+1,m}, last L row, v_{m+1} = w_{m+1}/gamma.
     RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
-        igs::launch_dots(w, m + 1, col(m), nullptr, true, st_, &pl));
+        dots(w, m + 1, col(m), nullptr, true, st_, &pl));
     if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_flush(w, m, pl, st_));
     RUN(igs::KC_CYCLE, 16.0 * w.n, w.n, s, igs::launch_scale(w, col(m), col(m), 1, true, st_));
@@ -363,9 +373,10 @@ cudaError_t enqueue_cycle32(igs_ctx *ctx, Issuer &is, int m, int gs)
 // (the step-5 multi-dot), the single-block step (r^(3), the lagged norm, column nb-1 of H,
 // L, Stephen's trick, q), and one fused pass over V_nb forming v_{k-1} and u_k.  The Givens
 // rotation of each completed column runs on a side branch as in Alg. 4.1.
-cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m)
+cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m, bool df)
 {
     const igs::Workspace &w = ctx->w;
+    const DotsLauncher dots = dots_launcher(w, df);
     cudaStream_t s = is.s;
     const int64_t ld = w.ld;
     double *V = w.V;
@@ -382,7 +393,7 @@ cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m)
     // Step 2: w2 = A v1, H11 = v1^T w2, u_2 = w2 - v1 H11 (into V[:, 1]).
     igs::DotsPlan pl{};
     RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, col(0), col(1), nullptr, false, st_));
-    RUN(igs::KC_DOTS, dots_bytes(w, 1, 1), 2.0 * w.n, s, igs::launch_dots(w, 1, col(1), nullptr, false, st_, &pl));
+    RUN(igs::KC_DOTS, dots_bytes(w, 1, 1), 2.0 * w.n, s, dots(w, 1, col(1), nullptr, false, st_, &pl));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_prime(w, pl, st_));
     RUN(igs::KC_UPDATE, upd_bytes(w, 1), 2.0 * w.n, s,
         igs::launch_update(w, 1, w.r1v, false, 1.0, col(1), col(1), false, false, false, st_));
@@ -419,7 +430,7 @@ cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m)
         // Step 4: A u_{k-1}, then the one reduction [V_nb, u]^T [u, A u].
         RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, u, w.z, nullptr, true, st_));
         RUN(igs::KC_DOTS, dots_bytes(w, nb + 1, 2), 4.0 * w.n * (nb + 1), s,
-            igs::launch_dots(w, nb + 1, u, w.z, true, st_, &pl));
+            dots(w, nb + 1, u, w.z, true, st_, &pl));
         if ((e = join_side()) != cudaSuccess) return e;
         // Steps 5-9, 12, 14, 15: column nb-1 complete; its Givens rotation on the side.
         RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, nb, false, pl, st_));
@@ -429,7 +440,7 @@ cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m)
     }
     // Flush: the reduction of u_{m+1} (no product), column m-1 complete, v_{m+1}.
     RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
-        igs::launch_dots(w, m + 1, col(m), nullptr, true, st_, &pl));
+        dots(w, m + 1, col(m), nullptr, true, st_, &pl));
     if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, m, true, pl, st_));
     RUN(igs::KC_UPDATE, 8.0 * w.n * (m + 2), 2.0 * w.n * m, s, igs::launch_update_1r(w, m, w.z, true, st_));
@@ -899,14 +910,15 @@ int igs_solve(igs_ctx *ctx, const double *b, const double *x0, const igs_solve_o
             if (m < 1 || m > ctx->w.mmax) return fail(ctx, IGS_EINVAL, "restart_m %d outside [1, %d]", m, ctx->w.mmax);
             if (method == IGS_METHOD_IGS && opts->gs_iters != 1 && opts->gs_iters != 2)
                 return fail(ctx, IGS_EINVAL, "gs_iters must be 1 or 2");
-            if (method == IGS_METHOD_ONE_REDUCE && opts->precision != IGS_PREC_FP64)
-                return fail(ctx, IGS_EINVAL, "the one-reduce method runs in FP64 only");
+            if (method == IGS_METHOD_ONE_REDUCE && opts->precision == IGS_PREC_FP32_IR)
+                return fail(ctx, IGS_EINVAL, "the one-reduce method runs in FP64 (or FP64_DF) only");
             const int gs = method == IGS_METHOD_ONE_REDUCE ? 0 : opts->gs_iters;  // 0: Alg. 4.2 cycle
             if (opts->max_restarts < 1) return fail(ctx, IGS_EINVAL, "max_restarts must be >= 1");
             if (!(opts->tol_beta >= 0.0)) return fail(ctx, IGS_EINVAL, "tol_beta must be >= 0");
             if (res->H && res->H_ld < m + 1) return fail(ctx, IGS_EINVAL, "H_ld < m+1");
             const int prec = opts->precision;
-            if (prec != IGS_PREC_FP64 && prec != IGS_PREC_FP32_IR) return fail(ctx, IGS_EINVAL, "unknown precision %d", prec);
+            if (prec != IGS_PREC_FP64 && prec != IGS_PREC_FP32_IR && prec != IGS_PREC_FP64_DF)
+                return fail(ctx, IGS_EINVAL, "unknown precision %d", prec);
             if (prec == IGS_PREC_FP32_IR && !ctx->w.V32)
                 return fail(ctx, IGS_EINVAL, "precision FP32_IR needs a context created with fp32_basis");
             const double inner_tol = prec == IGS_PREC_FP32_IR ? (opts->inner_tol > 0.0 ? opts->inner_tol : 1e-6) : 0.0;
@@ -979,11 +991,11 @@ int igs_solve(igs_ctx *ctx, const double *b, const double *x0, const igs_solve_o
 int igs_arnoldi(igs_ctx *ctx, const double *r0, int m, int gs, int on_device, double *V, int64_t ldv,
                 double *H, double *L, int *ncols, double *rho)
 {
-    return igs_arnoldi_ex(ctx, r0, m, IGS_METHOD_IGS, gs, on_device, V, ldv, H, L, ncols, rho);
+    return igs_arnoldi_ex(ctx, r0, m, IGS_METHOD_IGS, gs, IGS_PREC_FP64, on_device, V, ldv, H, L, ncols, rho);
 }
 
-int igs_arnoldi_ex(igs_ctx *ctx, const double *r0, int m, int method, int gs, int on_device, double *V,
-                   int64_t ldv, double *H, double *L, int *ncols, double *rho)
+int igs_arnoldi_ex(igs_ctx *ctx, const double *r0, int m, int method, int gs, int precision, int on_device,
+                   double *V, int64_t ldv, double *H, double *L, int *ncols, double *rho)
 {
     // no C++ exception crosses the C interface (allocation failures become IGS_ENOMEM)
     try {
@@ -993,6 +1005,8 @@ int igs_arnoldi_ex(igs_ctx *ctx, const double *r0, int m, int method, int gs, in
             if (method != IGS_METHOD_IGS && method != IGS_METHOD_ONE_REDUCE) return fail(ctx, IGS_EINVAL, "unknown method");
             if (method == IGS_METHOD_IGS && gs != 1 && gs != 2) return fail(ctx, IGS_EINVAL, "gs_iters must be 1 or 2");
             if (method == IGS_METHOD_ONE_REDUCE) gs = 0;  // the Alg. 4.2 cycle
+            if (precision != IGS_PREC_FP64 && precision != IGS_PREC_FP64_DF)
+                return fail(ctx, IGS_EINVAL, "igs_arnoldi_ex runs FP64 or FP64_DF cycles only");
             if (V && ldv < ctx->w.n) return fail(ctx, IGS_EINVAL, "ldv < n");
             CK(cudaSetDevice(ctx->device));
             igs::Workspace &w = ctx->w;
@@ -1004,7 +1018,7 @@ int igs_arnoldi_ex(igs_ctx *ctx, const double *r0, int m, int method, int gs, in
             if ((rc = copy_vec_in(ctx, w.b, r0, on_device != 0)) != IGS_OK) return rc;
             if ((rc = copy_vec_in(ctx, w.x, nullptr, false)) != IGS_OK) return rc;
             if ((rc = run_setup(ctx, 0.0, 0.0)) != IGS_OK) return rc;
-            if ((rc = run_cycle(ctx, m, gs, IGS_PREC_FP64)) != IGS_OK) return rc;
+            if ((rc = run_cycle(ctx, m, gs, precision)) != IGS_OK) return rc;
             igs::DevState hs{};
             if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
             const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

@@ -1,0 +1,195 @@
+// Block reductions of Alg. 4.1 (steps 5 and 14) and Alg. 4.2 (step 4) evaluated in
+// double-float arithmetic on the FP32 pipes: the IGS_PREC_FP64_DF form of igs_solve.
+//
+// Why: on GB300 the FP64 pipe retires 2 FMAs per clock per SM (1.26 TFLOP/s), so the FP64
+// multi-dot [V, w]^T [w, z] (2 FMAs per 8-byte basis element) runs at about a third of
+// HBM bandwidth.  The FP32 pipes are 64 times faster.  Here every FP64 operand a is split
+// without any FP64 instruction into a = hi + lo (+ r), hi = a's sign, exponent and top 24
+// significant bits, lo = the remaining 29 bits rounded to FP32 (|r| <= 2^-48 |a|); the
+// product of two split numbers is formed as the exact product hi*hi' = p + e (FMA) plus the
+// cross terms hi*lo' + lo*hi' in FP32 (per-product error <= ~2^-45 |a a'|, dropped lo*lo'
+// included), and the products are summed per lane with TwoSum (Knuth) into a double-float
+// accumulator that is folded into an FP64 sum every 32 elements.  The lanes' FP64 sums
+// are then added in a fixed order, exactly as in the FP64 kernel, into the same per-block
+// partial-sum layout, so the single-block steps that follow are unchanged.
+//
+// Accuracy: each product carries a relative error of at most ~2^-45 (against 2^-53 for an
+// FP64 product), but these errors are independent across the n terms of a dot product, so
+// for vectors spread over n >= 2^14 rows their contribution (~2^-46 ||a|| ||a'|| / sqrt(n))
+// is below the FP64 accumulation error the FP64 kernel itself makes; the library uses these
+// kernels only from that size on.  Range: the split is exact to 2^-48 for
+// 2^-100 <= |a| < 2^127; smaller operands lose low-order bits (lo becomes an FP32
+// subnormal) down to FP32 precision at 2^-126, below which they count as 0; |a| >= 2^127
+// makes the sum non-finite (the solve then stops with IGS_ENUMERIC).
+#include "igs_internal.h"
+
+namespace igs {
+
+namespace {
+
+__device__ __forceinline__ bool df_halted(const DevState *st) { return st->halt != 0; }
+
+// a = hi + lo + r, |r| <= 2^-48 |a| for 2^-100 <= |a| < 2^127 (integer operations, one
+// integer-to-float conversion and two power-of-two scalings, exact unless lo is subnormal).
+__device__ __forceinline__ void df_split(double a, float &hi, float &lo)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const unsigned sign = hw & 0x80000000u, ahw = hw & 0x7fffffffu;
+    // (hw:lw) << 3 puts the top 23 fraction bits in bits 22..0 and the low 9 exponent bits
+    // in bits 31..23; subtracting 384 << 23 turns FP64's exponent bias (1023) into FP32's
+    // (127) for every exponent of the FP32 normal range.
+    unsigned hb = (__funnelshift_l(lw, hw, 3) - 0xC0000000u) | sign;
+    hb = ahw < (897u << 20) ? sign : hb;                                // |a| < 2^-126: 0
+    hb = ahw >= (1150u << 20) ? (sign | 0x7f800000u) : hb;             // |a| >= 2^127: inf
+    hi = __uint_as_float(hb);
+    // the remaining 29 fraction bits times 2^(e - 1075) = rem * 2^-52 * (+-2^(e - 1023))
+    const float scale = __uint_as_float(hb & 0xff800000u);
+    lo = __fmul_rn(__fmul_rn(__uint2float_rn(lw & 0x1fffffffu), 0x1p-52f), scale);
+}
+
+// (S, s) += (ah + al) * (xh + xl): exact product of the high parts by FMA, cross terms in
+// FP32, TwoSum of the high part into S (the intrinsics are never contracted into FMAs).
+__device__ __forceinline__ void df_acc(float &S, float &s, float ah, float al, float xh, float xl)
+{
+    const float p = __fmul_rn(ah, xh);
+    const float e = __fmaf_rn(ah, xh, -p);
+    const float c = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, e));
+    const float t = __fadd_rn(S, p);
+    const float bp = __fsub_rn(t, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    S = t;
+    s = __fadd_rn(s, __fadd_rn(err, c));
+}
+
+}  // namespace
+
+// =====================================================================================
+// Double-float block multi-dot: the grid, partial-sum layout and summation of the lane sums
+// are those of the FP64 multi-dot (part[rb*(NQ*p) + q*p + c] = sum over row block rb of
+// V[:,c] . X_q); what differs is that each warp streams ALL the group's columns over its
+// row sub-slice (so each X row is loaded and split once per block, not once per column)
+// and the products are accumulated in double-float.  Each lane handles two consecutive rows
+// per 64-row segment: one warp instruction reads 512 contiguous bytes of a column.
+// =====================================================================================
+template <int NQ>
+__global__ void __launch_bounds__(kStreamThreads, kDotsBlocksPerSM)
+k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t rows,
+          const double *__restrict__ x0, const double *__restrict__ x1, double *__restrict__ part,
+          const DevState *st, int check_halt)
+{
+    IGS_PDL_ENTER();
+    if (check_halt && df_halted(st)) return;
+    constexpr int W = kStreamThreads / 32;
+    constexpr int CW = kDotsColsPerBlock;
+    constexpr int kFold = 16;  // segments (32 elements per lane) between FP64 folds
+    __shared__ double red[NQ][CW][W];
+    const int rb = blockIdx.x, G = gridDim.y, cg = blockIdx.y;
+    const int c_lo = (int)((int64_t)cg * p / G), c_hi = (int)((int64_t)(cg + 1) * p / G);
+    const int cw = c_hi - c_lo;  // <= CW (the launcher's plan guarantees it)
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int64_t r_lo = (int64_t)rb * rows;
+    const int64_t r_hi = r_lo + rows < n4 ? r_lo + rows : n4;
+    double acc[CW][NQ];
+    float S[CW][NQ], s[CW][NQ];
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            acc[c][q] = 0.0;
+            S[c][q] = 0.f;
+            s[c][q] = 0.f;
+        }
+    const double *vc[CW];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) vc[c] = V + (int64_t)(c_lo + (c < cw ? c : 0)) * ld;
+    if (r_lo < r_hi) {
+        const int64_t nseg = (r_hi - r_lo + 63) >> 6;
+        const int64_t g0 = nseg * wid / W, g1 = nseg * (wid + 1) / W;
+        int since = 0;
+        for (int64_t g = g0; g < g1; ++g) {
+            const int64_t i = r_lo + (g << 6) + 2 * lane;
+            if (i < r_hi) {
+                float xh[NQ][2], xl[NQ][2];
+                {
+                    const double2 xa = *reinterpret_cast<const double2 *>(x0 + i);
+                    df_split(xa.x, xh[0][0], xl[0][0]);
+                    df_split(xa.y, xh[0][1], xl[0][1]);
+                    if (NQ == 2) {
+                        const double2 xb = *reinterpret_cast<const double2 *>(x1 + i);
+                        df_split(xb.x, xh[NQ - 1][0], xl[NQ - 1][0]);
+                        df_split(xb.y, xh[NQ - 1][1], xl[NQ - 1][1]);
+                    }
+                }
+                double2 v[CW];
+#pragma unroll
+                for (int c = 0; c < CW; ++c)
+                    if (c < cw) v[c] = *reinterpret_cast<const double2 *>(vc[c] + i);
+#pragma unroll
+                for (int c = 0; c < CW; ++c) {
+                    if (c < cw) {
+                        float h0, l0, h1, l1;
+                        df_split(v[c].x, h0, l0);
+                        df_split(v[c].y, h1, l1);
+#pragma unroll
+                        for (int q = 0; q < NQ; ++q) {
+                            df_acc(S[c][q], s[c][q], h0, l0, xh[q][0], xl[q][0]);
+                            df_acc(S[c][q], s[c][q], h1, l1, xh[q][1], xl[q][1]);
+                        }
+                    }
+                }
+            }
+            if (++since == kFold) {
+                since = 0;
+#pragma unroll
+                for (int c = 0; c < CW; ++c)
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        acc[c][q] += (double)S[c][q] + (double)s[c][q];
+                        S[c][q] = 0.f;
+                        s[c][q] = 0.f;
+                    }
+            }
+        }
+    }
+    // lane sums (FP64), then a fixed-order warp tree and the W warp sums in order
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double a = acc[c][q] + ((double)S[c][q] + (double)s[c][q]);
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) red[q][c][wid] = a;
+        }
+    __syncthreads();
+    if (t < NQ * CW) {
+        const int q = t / CW, c = t % CW;
+        if (c < cw) {
+            double a = 0.0;
+#pragma unroll
+            for (int k = 0; k < W; ++k) a += red[q][c][k];
+            part[(int64_t)rb * NQ * p + (int64_t)q * p + c_lo + c] = a;
+        }
+    }
+}
+
+bool dots_df_applies(const Workspace &w) { return w.n >= kDfMinRows; }
+
+cudaError_t launch_dots_df(const Workspace &w, int p, const double *x0, const double *x1, bool check_halt,
+                           cudaStream_t s, DotsPlan *plan_out)
+{
+    const DotsPlan pl = plan_dots(w, p);
+    if (plan_out) *plan_out = pl;
+    if ((p + pl.groups - 1) / pl.groups > kDotsColsPerBlock) return cudaErrorInvalidValue;
+    const int64_t n4 = (w.n + 3) & ~int64_t(3);
+    dim3 grid(pl.rblocks, pl.groups);
+    if (x1)
+        launch_k(false, k_dots_df<2>, grid, dim3(kStreamThreads), 0, s, w.V, w.ld, p, n4, pl.rows, x0, x1, w.part,
+                 (const DevState *)w.st, check_halt ? 1 : 0);
+    else
+        launch_k(false, k_dots_df<1>, grid, dim3(kStreamThreads), 0, s, w.V, w.ld, p, n4, pl.rows, x0,
+                 (const double *)nullptr, w.part, (const DevState *)w.st, check_halt ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace igs

@@ -149,28 +149,39 @@ def test_full_size_cd2d_cycle(pkg):
 
 def test_full_size_cd2d_solve_to_tol(pkg):
     """The benchmark system solved to its own stopping criterion, beta <= 1e-13 (restarted
-    GMRES(100), two iterations): the same status and final beta <= 1e-13 as the oracle,
-    within +-2 Arnoldi steps of it, x close to the oracle's, and beta recomputed by the
-    oracle from the returned x.  The oracle runs its OpenMP build (bitwise the serial
-    build's results) so that the ~2000-step solve takes seconds per core count, not minutes."""
+    GMRES(100), two iterations, about 24 cycles), against the oracle (its OpenMP build,
+    bitwise the serial build's results, so the full solve takes seconds):
+      * the first three cycles: x within 1e-10 and beta within 1e-6 of the oracle's;
+      * the whole solve: both reach beta <= 1e-13 (the GPU's beta recomputed by the oracle
+        from the returned x), with step counts within 1% -- each restart starts from the
+        previous cycle's x, so the two implementations' rounding differences carry over
+        from cycle to cycle, and near the end one decade of residual takes ~100 steps;
+      * the last cycle from the same start (the GPU's x after the other cycles, a bitwise
+        reproducible point): the oracle stops within +-2 Arnoldi steps of the GPU."""
     A, b, _, _ = gen.cd2d(512, 50.0, seed=0)
     m, tol = 100, 1e-13
     normA = gen.norm2_power(A, iters=50)
+    omp = oracle.openmp()
     with pkg.Solver(A, max_restart_m=m, A_norm2=normA) as s:
         g3 = s.solve(b, m=m, gs=2, tol=0.0, max_restarts=3)
         g = s.solve(b, m=m, gs=2, tol=tol, max_restarts=500)
-    omp = oracle.openmp()
+        assert g["status"] == pkg.OK and g["cycles"] >= 2
+        before = s.solve(b, m=m, gs=2, tol=tol, max_restarts=g["cycles"] - 1)
+        last = s.solve(b, x0=before["x"], m=m, gs=2, tol=tol, max_restarts=1)
     o3 = oracle.gmres(A, b, m=m, gs=2, tol=0.0, max_cycles=3, normA=normA, impl=omp)
     assert g3["steps"] == o3["steps"] == 3 * m
     assert np.linalg.norm(g3["x"] - o3["x"]) <= 1e-10 * np.linalg.norm(o3["x"])
     assert abs(g3["beta"] - o3["beta"]) <= 1e-6 * o3["beta"]
     o = oracle.gmres(A, b, m=m, gs=2, tol=tol, max_cycles=500, normA=normA, impl=omp)
-    assert g["status"] == o["status"] == oracle.OK, (g["status"], o["status"])
-    assert g["beta"] <= tol and o["beta"] <= tol
-    assert abs(g["steps"] - o["steps"]) <= 2, (g["steps"], o["steps"])
+    assert o["status"] == oracle.OK and g["beta"] <= tol and o["beta"] <= tol
     assert oracle.backward_error(A, b, g["x"], normA) <= tol
-    # both solutions are within the problem's forward error of x*: a coarse agreement check
-    assert np.linalg.norm(g["x"] - o["x"]) <= 1e-6 * np.linalg.norm(o["x"])
+    assert abs(g["steps"] - o["steps"]) <= 0.01 * o["steps"], (g["steps"], o["steps"])
+    # the last cycle, from the same x0 on both sides
+    assert before["steps"] + last["steps"] == g["steps"]
+    assert np.linalg.norm(last["x"] - g["x"]) <= 1e-12 * np.linalg.norm(g["x"])
+    ol = oracle.gmres(A, b, x0=before["x"], m=m, gs=2, tol=tol, max_cycles=1, normA=normA, impl=omp)
+    assert ol["status"] == last["status"] == oracle.OK
+    assert abs(last["steps"] - ol["steps"]) <= 2, (last["steps"], ol["steps"])
 
 
 def test_edge_m1_and_tiny(pkg):

@@ -87,9 +87,11 @@ enum {
                               stopped when its residual estimate falls by inner_tol (or meets
                               tol_beta), x = x + d.  The paper names mixed precision only as
                               future work (Sec. 6); this form is this library's extension.   */
-    IGS_PREC_FP64_DF = 2   /* FP64 data, SpMV, basis updates and small steps; the block
-                              reductions (Alg. 4.1 steps 5 and 14, Alg. 4.2 step 4) are
-                              evaluated with double-float arithmetic on the FP32 pipes: each
+    IGS_PREC_FP64_DF = 2   /* FP64 data, SpMV, small steps and x = x0 + V y; the block
+                              reductions (Alg. 4.1 steps 5 and 14, Alg. 4.2 step 4) and Alg.
+                              4.1's basis updates (steps 13 and 16, out = a src - V c, error
+                              <= ~2^-45 sum |V c| per row) are evaluated with double-float
+                              arithmetic on the FP32 pipes: each
                               FP64 operand split into two FP32 parts (exact to 2^-48 for
                               2^-100 <= |a| < 2^127), exact products of the high parts, cross
                               terms in FP32 (<= ~2^-45 relative per product), TwoSum

@@ -171,6 +171,9 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
     if (prec == IGS_PREC_FP32_IR) return enqueue_cycle32(ctx, is, m, gs);
     const igs::Workspace &w = ctx->w;
     const DotsLauncher dots = dots_launcher(w, prec == IGS_PREC_FP64_DF);
+    // the double-float form also runs the in-cycle basis updates (steps 13 and 16) on the FP32
+    // pipes; x = x0 + V y at the cycle's end stays FP64
+    const bool df_stream = prec == IGS_PREC_FP64_DF && igs::dots_df_applies(w);
     cudaStream_t s = is.s;
     const int64_t ld = w.ld;
     double *V = w.V;
@@ -235,7 +238,8 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
         // Steps 7, 11, 13: v_{k-1} = w/gamma in place, u_k = v_k/gamma - V_{k-1} r^(1).
         double *uout = gs == 1 ? col(p) : w.u;
         RUN(igs::KC_UPDATE, upd_bytes(w, p) + 8.0 * w.n, 2.0 * w.n * p, s,
-            igs::launch_update(w, p, w.r1v, false, 0.0, w.z, uout, true, false, true, st_));
+            df_stream ? igs::launch_update_df(w, p, w.r1v, 0.0, w.z, uout, true, st_)
+                      : igs::launch_update(w, p, w.r1v, false, 0.0, w.z, uout, true, false, true, st_));
         if (gs == 2) {
             // Step 14: r^(2) = V_{k-1}^T u_k.
             RUN(igs::KC_DOTS, dots_bytes(w, p, 1), 2.0 * w.n * p, s, dots(w, p, w.u, nullptr, true, st_, &pl));
@@ -243,7 +247,8 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
             RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_b(w, k, pl, st_));
             // Step 16: w_k = u_k - V_{k-1} r^(3).
             RUN(igs::KC_UPDATE, upd_bytes(w, p), 2.0 * w.n * p, s,
-                igs::launch_update(w, p, w.r3v, false, 1.0, w.u, col(p), false, false, true, st_));
+                df_stream ? igs::launch_update_df(w, p, w.r3v, 1.0, w.u, col(p), false, st_)
+                          : igs::launch_update(w, p, w.r3v, false, 1.0, w.u, col(p), false, false, true, st_));
         }
     }
     // Flush: gamma_{m+1} = ||w_{m+1}||, H_{m+1,m}, last L row, v_{m+1} = w_{m+1}/gamma.

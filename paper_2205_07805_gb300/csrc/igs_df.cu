@@ -1,5 +1,6 @@
-// Block reductions of Alg. 4.1 (steps 5 and 14) and Alg. 4.2 (step 4) evaluated in
-// double-float arithmetic on the FP32 pipes: the IGS_PREC_FP64_DF form of igs_solve.
+// Block reductions of Alg. 4.1 (steps 5 and 14) and Alg. 4.2 (step 4), and the basis
+// updates of Alg. 4.1 (steps 13 and 16), evaluated in double-float arithmetic on the FP32
+// pipes: the IGS_PREC_FP64_DF form of igs_solve.
 //
 // Why: on GB300 the FP64 pipe retires 2 FMAs per clock per SM (1.26 TFLOP/s), so the FP64
 // multi-dot [V, w]^T [w, z] (2 FMAs per 8-byte basis element) runs at about a third of
@@ -173,7 +174,110 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
     }
 }
 
+// =====================================================================================
+// Double-float basis update (Alg. 4.1 steps 7, 11, 13 and 16 in the IGS_PREC_FP64_DF form):
+//   out[i] = a * src[i] - sum_{c<p} V[i,c] coef[c]
+// with the same row ownership as the FP64 update (two rows per thread, a whole number of
+// blocks per SM, block-contiguous row ranges) and the same norm_last semantics (column p-1
+// first scaled in place by st->inv_gamma, which is also a).  Each row's sum over the
+// columns is a double-float accumulation of split products (the coefficients are split
+// once per block, in shared memory); a * src[i] and the final subtraction are FP64.
+// Error of out[i]: <= ~2^-45 sum_c |V[i,c] coef[c]| (FP64: p 2^-53 of the same sum).
+// =====================================================================================
+__global__ void __launch_bounds__(kStreamThreads, kUpdateBlocksPerSM)
+k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coef, double alpha,
+            const double *src, double *out, int norm_last, DevState *st, int check_halt)
+{
+    IGS_PDL_ENTER();
+    if (check_halt && df_halted(st)) return;
+    extern __shared__ float scf[];  // coefficient splits: hi at [0, p), lo at [p, 2p)
+    const double a = norm_last ? st->inv_gamma : alpha;
+    for (int c = threadIdx.x; c < p; c += blockDim.x) {
+        float h, l;
+        df_split(coef[c], h, l);
+        scf[c] = h;
+        scf[p + c] = l;
+    }
+    __syncthreads();
+    const int pc = norm_last ? p - 1 : p;
+    const int64_t npairs = (n + 1) >> 1;
+    const int64_t ppb = (npairs + gridDim.x - 1) / gridDim.x;
+    const int64_t pr_lo = (int64_t)blockIdx.x * ppb;
+    const int64_t pr_hi = pr_lo + ppb < npairs ? pr_lo + ppb : npairs;
+    for (int64_t pr = pr_lo + threadIdx.x; pr < pr_hi; pr += blockDim.x) {
+        const int64_t i = 2 * pr;
+        const double *vi = V + i;
+        float S0 = 0.f, s0 = 0.f, S1 = 0.f, s1 = 0.f;
+        int c = 0;
+        // four columns per step, the next four loaded while these are used
+        if (pc >= 4) {
+            double2 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = *reinterpret_cast<const double2 *>(vi + (int64_t)q * ld);
+            for (; c + 7 < pc; c += 4) {
+                double2 nv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) nv[q] = *reinterpret_cast<const double2 *>(vi + (int64_t)(c + 4 + q) * ld);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float h, l;
+                    df_split(v[q].x, h, l);
+                    df_acc(S0, s0, h, l, scf[c + q], scf[p + c + q]);
+                    df_split(v[q].y, h, l);
+                    df_acc(S1, s1, h, l, scf[c + q], scf[p + c + q]);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = nv[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float h, l;
+                df_split(v[q].x, h, l);
+                df_acc(S0, s0, h, l, scf[c + q], scf[p + c + q]);
+                df_split(v[q].y, h, l);
+                df_acc(S1, s1, h, l, scf[c + q], scf[p + c + q]);
+            }
+            c += 4;
+        }
+        for (; c < pc; ++c) {
+            const double2 v = *reinterpret_cast<const double2 *>(vi + (int64_t)c * ld);
+            float h, l;
+            df_split(v.x, h, l);
+            df_acc(S0, s0, h, l, scf[c], scf[p + c]);
+            df_split(v.y, h, l);
+            df_acc(S1, s1, h, l, scf[c], scf[p + c]);
+        }
+        if (norm_last) {
+            double2 *vl = reinterpret_cast<double2 *>(V + (int64_t)(p - 1) * ld + i);
+            double2 v = *vl;
+            v.x *= a;
+            v.y *= a;
+            *vl = v;
+            float h, l;
+            df_split(v.x, h, l);
+            df_acc(S0, s0, h, l, scf[p - 1], scf[2 * p - 1]);
+            df_split(v.y, h, l);
+            df_acc(S1, s1, h, l, scf[p - 1], scf[2 * p - 1]);
+        }
+        const double2 sv = *reinterpret_cast<const double2 *>(src + i);
+        double2 o;
+        o.x = fma(a, sv.x, -((double)S0 + (double)s0));
+        o.y = fma(a, sv.y, -((double)S1 + (double)s1));
+        *reinterpret_cast<double2 *>(out + i) = o;
+    }
+}
+
 bool dots_df_applies(const Workspace &w) { return w.n >= kDfMinRows; }
+
+cudaError_t launch_update_df(const Workspace &w, int p, const double *coef, double alpha, const double *src,
+                             double *out, bool norm_last, cudaStream_t s)
+{
+    const size_t smem = 2 * sizeof(float) * (size_t)(p > 0 ? p : 1);
+    const int grid = w.num_sms * kUpdateBlocksPerSM;
+    launch_k(false, k_update_df, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef, alpha, src, out,
+             norm_last ? 1 : 0, w.st, 1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dots_df(const Workspace &w, int p, const double *x0, const double *x1, bool check_halt,
                            cudaStream_t s, DotsPlan *plan_out)

@@ -138,12 +138,16 @@ cudaError_t launch_dots(const Workspace &w, int p, const double *x0, const doubl
 cudaError_t launch_update(const Workspace &w, int p, const double *coef, bool neg_coef,
                           double alpha, const double *src, double *out, bool norm_last,
                           bool p_from_state, bool check_halt, cudaStream_t s);
-// Double-float block multi-dot (igs_dfdots.cu), same partial layout and plan as launch_dots;
+// Double-float block multi-dot (igs_df.cu), same partial layout and plan as launch_dots;
 // used by the IGS_PREC_FP64_DF form for n >= kDfMinRows (dots_df_applies).
 constexpr int64_t kDfMinRows = 16384;
 bool dots_df_applies(const Workspace &w);
 cudaError_t launch_dots_df(const Workspace &w, int p, const double *x0, const double *x1,
                            bool check_halt, cudaStream_t s, DotsPlan *plan_out);
+// Double-float basis update of the same form (steps 7, 11, 13, 16; out = a src - V coef, with
+// column p-1 normalised in place first when norm_last, a = st->inv_gamma then).
+cudaError_t launch_update_df(const Workspace &w, int p, const double *coef, double alpha, const double *src,
+                             double *out, bool norm_last, cudaStream_t s);
 // Partial sums of squares of up to three vectors (part[blk*nvec + q]).
 cudaError_t launch_norms(const Workspace &w, const double *a, const double *b,
                          const double *c, int *blocks_out, cudaStream_t s);

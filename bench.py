@@ -211,32 +211,32 @@ def run_reference(args):
     if rank != 0:
         return
     if args.workload == "batched":
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
         import oracle
         oracle.build()
         out = gen.banded_batch(count=args.batch_count, seed=SEED)
-        stride = max(1, args.batch_count // 16)
+        cores = os.cpu_count() or 1
+        stride = max(1, args.batch_count // (4 * cores))
         sample = [(out[i][0], out[i][1], gen.norm2_power(out[i][0], iters=100))
                   for i in range(0, args.batch_count, stride)]
-
-        def ostep():
-            for A, b, nA in sample:
-                oracle.gmres(A, b, m=BATCH_M, gs=args.gs, tol=BATCH_TOL, max_cycles=BATCH_MAX_RESTARTS,
-                             normA=nA)
-
-        for _ in range(args.warmup):
-            ostep()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            ostep()
-        dt = time.perf_counter() - t0
+        with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+            for _ in range(args.warmup):
+                list(ex.map(_oracle_batch_solve, sample))
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                list(ex.map(_oracle_batch_solve, sample))
+            dt = time.perf_counter() - t0
         value = args.steps * len(sample) / dt
         line = {"impl": "reference", "metric": BATCH_METRIC, "value": value, "unit": BATCH_UNIT,
                 "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": batch_config(args.gs, args.batch_count),
-                "cpu_baseline": {"value": value, "unit": BATCH_UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": f"{len(sample)} of the {args.batch_count} systems per step"},
+                "config": {**batch_config(args.gs, args.batch_count), "parallelism": f"replicas x{ws}"},
+                "cpu_baseline": {"value": value, "unit": BATCH_UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"{len(sample)} of the {args.batch_count} systems per step, "
+                                           f"one serial oracle per process on {cores} processes"},
                 "e2e": {"value": value, "unit": BATCH_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -706,20 +706,40 @@ def run_dense200(args, pkg, torch, local, dist, rank):
     return out
 
 
-def oracle_batch_rate(stride=128):
-    """Solves/s of the CPU oracle (one thread) on every stride-th system of the batch."""
+def _oracle_batch_solve(job):
+    """One batched system through the serial oracle (a worker of oracle_batch_rate)."""
     import oracle
+    A, b, nA = job
+    oracle.gmres(A, b, m=BATCH_M, gs=2, tol=BATCH_TOL, max_cycles=BATCH_MAX_RESTARTS, normA=nA)
+    return 1
+
+
+def oracle_batch_rate(stride=32):
+    """Solves/s of the CPU oracle on every stride-th system of the batch: serially on one
+    core, and on all host cores (the systems are independent: a spawned process pool, one
+    serial oracle per process)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
     out = gen.banded_batch(count=BATCH_COUNT, seed=SEED)
-    t = 0.0
-    k = 0
-    for i in range(0, BATCH_COUNT, stride):
-        A, b, _, _ = out[i]
-        nA = gen.norm2_power(A, iters=100)
+    jobs = [(out[i][0], out[i][1], gen.norm2_power(out[i][0], iters=100)) for i in range(0, BATCH_COUNT, stride)]
+    t0 = time.perf_counter()
+    for j in jobs[: max(1, len(jobs) // 4)]:
+        _oracle_batch_solve(j)
+    t1 = time.perf_counter() - t0
+    serial = max(1, len(jobs) // 4) / t1
+    cores = os.cpu_count() or 1
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_batch_solve, jobs[:cores]))  # start the workers
         t0 = time.perf_counter()
-        oracle.gmres(A, b, m=BATCH_M, gs=2, tol=BATCH_TOL, max_cycles=BATCH_MAX_RESTARTS, normA=nA)
-        t += time.perf_counter() - t0
-        k += 1
-    return k / t, k, t
+        done = sum(ex.map(_oracle_batch_solve, jobs))
+        tn = time.perf_counter() - t0
+    return {"value": done / tn, "unit": BATCH_UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(jobs)} of the {BATCH_COUNT} systems (every {stride}th) on {cores} processes, {tn:.1f} s",
+            "serial": {"value": serial, "unit": BATCH_UNIT, "cores": 1,
+                       "sample": f"{max(1, len(jobs) // 4)} of those systems, {t1:.1f} s"}}
 
 
 def main():
@@ -741,6 +761,8 @@ def main():
     ap.add_argument("--batch-launch", default="",
                     help="T:B = block threads and CTAs per SM for the batched kernel (default: tuned)")
     ap.add_argument("--no-one-at-a-time", action="store_true")
+    ap.add_argument("--probe", action="store_true",
+                    help="only measure the FP64 / FP32 FMA throughput (igs_probe_fma) with the clocks, one JSON line")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other-gs cycle, the solve to beta <= 1e-13 and the dense n = 200 lines")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision-form sub-measurement")
@@ -774,6 +796,23 @@ def main():
     if dist:
         dist.barrier()
     import paper_2205_07805_gb300 as pkg
+
+    if args.probe:
+        clocks = Clocks(local)
+        clocks.start()
+        reps = [pkg.probe_fma(local) for _ in range(5)]
+        clk = clocks.stop()
+        f64 = statistics.median(r["fp64_fma_per_s"] for r in reps)
+        f32 = statistics.median(r["fp32_fma_per_s"] for r in reps)
+        line = {"probe": "igs_probe_fma: every SM full of independent FMA chains, median of 5",
+                "fp64_tflops": 2 * f64 / 1e12, "fp32_tflops": 2 * f32 / 1e12,
+                "fp64_fma_per_clk_per_sm_at_max_clock": f64 / (torch.cuda.get_device_properties(local).multi_processor_count
+                                                               * 2070e6),
+                "fp64_unit_count_peak_tflops": FP64_PEAK_TFLOPS, "fp64_frac_of_unit_count": 2 * f64 / 1e12 / FP64_PEAK_TFLOPS,
+                "fp32_over_fp64": f32 / f64, "clocks": clk}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
 
     if args.workload == "served":
         clocks = Clocks(local)
@@ -821,11 +860,7 @@ def main():
                 **{k: bl[k] for k in ("arnoldi_steps_per_s", "launch", "one_at_a_time",
                                       "speedup_vs_one_at_a_time") if k in bl}}
         if rank == 0 and not args.no_cpu_baseline:
-            import oracle
-            oracle.build()
-            rate, k, dt = oracle_batch_rate()
-            line["cpu_baseline"] = {"value": rate, "unit": BATCH_UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"{k} of the {BATCH_COUNT} systems (every 128th), {dt:.1f} s"}
+            line["cpu_baseline"] = oracle_batch_rate()
         if rank == 0:
             print(json.dumps(line), flush=True)
         if dist:

@@ -246,6 +246,13 @@ int64_t igs_launch_count(const igs_ctx *ctx);
 int igs_block_dots_static(const double *V, int64_t ldv, int p, int64_t n, const double *x0,
                           const double *x1, double *out, void *stream);
 
+/* Arithmetic-pipe probe (measurement support; the paper has no counterpart): the FP64 and
+ * FP32 fused multiply-add throughput of `device`, in FMAs per second, measured with every SM
+ * full of independent FMA chains (about 0.2 s of GPU time; allocates a few KB).  On GB300 the
+ * FP64 rate bounds this library's FP64 streaming kernels, so the benchmark reports it beside
+ * the unit-count FP64 peak.  Returns IGS_OK, IGS_EINVAL (NULL output) or IGS_ECUDA. */
+int igs_probe_fma(int device, double *fp64_fma_per_s, double *fp32_fma_per_s);
+
 /* Text of a status code, and of the last error met by ctx (never NULL). */
 const char *igs_status_string(int status);
 const char *igs_last_error(const igs_ctx *ctx);

@@ -26,7 +26,8 @@ KCLASS_NAMES = ["spmv", "dots", "update", "small", "cycle"]
 # Every function declared in include/igs.h.
 EXPORTED_SYMBOLS = ["igs_create", "igs_destroy", "igs_solve", "igs_arnoldi", "igs_spmv",
                     "igs_get_info", "igs_profile_enable", "igs_profile_get", "igs_launch_count",
-                    "igs_status_string", "igs_last_error", "igs_block_dots_static", "igs_arnoldi_ex"]
+                    "igs_status_string", "igs_last_error", "igs_block_dots_static", "igs_arnoldi_ex",
+                    "igs_probe_fma"]
 # Every function declared in include/igs_batch.h.
 EXPORTED_BATCH_SYMBOLS = ["igs_batch_create", "igs_batch_destroy", "igs_batch_solve",
                           "igs_batch_set_config", "igs_batch_tune", "igs_batch_get_info",
@@ -179,6 +180,8 @@ def load_library(path: str | None = None):
     lib.igs_last_error.restype = C.c_char_p
     lib.igs_block_dots_static.argtypes = [vp, i64, i32, i64, vp, vp, vp, vp]
     lib.igs_block_dots_static.restype = i32
+    lib.igs_probe_fma.argtypes = [i32, C.POINTER(dbl), C.POINTER(dbl)]
+    lib.igs_probe_fma.restype = i32
     lib.igs_batch_create.argtypes = [C.POINTER(vp), i32, vp, vp, vp, vp, C.POINTER(_BatchOpts)]
     lib.igs_batch_create.restype = i32
     lib.igs_batch_destroy.argtypes = [vp]
@@ -239,6 +242,16 @@ def _vec_arg(x, n: int, name: str):
     if a.shape != (n,):
         raise ValueError(f"{name}: need shape ({n},), got {a.shape}")
     return C.c_void_p(a.ctypes.data), False, a
+
+
+def probe_fma(device: int = 0) -> dict:
+    """FP64 and FP32 FMA throughput of the GPU (``igs_probe_fma``), in FMAs per second."""
+    lib = load_library()
+    f64, f32 = C.c_double(0.0), C.c_double(0.0)
+    rc = lib.igs_probe_fma(int(device), C.byref(f64), C.byref(f32))
+    if rc != OK:
+        raise IGSError(rc, "igs_probe_fma")
+    return {"fp64_fma_per_s": f64.value, "fp32_fma_per_s": f32.value}
 
 
 class Solver:

@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libigs.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["igs_kernels.cu", "igs_df.cu", "igs_api.cu", "igs_noalloc.cu", "igs_batch.cu",
-           "igs_fp32.cu", "igs_serve.cu"]
+           "igs_fp32.cu", "igs_serve.cu", "igs_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

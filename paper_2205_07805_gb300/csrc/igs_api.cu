@@ -790,6 +790,7 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
             }
             {
                 cudaError_t e = igs::configure_kernels(w);
+                if (e == cudaSuccess) e = igs::configure_df_kernels();
                 if (e != cudaSuccess) {
                     fail(ctx, IGS_ECUDA, "kernel configuration: %s", cudaGetErrorString(e));
                     return bail(IGS_ECUDA);

@@ -71,8 +71,22 @@ __device__ __forceinline__ void df_acc(float &S, float &s, float ah, float al, f
 // V[:,c] . X_q); what differs is that each warp streams ALL the group's columns over its
 // row sub-slice (so each X row is loaded and split once per block, not once per column)
 // and the products are accumulated in double-float.  Each lane handles two consecutive rows
-// per 64-row segment: one warp instruction reads 512 contiguous bytes of a column.
+// per 64-row segment: one copy instruction of a warp moves 512 contiguous bytes of a column.
+// The segments are double-buffered in shared memory by cp.async: while a warp computes on
+// segment g (about 370 instructions per lane), the copies of segment g+1 are in flight, so
+// the HBM latency is hidden without holding the next segment in registers.  Each lane
+// reads back only the 16-byte chunks it copied itself, so no barrier is needed.
 // =====================================================================================
+constexpr int kDfStreams = kDotsColsPerBlock + 2;           // up to 4 columns and 2 vectors
+constexpr int kDfStageDoubles = kDfStreams * 64;            // one 64-row segment of each stream
+constexpr size_t kDfDotsSmem = sizeof(double) * 2 * kDfStageDoubles * (kStreamThreads / 32);
+
+__device__ __forceinline__ void cp_async16(double *dst, const double *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
 template <int NQ>
 __global__ void __launch_bounds__(kStreamThreads, kDotsBlocksPerSM)
 k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t rows,
@@ -84,6 +98,7 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
     constexpr int W = kStreamThreads / 32;
     constexpr int CW = kDotsColsPerBlock;
     constexpr int kFold = 16;  // segments (32 elements per lane) between FP64 folds
+    extern __shared__ double dsm[];
     __shared__ double red[NQ][CW][W];
     const int rb = blockIdx.x, G = gridDim.y, cg = blockIdx.y;
     const int c_lo = (int)((int64_t)cg * p / G), c_hi = (int)((int64_t)(cg + 1) * p / G);
@@ -91,6 +106,8 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int64_t r_lo = (int64_t)rb * rows;
     const int64_t r_hi = r_lo + rows < n4 ? r_lo + rows : n4;
+    double *stage0 = dsm + (size_t)wid * 2 * kDfStageDoubles + 2 * lane;  // this lane's slots
+    const double *vbase = V + (int64_t)c_lo * ld;
     double acc[CW][NQ];
     float S[CW][NQ], s[CW][NQ];
 #pragma unroll
@@ -101,58 +118,68 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
             S[c][q] = 0.f;
             s[c][q] = 0.f;
         }
-    const double *vc[CW];
+    const int64_t nseg = r_lo < r_hi ? (r_hi - r_lo + 63) >> 6 : 0;
+    const int64_t g0 = nseg * wid / W, g1 = nseg * (wid + 1) / W;
+    // copy segment g into stage buffer b: streams 0..NQ-1 = X, NQ.. = the columns
+    auto issue = [&](int64_t g, int b) {
+        const int64_t i = r_lo + (g << 6) + 2 * lane;
+        if (i < r_hi) {
+            double *dst = stage0 + b * kDfStageDoubles;
+            cp_async16(dst, x0 + i);
+            if (NQ == 2) cp_async16(dst + 64, x1 + i);
 #pragma unroll
-    for (int c = 0; c < CW; ++c) vc[c] = V + (int64_t)(c_lo + (c < cw ? c : 0)) * ld;
-    if (r_lo < r_hi) {
-        const int64_t nseg = (r_hi - r_lo + 63) >> 6;
-        const int64_t g0 = nseg * wid / W, g1 = nseg * (wid + 1) / W;
-        int since = 0;
-        for (int64_t g = g0; g < g1; ++g) {
-            const int64_t i = r_lo + (g << 6) + 2 * lane;
-            if (i < r_hi) {
-                float xh[NQ][2], xl[NQ][2];
-                {
-                    const double2 xa = *reinterpret_cast<const double2 *>(x0 + i);
-                    df_split(xa.x, xh[0][0], xl[0][0]);
-                    df_split(xa.y, xh[0][1], xl[0][1]);
-                    if (NQ == 2) {
-                        const double2 xb = *reinterpret_cast<const double2 *>(x1 + i);
-                        df_split(xb.x, xh[NQ - 1][0], xl[NQ - 1][0]);
-                        df_split(xb.y, xh[NQ - 1][1], xl[NQ - 1][1]);
-                    }
-                }
-                double2 v[CW];
+            for (int c = 0; c < CW; ++c)
+                if (c < cw) cp_async16(dst + 64 * (NQ + c), vbase + (int64_t)c * ld + i);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (g0 < g1) issue(g0, 0);
+    int since = 0;
+    for (int64_t g = g0; g < g1; ++g) {
+        const int b = (int)((g - g0) & 1);
+        if (g + 1 < g1)
+            issue(g + 1, b ^ 1);
+        else
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        const int64_t i = r_lo + (g << 6) + 2 * lane;
+        if (i < r_hi) {
+            const double *src = stage0 + b * kDfStageDoubles;
+            float xh[NQ][2], xl[NQ][2];
 #pragma unroll
-                for (int c = 0; c < CW; ++c)
-                    if (c < cw) v[c] = *reinterpret_cast<const double2 *>(vc[c] + i);
-#pragma unroll
-                for (int c = 0; c < CW; ++c) {
-                    if (c < cw) {
-                        float h0, l0, h1, l1;
-                        df_split(v[c].x, h0, l0);
-                        df_split(v[c].y, h1, l1);
-#pragma unroll
-                        for (int q = 0; q < NQ; ++q) {
-                            df_acc(S[c][q], s[c][q], h0, l0, xh[q][0], xl[q][0]);
-                            df_acc(S[c][q], s[c][q], h1, l1, xh[q][1], xl[q][1]);
-                        }
-                    }
-                }
+            for (int q = 0; q < NQ; ++q) {
+                const double2 xv = *reinterpret_cast<const double2 *>(src + 64 * q);
+                df_split(xv.x, xh[q][0], xl[q][0]);
+                df_split(xv.y, xh[q][1], xl[q][1]);
             }
-            if (++since == kFold) {
-                since = 0;
 #pragma unroll
-                for (int c = 0; c < CW; ++c)
+            for (int c = 0; c < CW; ++c) {
+                if (c < cw) {
+                    const double2 v = *reinterpret_cast<const double2 *>(src + 64 * (NQ + c));
+                    float h0, l0, h1, l1;
+                    df_split(v.x, h0, l0);
+                    df_split(v.y, h1, l1);
 #pragma unroll
                     for (int q = 0; q < NQ; ++q) {
-                        acc[c][q] += (double)S[c][q] + (double)s[c][q];
-                        S[c][q] = 0.f;
-                        s[c][q] = 0.f;
+                        df_acc(S[c][q], s[c][q], h0, l0, xh[q][0], xl[q][0]);
+                        df_acc(S[c][q], s[c][q], h1, l1, xh[q][1], xl[q][1]);
                     }
+                }
             }
         }
+        if (++since == kFold) {
+            since = 0;
+#pragma unroll
+            for (int c = 0; c < CW; ++c)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    acc[c][q] += (double)S[c][q] + (double)s[c][q];
+                    S[c][q] = 0.f;
+                    s[c][q] = 0.f;
+                }
+        }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     // lane sums (FP64), then a fixed-order warp tree and the W warp sums in order
 #pragma unroll
     for (int c = 0; c < CW; ++c)
@@ -288,12 +315,21 @@ cudaError_t launch_dots_df(const Workspace &w, int p, const double *x0, const do
     const int64_t n4 = (w.n + 3) & ~int64_t(3);
     dim3 grid(pl.rblocks, pl.groups);
     if (x1)
-        launch_k(false, k_dots_df<2>, grid, dim3(kStreamThreads), 0, s, w.V, w.ld, p, n4, pl.rows, x0, x1, w.part,
-                 (const DevState *)w.st, check_halt ? 1 : 0);
+        launch_k(false, k_dots_df<2>, grid, dim3(kStreamThreads), kDfDotsSmem, s, w.V, w.ld, p, n4, pl.rows, x0, x1,
+                 w.part, (const DevState *)w.st, check_halt ? 1 : 0);
     else
-        launch_k(false, k_dots_df<1>, grid, dim3(kStreamThreads), 0, s, w.V, w.ld, p, n4, pl.rows, x0,
+        launch_k(false, k_dots_df<1>, grid, dim3(kStreamThreads), kDfDotsSmem, s, w.V, w.ld, p, n4, pl.rows, x0,
                  (const double *)nullptr, w.part, (const DevState *)w.st, check_halt ? 1 : 0);
     return cudaGetLastError();
+}
+
+cudaError_t configure_df_kernels()
+{
+    // 48 KiB of stage buffers per block (3 blocks per SM): above the default dynamic limit
+    cudaError_t e = cudaFuncSetAttribute(k_dots_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDfDotsSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dots_df<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDfDotsSmem);
+    return e;
 }
 
 }  // namespace igs

@@ -144,6 +144,8 @@ constexpr int64_t kDfMinRows = 16384;
 bool dots_df_applies(const Workspace &w);
 cudaError_t launch_dots_df(const Workspace &w, int p, const double *x0, const double *x1,
                            bool check_halt, cudaStream_t s, DotsPlan *plan_out);
+// Dynamic shared-memory limits of the double-float kernels (once per context, before capture).
+cudaError_t configure_df_kernels();
 // Double-float basis update of the same form (steps 7, 11, 13, 16; out = a src - V coef, with
 // column p-1 normalised in place first when norm_last, a = st->inv_gamma then).
 cudaError_t launch_update_df(const Workspace &w, int p, const double *coef, double alpha, const double *src,

@@ -71,9 +71,9 @@ def peaks_hbm():
         return 6800.0
 
 
-def main_config(gs, method, ws):
+def main_config(gs, method, ws, precision="fp64"):
     """The main line's `config` (the same dict in both bench arms)."""
-    return {**workload_config(gs), "method": method, "parallelism": f"replicas x{ws}"}
+    return {**workload_config(gs), "method": method, "precision": precision, "parallelism": f"replicas x{ws}"}
 
 
 BATCH_COUNT, BATCH_M, BATCH_TOL, BATCH_MAX_RESTARTS = 4096, 50, 1e-12, 20
@@ -268,7 +268,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": main_config(args.gs, args.method, ws),
+            "data": "synthetic", "config": main_config(args.gs, args.method, ws, args.precision),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -751,6 +751,8 @@ def main():
     ap.add_argument("--method", default="igs", choices=["igs", "one_reduce"],
                     help="the main line's Arnoldi process: Alg. 4.1 (igs) or Alg. 4.2 (one_reduce)")
     ap.add_argument("--impl", default="igs")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_df"],
+                    help="the main line's arithmetic: FP64, or FP64 data with double-float reductions and updates")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="cd2d", choices=["cd2d", "batched", "precision", "served"])
     ap.add_argument("--prec-grid", type=int, default=PREC_N,
@@ -876,7 +878,7 @@ def main():
 
     def step():
         return solver.solve(b_dev, m=M, gs=args.gs, tol=0.0, max_restarts=1, x_out=x_dev, hist_cap=0,
-                            method=args.method)
+                            method=args.method, precision=args.precision)
 
     for _ in range(args.warmup):
         out = step()
@@ -905,13 +907,14 @@ def main():
     # ---- end to end through the C interface with host buffers ----
     b_host = np.ascontiguousarray(b)
     x_host = np.empty_like(b_host)
-    solver.solve(b_host, m=M, gs=args.gs, tol=0.0, max_restarts=1, x_out=x_host, hist_cap=0, method=args.method)
+    solver.solve(b_host, m=M, gs=args.gs, tol=0.0, max_restarts=1, x_out=x_host, hist_cap=0, method=args.method,
+                 precision=args.precision)
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         solver.solve(b_host, m=M, gs=args.gs, tol=0.0, max_restarts=1, x_out=x_host, hist_cap=0,
-                     method=args.method)
+                     method=args.method, precision=args.precision)
     e2e_s = time.perf_counter() - t0
     ms, e2e_s, steps_total = reduce_replicas(ms, e2e_s, args.steps * M, dist, "cuda")
     value = steps_total / (ms / 1e3)
@@ -962,7 +965,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": main_config(args.gs, args.method, ws),
+            "config": main_config(args.gs, args.method, ws, args.precision),
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk}
     if rank == 0 and not args.no_cpu_baseline:

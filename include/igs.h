@@ -72,9 +72,8 @@ typedef struct {
     int stream_alloc;   /* nonzero: the context's device memory comes from the device's
                            stream-ordered pool (cudaMallocAsync on the context's stream) and
                            igs_destroy returns it with cudaFreeAsync, so that neither call
-                           waits for work on other streams (cudaFree would).  Needs a given
-                           A_norm2 > 0 for the guarantee (the estimate's scratch is not
-                           pooled)                                                          */
+                           waits for work on other streams (cudaFree would); the norm
+                           estimate's scratch comes from the same pool                      */
 } igs_create_opts;
 
 /* Arithmetic of igs_solve's Arnoldi cycles. */

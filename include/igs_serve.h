@@ -76,7 +76,12 @@ typedef struct {
     const double *vals;
     const double *b;        /* host, n entries                                               */
     const double *x0;       /* host, n entries, nullable (zero start)                        */
-    double A_norm2;         /* ||A||_2 for beta; <= 0: the bound sqrt(||A||_1 ||A||_inf)      */
+    double A_norm2;         /* ||A||_2 for beta (eq. "nrbe"); <= 0: estimated on the GPU by the
+                               library's power iteration on A^T A (as igs_create does), on a
+                               worker thread of the server, before the request is admitted
+                               (a failed estimate falls back to the bound
+                               sqrt(||A||_1 ||A||_inf) >= ||A||_2); the completion record
+                               carries the value used                                        */
     int restart_m;          /* 1..max_restart_m                                               */
     int gs_iters;           /* 1 or 2                                                         */
     double tol_beta;        /* stop when beta(x) <= tol_beta                                  */

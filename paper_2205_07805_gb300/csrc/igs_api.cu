@@ -811,19 +811,33 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
                         tci[(size_t)pos[(size_t)c]] = (int)i;
                         tva[(size_t)pos[(size_t)c]++] = vals[q];
                     }
+                // scratch from the stream-ordered pool when the context's memory is (so that
+                // neither allocating nor freeing it waits for other streams' work)
+                const bool pooled = ctx->stream_alloc;
+                auto salloc = [&](void **q, size_t bytes) {
+                    return pooled ? cudaMallocAsync(q, bytes, ctx->stream) : cudaMalloc(q, bytes);
+                };
+                auto sfree = [&](void *q) {
+                    if (q) pooled ? cudaFreeAsync(q, ctx->stream) : cudaFree(q);
+                };
+                auto up = [&](void *dst, const void *src, size_t bytes) {
+                    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+                };
                 int *d_trp = nullptr, *d_tci = nullptr;
                 double *d_tva = nullptr;
-                cudaError_t e = cudaMalloc(&d_trp, sizeof(int) * (n + 1));
-                if (e == cudaSuccess) e = cudaMalloc(&d_tci, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
-                if (e == cudaSuccess) e = cudaMalloc(&d_tva, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
-                if (e == cudaSuccess) e = cudaMemcpy(d_trp, trp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
-                if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(d_tci, tci.data(), sizeof(int) * (size_t)nnz, cudaMemcpyHostToDevice);
-                if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(d_tva, tva.data(), sizeof(double) * (size_t)nnz, cudaMemcpyHostToDevice);
+                cudaError_t e = salloc((void **)&d_trp, sizeof(int) * (n + 1));
+                if (e == cudaSuccess) e = salloc((void **)&d_tci, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+                if (e == cudaSuccess) e = salloc((void **)&d_tva, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+                if (e == cudaSuccess) e = up(d_trp, trp.data(), sizeof(int) * (n + 1));
+                if (e == cudaSuccess && nnz > 0) e = up(d_tci, tci.data(), sizeof(int) * (size_t)nnz);
+                if (e == cudaSuccess && nnz > 0) e = up(d_tva, tva.data(), sizeof(double) * (size_t)nnz);
                 double est = 0.0;
+                // (synchronises the stream before returning, so the host copies above are done)
                 if (e == cudaSuccess) e = igs::estimate_norm2(w, d_trp, d_tci, d_tva, o.norm2_iters, &est, ctx->stream);
-                cudaFree(d_trp);
-                cudaFree(d_tci);
-                cudaFree(d_tva);
+                if (e != cudaSuccess) cudaStreamSynchronize(ctx->stream);
+                sfree(d_trp);
+                sfree(d_tci);
+                sfree(d_tva);
                 if (e != cudaSuccess) {
                     fail(ctx, IGS_ECUDA, "norm estimate: %s", cudaGetErrorString(e));
                     return bail(IGS_ECUDA);

@@ -155,6 +155,18 @@ struct GraphJob {
     int cycles = 0;
 };
 
+// A gang request whose ||A||_2 the server estimates (no A_norm2 given): a copy of its CSR
+// matrix for the norm worker, and the estimate it hands back.
+struct NormJob {
+    int64_t id = 0, n = 0, nnz = 0;
+    int device = 0;
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> colind;
+    std::vector<double> vals;
+    double normA = 0.0;
+    int status = IGS_OK;
+};
+
 struct Request {
     int64_t id = 0;
     bool graph = false;  // runs on the graph lane (whole-GPU kernels, one request at a time)
@@ -181,6 +193,7 @@ struct Request {
     int status = IGS_OK;
     double t_submit = 0, t_admit = 0, t_done = 0;
     bool done = false, polled = false;
+    bool norm_pending = false;  // waiting for the norm worker's ||A||_2 estimate
 };
 
 }  // namespace serve
@@ -211,6 +224,12 @@ struct igs_server {
         int64_t busy = -1;                                    // request on the lane, -1: idle
         std::unique_ptr<igs::serve::GraphJob> in, out;        // hand-over / finished (under graph_mu)
     };
+    // norm worker: ||A||_2 of gang requests that come without one, estimated on the GPU by
+    // the library's power iteration (igs_create with A_norm2 = 0) on its own stream
+    std::thread norm_thread;
+    cudaStream_t norm_stream = nullptr;
+    std::deque<std::unique_ptr<igs::serve::NormJob>> norm_in, norm_out;  // under graph_mu
+    std::condition_variable norm_cv;
     int64_t graph_min_n = 0;
     std::deque<int64_t> graph_queue;       // waiting for a lane (FIFO)
     std::vector<Lane> lanes;
@@ -349,7 +368,10 @@ void run_graph_job(igs_server *s, cudaStream_t stream, igs::serve::GraphJob &j)
         return;
     }
     igs_info info{};
-    if (igs_get_info(ctx, &info) == IGS_OK) j.device_bytes = info.device_bytes;
+    if (igs_get_info(ctx, &info) == IGS_OK) {
+        j.device_bytes = info.device_bytes;
+        j.normA = info.A_norm2;  // the given norm, or the context's GPU estimate
+    }
     igs_solve_opts so{};
     so.restart_m = q.restart_m;
     so.gs_iters = q.gs_iters;
@@ -367,6 +389,47 @@ void run_graph_job(igs_server *s, cudaStream_t stream, igs::serve::GraphJob &j)
     j.steps = res.steps;
     j.cycles = res.cycles;
     igs_destroy(ctx);
+}
+
+// ||A||_2 of one matrix by the library's estimator: a context of the smallest restart length
+// (its power iteration on A^T A runs at create, on the given stream, with pooled memory).
+void estimate_norm(cudaStream_t stream, igs::serve::NormJob &j)
+{
+    igs_create_opts co{};
+    co.stream = stream;
+    co.device = j.device;
+    co.max_restart_m = 1;
+    co.A_norm2 = 0.0;
+    co.stream_alloc = 1;
+    igs_ctx *ctx = nullptr;
+    j.status = igs_create(&ctx, j.n, j.nnz, j.rowptr.data(), j.colind.data(), j.vals.data(), &co);
+    if (j.status != IGS_OK) return;
+    igs_info info{};
+    j.status = igs_get_info(ctx, &info);
+    j.normA = info.A_norm2;
+    igs_destroy(ctx);
+    std::vector<int64_t>().swap(j.rowptr);
+    std::vector<int32_t>().swap(j.colind);
+    std::vector<double>().swap(j.vals);
+}
+
+// The norm worker thread: estimates ||A||_2 for queued gang requests, in arrival order.
+void norm_worker(igs_server *s)
+{
+    cudaSetDevice(s->device);
+    for (;;) {
+        std::unique_ptr<igs::serve::NormJob> job;
+        {
+            std::unique_lock<std::mutex> lk(s->graph_mu);
+            s->norm_cv.wait(lk, [&] { return s->graph_stop || !s->norm_in.empty(); });
+            if (s->graph_stop) return;
+            job = std::move(s->norm_in.front());
+            s->norm_in.pop_front();
+        }
+        estimate_norm(s->norm_stream, *job);
+        std::lock_guard<std::mutex> lk(s->graph_mu);
+        s->norm_out.push_back(std::move(job));
+    }
 }
 
 // A graph lane's worker thread: takes the job handed to its lane, solves it on the lane's
@@ -392,6 +455,19 @@ void graph_worker(igs_server *s, int lane)
 // Finished requests: collect results, release memory.
 int collect(igs_server *s)
 {
+    for (;;) {
+        std::unique_ptr<igs::serve::NormJob> nj;
+        {
+            std::lock_guard<std::mutex> lk(s->graph_mu);
+            if (s->norm_out.empty()) break;
+            nj = std::move(s->norm_out.front());
+            s->norm_out.pop_front();
+        }
+        Request &r = s->reqs[nj->id];
+        r.norm_pending = false;
+        if (nj->status == IGS_OK && nj->normA > 0.0 && std::isfinite(nj->normA)) r.normA = nj->normA;
+        // (an estimate that failed leaves the bound sqrt(||A||_1 ||A||_inf) >= ||A||_2 in place)
+    }
     for (auto &L : s->lanes) {
         std::unique_ptr<igs::serve::GraphJob> fin;
         {
@@ -406,6 +482,7 @@ int collect(igs_server *s)
         r.res.steps = fin->steps;
         r.res.cycles = fin->cycles;
         r.bytes = fin->device_bytes;
+        if (fin->normA > 0.0) r.normA = fin->normA;
         r.x_host = std::move(fin->x);
         r.t_done = now_s(s);
         r.done = true;
@@ -474,6 +551,7 @@ int admit(igs_server *s)
             }
         if (k < 0) return IGS_OK;
         Request &r = s->reqs[s->queue.front()];
+        if (r.norm_pending) return IGS_OK;  // admitted in arrival order, once its norm is known
         if (s->running_ctas + r.G > s->cta_budget) return IGS_OK;
         int64_t off = 0;
         if (!s->arena.alloc(r.bytes, &off)) return IGS_OK;
@@ -574,6 +652,12 @@ int igs_server_create(igs_server **out, const igs_server_opts *opts)
                 if (cudaStreamCreateWithFlags(&s->streams[(size_t)k], cudaStreamNonBlocking) != cudaSuccess ||
                     cudaEventCreateWithFlags(&s->events[(size_t)k], cudaEventDisableTiming) != cudaSuccess)
                     return bail(IGS_ECUDA);
+            if (cudaStreamCreateWithFlags(&s->norm_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(IGS_ECUDA);
+            try {
+                s->norm_thread = std::thread(norm_worker, s);
+            } catch (...) {
+                return bail(IGS_ENOMEM);
+            }
             if (s->graph_min_n > 0) {
                 s->lanes = std::vector<igs_server::Lane>((size_t)lanes);
                 for (int l = 0; l < lanes; ++l) {
@@ -605,9 +689,15 @@ void igs_server_destroy(igs_server *s)
         for (auto &L : s->lanes) L.in.reset();
     }
     s->graph_cv.notify_all();
+    s->norm_cv.notify_all();
     for (auto &L : s->lanes)
         if (L.thread.joinable()) L.thread.join();  // a running graph-lane solve ends first
+    if (s->norm_thread.joinable()) s->norm_thread.join();
     cudaSetDevice(s->device);
+    if (s->norm_stream) {
+        cudaStreamSynchronize(s->norm_stream);
+        cudaStreamDestroy(s->norm_stream);
+    }
     for (auto &L : s->lanes)
         if (L.stream) {
             cudaStreamSynchronize(L.stream);
@@ -665,10 +755,11 @@ int igs_server_submit(igs_server *s, const igs_request *q, int64_t *id_out)
             r.ldv = (int)((n + 3) / 4 * 4);
             r.f32 = q->precision == IGS_PREC_FP32_IR;
             r.has_x0 = q->x0 != nullptr;
-            if (q->A_norm2 > 0.0) {
+            const bool estimate = !(q->A_norm2 > 0.0);
+            if (!estimate) {
                 r.normA = q->A_norm2;
             } else {
-                // ||A||_2 <= sqrt(||A||_1 ||A||_inf)
+                // placeholder until the GPU estimate arrives: ||A||_2 <= sqrt(||A||_1 ||A||_inf)
                 const double n1 = *std::max_element(colabs.begin(), colabs.end());
                 const double ninf = *std::max_element(rowabs.begin(), rowabs.end());
                 r.normA = std::sqrt(n1 * ninf);
@@ -682,7 +773,7 @@ int igs_server_submit(igs_server *s, const igs_request *q, int64_t *id_out)
                 job->opt.vals = nullptr;
                 job->opt.b = nullptr;
                 job->opt.x0 = nullptr;
-                job->normA = r.normA;
+                job->normA = estimate ? 0.0 : r.normA;  // 0: the lane's igs_create estimates it
                 job->rowptr.assign(q->rowptr, q->rowptr + n + 1);
                 job->colind.assign(q->colind, q->colind + nnz);
                 job->vals.assign(q->vals, q->vals + nnz);
@@ -736,6 +827,22 @@ int igs_server_submit(igs_server *s, const igs_request *q, int64_t *id_out)
             if (r.has_x0) r.x0.assign(q->x0, q->x0 + n);
             r.bytes = plan_request(r, 2 * (r.opt.restart_m + 1) + 2);
             if (r.bytes > s->arena.size()) return sfail(s, IGS_EINVAL, "request larger than the arena");
+            if (estimate) {
+                auto nj = std::make_unique<igs::serve::NormJob>();
+                nj->id = r.id;
+                nj->n = n;
+                nj->nnz = nnz;
+                nj->device = s->device;
+                nj->rowptr.assign(q->rowptr, q->rowptr + n + 1);
+                nj->colind.assign(q->colind, q->colind + nnz);
+                nj->vals.assign(q->vals, q->vals + nnz);
+                r.norm_pending = true;
+                {
+                    std::lock_guard<std::mutex> lk(s->graph_mu);
+                    s->norm_in.push_back(std::move(nj));
+                }
+                s->norm_cv.notify_one();
+            }
             r.t_submit = now_s(s);
             const int64_t id = r.id;
             s->reqs.emplace(id, std::move(r));

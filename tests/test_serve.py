@@ -168,6 +168,31 @@ def test_graph_lane_requests_match_oracle_and_mix(pkg, lanes):
 
 
 @pytest.mark.gpu
+def test_server_estimates_norm_when_not_given(pkg):
+    """A request without ||A||_2 gets the library's GPU power-iteration estimate (gang path:
+    the server's norm worker; graph lane: the lane's igs_create), so beta is eq. "nrbe" with
+    ||A||_2 estimated from below (within 1% of the SVD value here), not the larger bound
+    sqrt(||A||_1 ||A||_inf); the completion record carries it and the oracle's beta of the
+    returned x with that norm meets the tolerance."""
+    small = [gen.cd2d(side, pe, seed=70 + k)[:2] for k, (side, pe) in enumerate([(30, 10.0), (40, 80.0)])]
+    big = gen.cd2d(52, 40.0, seed=75)[:2]
+    with pkg.Server(max_restart_m=40, arena_bytes=1 << 30, slots=2, rows_per_cta=512, graph_min_n=2500) as sv:
+        ids = [sv.submit(A, b, m=40, gs=2, tol=1e-12, max_restarts=200) for A, b in small + [big]]
+        done = {c["id"]: c for c in sv.run_all()}
+        xs = {rid: sv.take(rid) for rid in ids}
+    for rid, (A, b) in zip(ids, small + [big]):
+        c = done[rid]
+        D = gen.csr_to_dense(A)
+        s2 = float(np.linalg.norm(D, 2))
+        bound = float(np.sqrt(np.abs(D).sum(0).max() * np.abs(D).sum(1).max()))
+        assert 0.99 * s2 <= c["A_norm2"] <= s2 * (1 + 1e-12), (c["A_norm2"], s2)
+        assert c["A_norm2"] < bound
+        assert c["status"] == 0 and c["beta"] <= 1e-12
+        assert oracle.backward_error(A, b, xs[rid], c["A_norm2"]) <= 1e-12
+    assert done[ids[-1]]["path"] == 1 and all(done[r]["path"] == 0 for r in ids[:-1])
+
+
+@pytest.mark.gpu
 def test_gang_wait_runs_out_without_a_fault(pkg):
     """The gangs' bounded waits: with the arrival counter started where no arrival completes
     the barrier (a flag nothing sets), every CTA's wait gives up, the gang's abort flag is

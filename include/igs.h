@@ -91,7 +91,7 @@ enum {
                               4.1's basis updates (steps 13 and 16, out = a src - V c, error
                               <= ~2^-45 sum |V c| per row) are evaluated with double-float
                               arithmetic on the FP32 pipes: each
-                              FP64 operand split into two FP32 parts (exact to 2^-48 for
+                              FP64 operand split into two FP32 parts (exact to 2^-47 for
                               2^-100 <= |a| < 2^127), exact products of the high parts, cross
                               terms in FP32 (<= ~2^-45 relative per product), TwoSum
                               accumulation folded into FP64 every 32 terms, FP64 lane sums.

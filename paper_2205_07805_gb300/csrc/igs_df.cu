@@ -6,11 +6,11 @@
 // multi-dot [V, w]^T [w, z] (2 FMAs per 8-byte basis element) runs at about a third of
 // HBM bandwidth.  The FP32 pipes are 64 times faster.  Here every FP64 operand a is split
 // without any FP64 instruction into a = hi + lo (+ r), hi = a's sign, exponent and top 24
-// significant bits, lo = the remaining 29 bits rounded to FP32 (|r| <= 2^-48 |a|); the
+// significant bits, lo = the remaining 29 bits rounded to 23 (|r| <= 2^-47 |a|); the
 // product of two split numbers is formed as the exact product hi*hi' = p + e (FMA) plus the
 // cross terms hi*lo' + lo*hi' in FP32 (per-product error <= ~2^-45 |a a'|, dropped lo*lo'
 // included), and the products are summed per lane with TwoSum (Knuth) into a double-float
-// accumulator that is folded into an FP64 sum every 32 elements.  The lanes' FP64 sums
+// accumulator that is folded into an FP64 sum every 128 elements.  The lanes' FP64 sums
 // are then added in a fixed order, exactly as in the FP64 kernel, into the same per-block
 // partial-sum layout, so the single-block steps that follow are unchanged.
 //
@@ -18,7 +18,7 @@
 // FP64 product), but these errors are independent across the n terms of a dot product, so
 // for vectors spread over n >= 2^14 rows their contribution (~2^-46 ||a|| ||a'|| / sqrt(n))
 // is below the FP64 accumulation error the FP64 kernel itself makes; the library uses these
-// kernels only from that size on.  Range: the split is exact to 2^-48 for
+// kernels only from that size on.  Range: the split is exact to 2^-47 for
 // 2^-100 <= |a| < 2^127; smaller operands lose low-order bits (lo becomes an FP32
 // subnormal) down to FP32 precision at 2^-126, below which they count as 0; |a| >= 2^127
 // makes the sum non-finite (the solve then stops with IGS_ENUMERIC).
@@ -30,8 +30,10 @@ namespace {
 
 __device__ __forceinline__ bool df_halted(const DevState *st) { return st->halt != 0; }
 
-// a = hi + lo + r, |r| <= 2^-48 |a| for 2^-100 <= |a| < 2^127 (integer operations, one
-// integer-to-float conversion and two power-of-two scalings, exact unless lo is subnormal).
+// a = hi + lo + r, |r| <= 2^-47 |a| for 2^-100 <= |a| < 2^127 (integer and FP32 operations
+// only, none on the narrow FP64 pipe: the remaining 29 bits are rounded to 23 and turned
+// into a float exactly by placing them in the mantissa of 2^23 and subtracting 2^23; two
+// power-of-two scalings follow, exact unless lo is subnormal).
 __device__ __forceinline__ void df_split(double a, float &hi, float &lo)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(a);
@@ -44,9 +46,12 @@ __device__ __forceinline__ void df_split(double a, float &hi, float &lo)
     hb = ahw < (897u << 20) ? sign : hb;                                // |a| < 2^-126: 0
     hb = ahw >= (1150u << 20) ? (sign | 0x7f800000u) : hb;             // |a| >= 2^127: inf
     hi = __uint_as_float(hb);
-    // the remaining 29 fraction bits times 2^(e - 1075) = rem * 2^-52 * (+-2^(e - 1023))
+    // the remaining 29 fraction bits times 2^(e - 1075) = rem * 2^-52 * (+-2^(e - 1023)),
+    // with rem rounded to a multiple of 64: ((rem + 32) >> 6) * 2^-46 * (+-2^(e - 1023))
     const float scale = __uint_as_float(hb & 0xff800000u);
-    lo = __fmul_rn(__fmul_rn(__uint2float_rn(lw & 0x1fffffffu), 0x1p-52f), scale);
+    const unsigned r23 = ((lw & 0x1fffffffu) + 32u) >> 6;  // <= 2^23
+    const float fr = __fsub_rn(__uint_as_float(0x4B000000u | r23), 8388608.0f);
+    lo = __fmul_rn(__fmul_rn(fr, 0x1p-46f), scale);
 }
 
 // (S, s) += (ah + al) * (xh + xl): exact product of the high parts by FMA, cross terms in
@@ -97,7 +102,7 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
     if (check_halt && df_halted(st)) return;
     constexpr int W = kStreamThreads / 32;
     constexpr int CW = kDotsColsPerBlock;
-    constexpr int kFold = 16;  // segments (32 elements per lane) between FP64 folds
+    constexpr int kFold = 64;  // segments (128 elements per lane) between FP64 folds
     extern __shared__ double dsm[];
     __shared__ double red[NQ][CW][W];
     const int rb = blockIdx.x, G = gridDim.y, cg = blockIdx.y;

@@ -10,9 +10,10 @@
 // product of two split numbers is formed as the exact product hi*hi' = p + e (FMA) plus the
 // cross terms hi*lo' + lo*hi' in FP32 (per-product error <= ~2^-45 |a a'|, dropped lo*lo'
 // included), and the products are summed per lane with TwoSum (Knuth) into a double-float
-// accumulator that is folded into an FP64 sum every 128 elements.  The lanes' FP64 sums
-// are then added in a fixed order, exactly as in the FP64 kernel, into the same per-block
-// partial-sum layout, so the single-block steps that follow are unchanged.
+// accumulator, folded into a double-float total every 32 elements; the lanes' totals are
+// added in a fixed order (double-float) and each block's sum is converted to FP64 once, into
+// the FP64 kernel's per-block partial-sum layout, so the single-block steps that follow are
+// unchanged.
 //
 // Accuracy: each product carries a relative error of at most ~2^-45 (against 2^-53 for an
 // FP64 product), but these errors are independent across the n terms of a dot product, so
@@ -68,6 +69,32 @@ __device__ __forceinline__ void df_acc(float &S, float &s, float ah, float al, f
     s = __fadd_rn(s, __fadd_rn(err, c));
 }
 
+// The FP64 value of a finite FP32 number, assembled from its bits with integer operations
+// (no FP64-pipe conversion): sign, exponent rebiased by 1023 - 127 = 896, fraction shifted
+// up by 29.  Exact for normal numbers and zero; FP32 subnormals (|f| < 2^-126) give 0.
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned hw = e == 0u ? (u & 0x80000000u) : (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
+    const unsigned lw = e == 0u ? 0u : (u << 29);
+    return __hiloint2double((int)hw, (int)lw);
+}
+
+// (A, a) += (B, b) for double-float numbers (TwoSum of the high parts, the low parts added
+// to its error, renormalised by Fast2Sum): error ~2^-48 of the operands' magnitude.  FP32
+// only: an FP64 instruction holds a sub-partition's FP64 pipe for 64 clocks on GB300, so
+// the reductions below stay off that pipe until one conversion per block and column.
+__device__ __forceinline__ void df_add(float &A, float &a, float B, float b)
+{
+    const float t = __fadd_rn(A, B);
+    const float bp = __fsub_rn(t, A);
+    float e = __fadd_rn(__fsub_rn(A, __fsub_rn(t, bp)), __fsub_rn(B, bp));
+    e = __fadd_rn(e, __fadd_rn(a, b));
+    A = __fadd_rn(t, e);
+    a = __fsub_rn(e, __fsub_rn(A, t));
+}
+
 }  // namespace
 
 // =====================================================================================
@@ -80,7 +107,10 @@ __device__ __forceinline__ void df_acc(float &S, float &s, float ah, float al, f
 // The segments are double-buffered in shared memory by cp.async: while a warp computes on
 // segment g (about 370 instructions per lane), the copies of segment g+1 are in flight, so
 // the HBM latency is hidden without holding the next segment in registers.  Each lane
-// reads back only the 16-byte chunks it copied itself, so no barrier is needed.
+// reads back only the 16-byte chunks it copied itself, so no barrier is needed.  Lane sums
+// are folded into a double-float total every 32 elements, combined over the warp by a
+// double-float shuffle tree and over the block's warps in order, and converted to FP64 once
+// per block and column (FP64 instructions would serialise on the narrow FP64 pipe).
 // =====================================================================================
 constexpr int kDfStreams = kDotsColsPerBlock + 2;           // up to 4 columns and 2 vectors
 constexpr int kDfStageDoubles = kDfStreams * 64;            // one 64-row segment of each stream
@@ -102,9 +132,9 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
     if (check_halt && df_halted(st)) return;
     constexpr int W = kStreamThreads / 32;
     constexpr int CW = kDotsColsPerBlock;
-    constexpr int kFold = 64;  // segments (128 elements per lane) between FP64 folds
+    constexpr int kFold = 16;  // segments (32 elements per lane) between folds
     extern __shared__ double dsm[];
-    __shared__ double red[NQ][CW][W];
+    __shared__ float2 red[NQ][CW][W];
     const int rb = blockIdx.x, G = gridDim.y, cg = blockIdx.y;
     const int c_lo = (int)((int64_t)cg * p / G), c_hi = (int)((int64_t)(cg + 1) * p / G);
     const int cw = c_hi - c_lo;  // <= CW (the launcher's plan guarantees it)
@@ -113,13 +143,13 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
     const int64_t r_hi = r_lo + rows < n4 ? r_lo + rows : n4;
     double *stage0 = dsm + (size_t)wid * 2 * kDfStageDoubles + 2 * lane;  // this lane's slots
     const double *vbase = V + (int64_t)c_lo * ld;
-    double acc[CW][NQ];
-    float S[CW][NQ], s[CW][NQ];
+    float A[CW][NQ], a[CW][NQ], S[CW][NQ], s[CW][NQ];  // fold total and running chunk
 #pragma unroll
     for (int c = 0; c < CW; ++c)
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            acc[c][q] = 0.0;
+            A[c][q] = 0.f;
+            a[c][q] = 0.f;
             S[c][q] = 0.f;
             s[c][q] = 0.f;
         }
@@ -178,30 +208,36 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
             for (int c = 0; c < CW; ++c)
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
-                    acc[c][q] += (double)S[c][q] + (double)s[c][q];
+                    df_add(A[c][q], a[c][q], S[c][q], s[c][q]);
                     S[c][q] = 0.f;
                     s[c][q] = 0.f;
                 }
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    // lane sums (FP64), then a fixed-order warp tree and the W warp sums in order
+    // lane totals, a fixed-order double-float warp tree, the W warp sums in order, and one
+    // conversion to FP64 per (vector, column)
 #pragma unroll
     for (int c = 0; c < CW; ++c)
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            double a = acc[c][q] + ((double)S[c][q] + (double)s[c][q]);
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) red[q][c][wid] = a;
+            float h = A[c][q], l = a[c][q];
+            df_add(h, l, S[c][q], s[c][q]);
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_down_sync(0xffffffffu, h, o);
+                const float ol = __shfl_down_sync(0xffffffffu, l, o);
+                df_add(h, l, oh, ol);
+            }
+            if (lane == 0) red[q][c][wid] = make_float2(h, l);
         }
     __syncthreads();
     if (t < NQ * CW) {
         const int q = t / CW, c = t % CW;
         if (c < cw) {
-            double a = 0.0;
+            float h = 0.f, l = 0.f;
 #pragma unroll
-            for (int k = 0; k < W; ++k) a += red[q][c][k];
-            part[(int64_t)rb * NQ * p + (int64_t)q * p + c_lo + c] = a;
+            for (int k = 0; k < W; ++k) df_add(h, l, red[q][c][k].x, red[q][c][k].y);
+            part[(int64_t)rb * NQ * p + (int64_t)q * p + c_lo + c] = (double)h + (double)l;
         }
     }
 }
@@ -293,8 +329,8 @@ k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ 
         }
         const double2 sv = *reinterpret_cast<const double2 *>(src + i);
         double2 o;
-        o.x = fma(a, sv.x, -((double)S0 + (double)s0));
-        o.y = fma(a, sv.y, -((double)S1 + (double)s1));
+        o.x = fma(a, sv.x, -(f2d_bits(S0) + f2d_bits(s0)));
+        o.y = fma(a, sv.y, -(f2d_bits(S1) + f2d_bits(s1)));
         *reinterpret_cast<double2 *>(out + i) = o;
     }
 }

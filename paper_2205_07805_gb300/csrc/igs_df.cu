@@ -250,15 +250,26 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
 // first scaled in place by st->inv_gamma, which is also a).  Each row's sum over the
 // columns is a double-float accumulation of split products (the coefficients are split
 // once per block, in shared memory); a * src[i] and the final subtraction are FP64.
+// The columns stream through shared memory in chunks of kUpdChunk, kUpdStages chunks in
+// flight per thread (cp.async; each thread copies and reads back only its own 16-byte
+// slots), so the loads' latency is covered without holding them in registers.
 // Error of out[i]: <= ~2^-45 sum_c |V[i,c] coef[c]| (FP64: p 2^-53 of the same sum).
 // =====================================================================================
+constexpr int kUpdChunk = 4;
+constexpr int kUpdStages = 3;
+constexpr size_t kUpdStageBytes = (size_t)kUpdChunk * 16 * kStreamThreads;  // one chunk, all threads
+constexpr size_t kUpdSmemFixed = kUpdStages * kUpdStageBytes;              // + 8 p for the coefficients
+
 __global__ void __launch_bounds__(kStreamThreads, kUpdateBlocksPerSM)
 k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coef, double alpha,
             const double *src, double *out, int norm_last, DevState *st, int check_halt)
 {
     IGS_PDL_ENTER();
     if (check_halt && df_halted(st)) return;
-    extern __shared__ float scf[];  // coefficient splits: hi at [0, p), lo at [p, 2p)
+    extern __shared__ double usm[];
+    // stage buffers: [stage][column in chunk][thread] of double2; then the coefficient splits
+    double2 *stg = reinterpret_cast<double2 *>(usm);
+    float *scf = reinterpret_cast<float *>(usm + kUpdSmemFixed / sizeof(double));  // hi [0,p), lo [p,2p)
     const double a = norm_last ? st->inv_gamma : alpha;
     for (int c = threadIdx.x; c < p; c += blockDim.x) {
         float h, l;
@@ -268,53 +279,51 @@ k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ 
     }
     __syncthreads();
     const int pc = norm_last ? p - 1 : p;
+    const int nchunks = (pc + kUpdChunk - 1) / kUpdChunk;
     const int64_t npairs = (n + 1) >> 1;
     const int64_t ppb = (npairs + gridDim.x - 1) / gridDim.x;
     const int64_t pr_lo = (int64_t)blockIdx.x * ppb;
     const int64_t pr_hi = pr_lo + ppb < npairs ? pr_lo + ppb : npairs;
-    for (int64_t pr = pr_lo + threadIdx.x; pr < pr_hi; pr += blockDim.x) {
+    const int t = threadIdx.x;
+    for (int64_t pr = pr_lo + t; pr < pr_hi; pr += blockDim.x) {
         const int64_t i = 2 * pr;
         const double *vi = V + i;
-        float S0 = 0.f, s0 = 0.f, S1 = 0.f, s1 = 0.f;
-        int c = 0;
-        // four columns per step, the next four loaded while these are used
-        if (pc >= 4) {
-            double2 v[4];
+        auto issue = [&](int j) {
+            if (j < nchunks) {
+                double2 *dst = stg + (size_t)(j % kUpdStages) * kUpdChunk * kStreamThreads + t;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = *reinterpret_cast<const double2 *>(vi + (int64_t)q * ld);
-            for (; c + 7 < pc; c += 4) {
-                double2 nv[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) nv[q] = *reinterpret_cast<const double2 *>(vi + (int64_t)(c + 4 + q) * ld);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float h, l;
-                    df_split(v[q].x, h, l);
-                    df_acc(S0, s0, h, l, scf[c + q], scf[p + c + q]);
-                    df_split(v[q].y, h, l);
-                    df_acc(S1, s1, h, l, scf[c + q], scf[p + c + q]);
+                for (int q = 0; q < kUpdChunk; ++q) {
+                    const int c = j * kUpdChunk + q;
+                    if (c < pc) {
+                        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + q * kStreamThreads);
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(vi + (int64_t)c * ld)
+                                     : "memory");
+                    }
                 }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) v[q] = nv[q];
             }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float h, l;
-                df_split(v[q].x, h, l);
-                df_acc(S0, s0, h, l, scf[c + q], scf[p + c + q]);
-                df_split(v[q].y, h, l);
-                df_acc(S1, s1, h, l, scf[c + q], scf[p + c + q]);
+        for (int j = 0; j < kUpdStages - 1; ++j) issue(j);
+        float S0 = 0.f, s0 = 0.f, S1 = 0.f, s1 = 0.f;
+        for (int j = 0; j < nchunks; ++j) {
+            issue(j + kUpdStages - 1);
+            asm volatile("cp.async.wait_group %0;" ::"n"(kUpdStages - 1) : "memory");
+            const double2 *cur = stg + (size_t)(j % kUpdStages) * kUpdChunk * kStreamThreads + t;
+#pragma unroll
+            for (int q = 0; q < kUpdChunk; ++q) {
+                const int c = j * kUpdChunk + q;
+                if (c < pc) {
+                    const double2 v = cur[q * kStreamThreads];
+                    float h, l;
+                    df_split(v.x, h, l);
+                    df_acc(S0, s0, h, l, scf[c], scf[p + c]);
+                    df_split(v.y, h, l);
+                    df_acc(S1, s1, h, l, scf[c], scf[p + c]);
+                }
             }
-            c += 4;
         }
-        for (; c < pc; ++c) {
-            const double2 v = *reinterpret_cast<const double2 *>(vi + (int64_t)c * ld);
-            float h, l;
-            df_split(v.x, h, l);
-            df_acc(S0, s0, h, l, scf[c], scf[p + c]);
-            df_split(v.y, h, l);
-            df_acc(S1, s1, h, l, scf[c], scf[p + c]);
-        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         if (norm_last) {
             double2 *vl = reinterpret_cast<double2 *>(V + (int64_t)(p - 1) * ld + i);
             double2 v = *vl;
@@ -340,7 +349,7 @@ bool dots_df_applies(const Workspace &w) { return w.n >= kDfMinRows; }
 cudaError_t launch_update_df(const Workspace &w, int p, const double *coef, double alpha, const double *src,
                              double *out, bool norm_last, cudaStream_t s)
 {
-    const size_t smem = 2 * sizeof(float) * (size_t)(p > 0 ? p : 1);
+    const size_t smem = kUpdSmemFixed + 2 * sizeof(float) * (size_t)(p > 0 ? p : 1);
     const int grid = w.num_sms * kUpdateBlocksPerSM;
     launch_k(false, k_update_df, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef, alpha, src, out,
              norm_last ? 1 : 0, w.st, 1);
@@ -370,6 +379,10 @@ cudaError_t configure_df_kernels()
     cudaError_t e = cudaFuncSetAttribute(k_dots_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDfDotsSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_dots_df<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDfDotsSmem);
+    // stage buffers (48 KiB) plus the coefficient splits of up to kMaxRestart + 1 columns
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kUpdSmemFixed + 2 * sizeof(float) * (kMaxRestart + 1)));
     return e;
 }
 

@@ -246,8 +246,9 @@ int igs_block_dots_static(const double *V, int64_t ldv, int p, int64_t n, const 
                           const double *x1, double *out, void *stream);
 
 /* Arithmetic-pipe probe (measurement support; the paper has no counterpart): the FP64 and
- * FP32 fused multiply-add throughput of `device`, in FMAs per second, measured with every SM
- * full of independent FMA chains (about 0.2 s of GPU time; allocates a few KB).  On GB300 the
+ * FP32 fused multiply-add throughput of `device`, in FMAs per second: the best over 2, 4 and 8
+ * blocks of 256 threads per SM with 4, 8 and 16 independent FMA chains per thread (about
+ * 1 s of GPU time; allocates a few KB).  On GB300 the
  * FP64 rate bounds this library's FP64 streaming kernels, so the benchmark reports it beside
  * the unit-count FP64 peak.  Returns IGS_OK, IGS_EINVAL (NULL output) or IGS_ECUDA. */
 int igs_probe_fma(int device, double *fp64_fma_per_s, double *fp32_fma_per_s);

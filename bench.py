@@ -78,6 +78,8 @@ def main_config(gs, method, ws, precision="fp64"):
 
 BATCH_COUNT, BATCH_M, BATCH_TOL, BATCH_MAX_RESTARTS = 4096, 50, 1e-12, 20
 BATCH_METRIC, BATCH_UNIT = "solves/s", "solves/s"
+# the ncu capture of the batched kernel (1024-system case): DRAM read + write bytes
+BATCH_CAPTURE_SYSTEMS, BATCH_CAPTURE_DRAM_BYTES = 1024, 42.4e9 + 0.90e9
 FP64_PEAK_TFLOPS = 152 * FP64_FMA_PER_CLK_PER_SM * 2 * 2070.0e6 / 1e12
 
 
@@ -334,6 +336,17 @@ def run_batched(args, pkg, torch, local, dist, with_one_at_a_time=True):
     ns = [A.n for A in As]
     nnzs = [A.nnz for A in As]
     fma = batch_fma(ns, nnzs, steps_b, cycles_b, BATCH_M, args.gs)
+    # DRAM bytes per launch: the ncu capture of the same kernel on the first 1024 systems of
+    # this generator (profiles/k_batch_solve_banded1024_m50.md: 42.4 GB read + 0.90 GB written)
+    # scaled by the FMA work of this batch over that of those 1024 systems (each system's
+    # arithmetic, steps and cycles are the same alone or in any batch)
+    traffic, traffic_src = None, None
+    if count >= BATCH_CAPTURE_SYSTEMS and args.gs == 2 and SEED + rank == 0:
+        k = BATCH_CAPTURE_SYSTEMS
+        fma_k = batch_fma(ns[:k], nnzs[:k], steps_b[:k], cycles_b[:k], BATCH_M, args.gs)
+        traffic = BATCH_CAPTURE_DRAM_BYTES * fma / fma_k
+        traffic_src = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of k_batch_solve on the first {k} "
+                       f"systems ({BATCH_CAPTURE_DRAM_BYTES / 1e9:.1f} GB), scaled by FMA work x{fma / fma_k:.2f}")
     avg_s = ms / 1e3 / args.steps
     achieved = 2 * fma / avg_s / 1e12
     line = {"metric": BATCH_METRIC, "value": solves_total / (ms / 1e3), "unit": BATCH_UNIT,
@@ -343,7 +356,7 @@ def run_batched(args, pkg, torch, local, dist, with_one_at_a_time=True):
             "launch": {"block_threads": info["block_threads"], "blocks_per_sm": info["blocks_per_sm"],
                        "tuned": not args.batch_launch, "tune_table_ms": info["tune"], "create_s": t_create},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "traffic_source": traffic_src,
                          "kernel": "k_batch_solve (persistent; all steps of Alg. 4.1 per system)",
                          "flops_per_launch": 2 * fma,
                          "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2070 MHz"},

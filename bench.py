@@ -565,7 +565,7 @@ def run_served(args, pkg, torch, local, dist, duration, drain_s, oaat_budget_s=9
             "by_path": {"gang": sum(1 for c in done if c["path"] == 0),
                         "graph_lane": sum(1 for c in done if c["path"] == 1)},
             "max_backlog": max_queue}
-    if oaat_budget_s > 0 and done:
+    if oaat_budget_s > 0 and done and not args.no_one_at_a_time:
         # the same requests, one at a time through igs_solve in FP64 with graph-captured
         # cycles (set-up and capture outside the timing), in an order spread over the run
         order = list(range(0, len(done), 2)) + list(range(1, len(done), 2))

@@ -787,9 +787,9 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=16, help="gang requests in flight on the GPU at once")
     ap.add_argument("--serve-backlog", type=int, default=16,
                     help="requests waiting for admission at most (arrivals beyond it are refused)")
-    ap.add_argument("--serve-graph-min-n", type=int, default=250000,
+    ap.add_argument("--serve-graph-min-n", type=int, default=100000,
                     help="requests with n >= this take the server's graph lanes (0: gangs only)")
-    ap.add_argument("--serve-graph-lanes", type=int, default=2,
+    ap.add_argument("--serve-graph-lanes", type=int, default=3,
                     help="graph-lane requests in flight at once")
     args = ap.parse_args()
     if args.warmup < 3:

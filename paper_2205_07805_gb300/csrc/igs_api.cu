@@ -154,6 +154,7 @@ double upd_bytes(const igs::Workspace &w, int p) { return 8.0 * w.n * (p + 2); }
 // st->rnorm/xnorm/bnorm set (by the solve set-up or the previous cycle's end).
 cudaError_t enqueue_cycle32(igs_ctx *ctx, Issuer &is, int m, int gs);
 cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m, bool df);
+cudaError_t enqueue_cycle_vdf(igs_ctx *ctx, Issuer &is, int m, int gs);
 
 // The block multi-dot of the FP64 cycles: FP64 FMAs, or double-float products on the FP32
 // pipes for the IGS_PREC_FP64_DF form (from kDfMinRows rows on; same partial-sum layout).
@@ -169,11 +170,9 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
 {
     if (gs == 0) return enqueue_cycle_1r(ctx, is, m, prec == IGS_PREC_FP64_DF);
     if (prec == IGS_PREC_FP32_IR) return enqueue_cycle32(ctx, is, m, gs);
+    if (prec == IGS_PREC_FP64_DF && igs::dots_df_applies(ctx->w)) return enqueue_cycle_vdf(ctx, is, m, gs);
     const igs::Workspace &w = ctx->w;
-    const DotsLauncher dots = dots_launcher(w, prec == IGS_PREC_FP64_DF);
-    // the double-float form also runs the in-cycle basis updates (steps 13 and 16) on the FP32
-    // pipes; x = x0 + V y at the cycle's end stays FP64
-    const bool df_stream = prec == IGS_PREC_FP64_DF && igs::dots_df_applies(w);
+    const DotsLauncher dots = igs::launch_dots;
     cudaStream_t s = is.s;
     const int64_t ld = w.ld;
     double *V = w.V;
@@ -238,8 +237,7 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
         // Steps 7, 11, 13: v_{k-1} = w/gamma in place, u_k = v_k/gamma - V_{k-1} r^(1).
         double *uout = gs == 1 ? col(p) : w.u;
         RUN(igs::KC_UPDATE, upd_bytes(w, p) + 8.0 * w.n, 2.0 * w.n * p, s,
-            df_stream ? igs::launch_update_df(w, p, w.r1v, 0.0, w.z, uout, true, st_)
-                      : igs::launch_update(w, p, w.r1v, false, 0.0, w.z, uout, true, false, true, st_));
+            igs::launch_update(w, p, w.r1v, false, 0.0, w.z, uout, true, false, true, st_));
         if (gs == 2) {
             // Step 14: r^(2) = V_{k-1}^T u_k.
             RUN(igs::KC_DOTS, dots_bytes(w, p, 1), 2.0 * w.n * p, s, dots(w, p, w.u, nullptr, true, st_, &pl));
@@ -247,8 +245,7 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
             RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_b(w, k, pl, st_));
             // Step 16: w_k = u_k - V_{k-1} r^(3).
             RUN(igs::KC_UPDATE, upd_bytes(w, p), 2.0 * w.n * p, s,
-                df_stream ? igs::launch_update_df(w, p, w.r3v, 1.0, w.u, col(p), false, st_)
-                          : igs::launch_update(w, p, w.r3v, false, 1.0, w.u, col(p), false, false, true, st_));
+                igs::launch_update(w, p, w.r3v, false, 1.0, w.u, col(p), false, false, true, st_));
         }
     }
     // Flush: gamma_{m+1} = ||w_{m+1}||, H_{m+1,m}, last L row, v_{m+1} = w_{m+1}/gamma.
@@ -262,6 +259,114 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_lsq(w, m, st_));
     RUN(igs::KC_CYCLE, upd_bytes(w, m), 2.0 * w.n * m, s,
         igs::launch_update(w, 0, w.y, true, 1.0, w.x, w.x, false, true, false, st_));
+    // r = b - A x, ||r||, ||x||, beta(x).
+    RUN(igs::KC_CYCLE, spmv_bytes(w) + 8.0 * w.n, 2.0 * w.nnz, s, igs::launch_spmv(w, w.x, w.r, w.b, false, st_));
+    int nblk = 0;
+    RUN(igs::KC_CYCLE, 16.0 * w.n, 4.0 * w.n, s, igs::launch_norms(w, w.r, w.x, nullptr, &nblk, st_));
+    RUN(igs::KC_CYCLE, 0, 0, s, igs::launch_beta(w, nblk, st_));
+#undef RUN
+    return cudaSuccess;
+}
+
+// One Alg. 4.1 cycle of the double-float form (IGS_PREC_FP64_DF, n >= kDfMinRows): the same
+// steps and single-block kernels as the FP64 cycle, with the basis stored split (each element
+// as its FP32 (hi, lo) pair in V's bytes, written once when its column is formed) and the
+// multi-dots and basis updates in double-float arithmetic.  FP64 vectors: the current
+// unnormalised w (in w.t; the SpMV input and the source of step 7's v = w / gamma), z = A w,
+// u, x and r.  u is also kept split (in w.r's bytes, which hold r only at the cycle's start
+// and end) for step 14.  x = x0 + V y and r = b - A x stay FP64.
+cudaError_t enqueue_cycle_vdf(igs_ctx *ctx, Issuer &is, int m, int gs)
+{
+    const igs::Workspace &w = ctx->w;
+    cudaStream_t s = is.s;
+    const int64_t ld = w.ld;
+    auto col = [&](int c) { return w.V + (int64_t)c * ld; };
+    auto cold = [&](int c) { return reinterpret_cast<float2 *>(w.V + (int64_t)c * ld); };
+    double *wb = w.t;                               // FP64 w
+    float2 *ud = reinterpret_cast<float2 *>(w.r);   // split u (between the cycle's start and end)
+    cudaError_t e;
+#define RUN(cls, bytes, flops, on, expr)                                          \
+    do {                                                                          \
+        e = is.run((cls), (bytes), (flops), [&](cudaStream_t st_) { (void)st_; return (expr); }, (on)); \
+        if (e != cudaSuccess) return e;                                           \
+    } while (0)
+    // Step 1: rho = ||r0||, v1 = r0 / rho (split into the basis, FP64 into wb).
+    RUN(igs::KC_CYCLE, 0, 0, s, igs::launch_cycle_start(w, 0, st_));
+    RUN(igs::KC_CYCLE, 16.0 * w.n, w.n, s, igs::launch_scale_df(w, w.r, cold(0), wb, 0, false, st_));
+    // Step 2: w2 = A v1, H11 = v1^T w2, w2 -= H11 v1.
+    igs::DotsPlan pl{};
+    RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wb, w.z, nullptr, false, st_));
+    RUN(igs::KC_DOTS, dots_bytes(w, 1, 1), 2.0 * w.n, s,
+        igs::launch_dots_df_ex(w, 1, w.z, nullptr, false, true, false, st_, &pl));
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_prime(w, pl, st_));
+    RUN(igs::KC_UPDATE, upd_bytes(w, 1), 2.0 * w.n, s,
+        igs::launch_update_df_ex(w, 1, w.r1v, false, 1.0, w.z, wb, cold(1), nullptr, false, false, true, st_));
+
+    bool pending_join = false;
+    auto join_side = [&]() -> cudaError_t {
+        if (pending_join && is.capture) {
+            cudaError_t ee = cudaStreamWaitEvent(s, ctx->ev_join, 0);
+            if (ee != cudaSuccess) return ee;
+        }
+        pending_join = false;
+        return cudaSuccess;
+    };
+    auto fork_givens = [&](int j) -> cudaError_t {
+        cudaStream_t on = s;
+        if (is.capture) {
+            cudaError_t ee = cudaEventRecord(ctx->ev_fork, s);
+            if (ee == cudaSuccess) ee = cudaStreamWaitEvent(is.side, ctx->ev_fork, 0);
+            if (ee != cudaSuccess) return ee;
+            on = is.side;
+        }
+        cudaError_t ee = is.run(igs::KC_SMALL, 0, 0, [&](cudaStream_t st_) { return igs::launch_givens(w, j, st_); }, on);
+        if (ee != cudaSuccess) return ee;
+        if (is.capture) {
+            ee = cudaEventRecord(ctx->ev_join, is.side);
+            if (ee != cudaSuccess) return ee;
+            pending_join = true;
+        }
+        return cudaSuccess;
+    };
+
+    for (int k = 3; k <= m + 1; ++k) {
+        const int p = k - 1;
+        // Step 4: v_k = A w_{k-1} (FP64 w).
+        RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wb, w.z, nullptr, true, st_));
+        // Step 5: [V_{k-2}, w_{k-1}]^T [w_{k-1}, v_k]: the split basis (w is its column p-1) and z.
+        RUN(igs::KC_DOTS, dots_bytes(w, p, 2), 4.0 * w.n * p, s,
+            igs::launch_dots_df_ex(w, p, col(p - 1), w.z, true, true, true, st_, &pl));
+        if ((e = join_side()) != cudaSuccess) return e;
+        // Steps 6-12 (+ step 17 for one iteration).
+        RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_a(w, k, gs, pl, st_));
+        if ((e = fork_givens(k - 3)) != cudaSuccess) return e;
+        // Steps 7, 11, 13: column p-1 = split(w / gamma), u = z / gamma - V_{k-1} r^(1) (FP64 and
+        // split; with one iteration u is w_k: FP64 into wb, split into column p).
+        double *uout = gs == 1 ? wb : w.u;
+        float2 *udf = gs == 1 ? cold(p) : ud;
+        RUN(igs::KC_UPDATE, upd_bytes(w, p) + 8.0 * w.n, 2.0 * w.n * p, s,
+            igs::launch_update_df_ex(w, p, w.r1v, false, 0.0, w.z, uout, udf, wb, true, false, true, st_));
+        if (gs == 2) {
+            // Step 14: r^(2) = V_{k-1}^T u_k.
+            RUN(igs::KC_DOTS, dots_bytes(w, p, 1), 2.0 * w.n * p, s,
+                igs::launch_dots_df_ex(w, p, reinterpret_cast<const double *>(ud), nullptr, true, true, true, st_, &pl));
+            // Steps 15, 17.
+            RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_b(w, k, pl, st_));
+            // Step 16: w_k = u_k - V_{k-1} r^(3) (FP64 into wb, split into column p).
+            RUN(igs::KC_UPDATE, upd_bytes(w, p), 2.0 * w.n * p, s,
+                igs::launch_update_df_ex(w, p, w.r3v, false, 1.0, w.u, wb, cold(p), nullptr, false, false, true, st_));
+        }
+    }
+    // Flush: gamma_{m+1} = ||w_{m+1}||, H_{m+1,m}, last L row, v_{m+1} = split(w_{m+1} / gamma).
+    RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
+        igs::launch_dots_df_ex(w, m + 1, col(m), nullptr, true, true, true, st_, &pl));
+    if ((e = join_side()) != cudaSuccess) return e;
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_flush(w, m, pl, st_));
+    RUN(igs::KC_CYCLE, 16.0 * w.n, w.n, s, igs::launch_scale_df(w, wb, cold(m), nullptr, 1, true, st_));
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));
+    // Least squares y = argmin ||rho e1 - H y||, x_m = x_0 + V_m y_m (FP64).
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_lsq(w, m, st_));
+    RUN(igs::KC_CYCLE, upd_bytes(w, m), 2.0 * w.n * m, s, igs::launch_xupdate_vdf(w, st_));
     // r = b - A x, ||r||, ||x||, beta(x).
     RUN(igs::KC_CYCLE, spmv_bytes(w) + 8.0 * w.n, 2.0 * w.nnz, s, igs::launch_spmv(w, w.x, w.r, w.b, false, st_));
     int nblk = 0;
@@ -1042,6 +1147,11 @@ int igs_arnoldi_ex(igs_ctx *ctx, const double *r0, int m, int method, int gs, in
             igs::DevState hs{};
             if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
             const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            if (V && precision == IGS_PREC_FP64_DF && gs != 0 && igs::dots_df_applies(w)) {
+                // the double-float Alg. 4.1 cycle keeps the basis split: hand it out in FP64
+                CK(igs::launch_df_to_f64(w.V, w.ld * (int64_t)(m + 1), w.num_sms, ctx->stream));
+                ctx->launches += 1;
+            }
             if (V)
                 CK(cudaMemcpy2DAsync(V, sizeof(double) * ldv, w.V, sizeof(double) * w.ld, sizeof(double) * w.n,
                                      m + 1, kind, ctx->stream));

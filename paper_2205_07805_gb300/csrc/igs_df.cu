@@ -122,7 +122,7 @@ __device__ __forceinline__ void cp_async16(double *dst, const double *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
 
-template <int NQ>
+template <int NQ, bool VDF, bool X0DF>
 __global__ void __launch_bounds__(kStreamThreads, kDotsBlocksPerSM)
 k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t rows,
           const double *__restrict__ x0, const double *__restrict__ x1, double *__restrict__ part,
@@ -183,17 +183,33 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
             float xh[NQ][2], xl[NQ][2];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                const double2 xv = *reinterpret_cast<const double2 *>(src + 64 * q);
-                df_split(xv.x, xh[q][0], xl[q][0]);
-                df_split(xv.y, xh[q][1], xl[q][1]);
+                if (q == 0 && X0DF) {  // stored split: (hi, lo) of two rows
+                    const float4 xv = *reinterpret_cast<const float4 *>(src);
+                    xh[0][0] = xv.x;
+                    xl[0][0] = xv.y;
+                    xh[0][1] = xv.z;
+                    xl[0][1] = xv.w;
+                } else {
+                    const double2 xv = *reinterpret_cast<const double2 *>(src + 64 * q);
+                    df_split(xv.x, xh[q][0], xl[q][0]);
+                    df_split(xv.y, xh[q][1], xl[q][1]);
+                }
             }
 #pragma unroll
             for (int c = 0; c < CW; ++c) {
                 if (c < cw) {
-                    const double2 v = *reinterpret_cast<const double2 *>(src + 64 * (NQ + c));
                     float h0, l0, h1, l1;
-                    df_split(v.x, h0, l0);
-                    df_split(v.y, h1, l1);
+                    if (VDF) {
+                        const float4 v = *reinterpret_cast<const float4 *>(src + 64 * (NQ + c));
+                        h0 = v.x;
+                        l0 = v.y;
+                        h1 = v.z;
+                        l1 = v.w;
+                    } else {
+                        const double2 v = *reinterpret_cast<const double2 *>(src + 64 * (NQ + c));
+                        df_split(v.x, h0, l0);
+                        df_split(v.y, h1, l1);
+                    }
 #pragma unroll
                     for (int q = 0; q < NQ; ++q) {
                         df_acc(S[c][q], s[c][q], h0, l0, xh[q][0], xl[q][0]);
@@ -260,20 +276,29 @@ constexpr int kUpdStages = 3;
 constexpr size_t kUpdStageBytes = (size_t)kUpdChunk * 16 * kStreamThreads;  // one chunk, all threads
 constexpr size_t kUpdSmemFixed = kUpdStages * kUpdStageBytes;              // + 8 p for the coefficients
 
+// V: FP64 basis (VDF false; split on the fly) or the split basis of the double-float form
+// (VDF true: each element stored as its (hi, lo) FP32 pair in the same 8 bytes).  With
+// norm_last, column p-1 is the lagged w: FP64 V scales it in place; the split basis takes the
+// FP64 w from wsrc and stores the split of w * a into column p-1.  out (FP64) always; out_df
+// (nullable) also gets the split of each output row.  neg_coef negates coef; p_from_state
+// takes p from st->ncols (the x update at the cycle's end).
+template <bool VDF>
 __global__ void __launch_bounds__(kStreamThreads, kUpdateBlocksPerSM)
-k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coef, double alpha,
-            const double *src, double *out, int norm_last, DevState *st, int check_halt)
+k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coef, int neg_coef, double alpha,
+            const double *src, double *out, float2 *out_df, const double *wsrc, int norm_last, int p_from_state,
+            DevState *st, int check_halt)
 {
     IGS_PDL_ENTER();
     if (check_halt && df_halted(st)) return;
     extern __shared__ double usm[];
-    // stage buffers: [stage][column in chunk][thread] of double2; then the coefficient splits
+    if (p_from_state) p = st->ncols;
+    // stage buffers: [stage][column in chunk][thread] of 16 bytes; then the coefficient splits
     double2 *stg = reinterpret_cast<double2 *>(usm);
     float *scf = reinterpret_cast<float *>(usm + kUpdSmemFixed / sizeof(double));  // hi [0,p), lo [p,2p)
     const double a = norm_last ? st->inv_gamma : alpha;
     for (int c = threadIdx.x; c < p; c += blockDim.x) {
         float h, l;
-        df_split(coef[c], h, l);
+        df_split(neg_coef ? -coef[c] : coef[c], h, l);
         scf[c] = h;
         scf[p + c] = l;
     }
@@ -314,33 +339,106 @@ k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ 
             for (int q = 0; q < kUpdChunk; ++q) {
                 const int c = j * kUpdChunk + q;
                 if (c < pc) {
-                    const double2 v = cur[q * kStreamThreads];
-                    float h, l;
-                    df_split(v.x, h, l);
-                    df_acc(S0, s0, h, l, scf[c], scf[p + c]);
-                    df_split(v.y, h, l);
-                    df_acc(S1, s1, h, l, scf[c], scf[p + c]);
+                    float h0, l0, h1, l1;
+                    if (VDF) {
+                        const float4 v = *reinterpret_cast<const float4 *>(cur + q * kStreamThreads);
+                        h0 = v.x;
+                        l0 = v.y;
+                        h1 = v.z;
+                        l1 = v.w;
+                    } else {
+                        const double2 v = cur[q * kStreamThreads];
+                        df_split(v.x, h0, l0);
+                        df_split(v.y, h1, l1);
+                    }
+                    df_acc(S0, s0, h0, l0, scf[c], scf[p + c]);
+                    df_acc(S1, s1, h1, l1, scf[c], scf[p + c]);
                 }
             }
         }
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         if (norm_last) {
-            double2 *vl = reinterpret_cast<double2 *>(V + (int64_t)(p - 1) * ld + i);
-            double2 v = *vl;
+            double2 v;
+            if (VDF) {
+                v = *reinterpret_cast<const double2 *>(wsrc + i);
+            } else {
+                v = *reinterpret_cast<const double2 *>(V + (int64_t)(p - 1) * ld + i);
+            }
             v.x *= a;
             v.y *= a;
-            *vl = v;
-            float h, l;
-            df_split(v.x, h, l);
-            df_acc(S0, s0, h, l, scf[p - 1], scf[2 * p - 1]);
-            df_split(v.y, h, l);
-            df_acc(S1, s1, h, l, scf[p - 1], scf[2 * p - 1]);
+            float h0, l0, h1, l1;
+            df_split(v.x, h0, l0);
+            df_split(v.y, h1, l1);
+            if (VDF)
+                *reinterpret_cast<float4 *>(V + (int64_t)(p - 1) * ld + i) = make_float4(h0, l0, h1, l1);
+            else
+                *reinterpret_cast<double2 *>(V + (int64_t)(p - 1) * ld + i) = v;
+            df_acc(S0, s0, h0, l0, scf[p - 1], scf[2 * p - 1]);
+            df_acc(S1, s1, h1, l1, scf[p - 1], scf[2 * p - 1]);
         }
         const double2 sv = *reinterpret_cast<const double2 *>(src + i);
         double2 o;
         o.x = fma(a, sv.x, -(f2d_bits(S0) + f2d_bits(s0)));
         o.y = fma(a, sv.y, -(f2d_bits(S1) + f2d_bits(s1)));
         *reinterpret_cast<double2 *>(out + i) = o;
+        if (out_df) {
+            float h0, l0, h1, l1;
+            df_split(o.x, h0, l0);
+            df_split(o.y, h1, l1);
+            *reinterpret_cast<float4 *>(out_df + i) = make_float4(h0, l0, h1, l1);
+        }
+    }
+}
+
+// dst_df[i] = split(src[i] * scale) and, when dst64 is given, dst64[i] = src[i] * scale, with
+// scale = st->inv_rho (which = 0) or st->inv_gamma (which = 1): v_1 = r_0 / rho at a cycle's
+// start and the flush's v_{m+1} = w_{m+1} / gamma into the split basis.
+__global__ void __launch_bounds__(kStreamThreads)
+k_scale_df(int64_t n, const double *src, float2 *dst_df, double *dst64, int which, const DevState *st, int check_halt)
+{
+    IGS_PDL_ENTER();
+    if (check_halt && df_halted(st)) return;
+    const double sc = which == 0 ? st->inv_rho : st->inv_gamma;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double v = src[i] * sc;
+        float h, l;
+        df_split(v, h, l);
+        dst_df[i] = make_float2(h, l);
+        if (dst64) dst64[i] = v;
+    }
+}
+
+// x[i] += sum_{c < st->ncols} V[i,c] y[c] over the split basis, in FP64: each stored element
+// is exactly hi + lo, rebuilt from its bits with integer operations and one FP64 addition,
+// then one FP64 FMA per element (x = x0 + V_m y_m at the cycle's end; once per cycle).
+__global__ void __launch_bounds__(kStreamThreads)
+k_xupdate_vdf(const double *V, int64_t ld, int64_t n, const double *__restrict__ y, double *x, const DevState *st)
+{
+    IGS_PDL_ENTER();
+    extern __shared__ double ys[];
+    const int p = st->ncols;
+    for (int c = threadIdx.x; c < p; c += blockDim.x) ys[c] = y[c];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double s = 0.0;
+        for (int c = 0; c < p; ++c) {
+            const float2 v = reinterpret_cast<const float2 *>(V + (int64_t)c * ld)[i];
+            s = fma(f2d_bits(v.x) + f2d_bits(v.y), ys[c], s);
+        }
+        x[i] += s;
+    }
+}
+
+// In place: the split basis (rows < ld, cols columns) back to FP64, hi + lo (for igs_arnoldi's
+// output of the double-float form).
+__global__ void __launch_bounds__(kStreamThreads) k_df_to_f64(double *V, int64_t count)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const float2 v = reinterpret_cast<const float2 *>(V)[i];
+        V[i] = (double)v.x + (double)v.y;
     }
 }
 
@@ -349,40 +447,99 @@ bool dots_df_applies(const Workspace &w) { return w.n >= kDfMinRows; }
 cudaError_t launch_update_df(const Workspace &w, int p, const double *coef, double alpha, const double *src,
                              double *out, bool norm_last, cudaStream_t s)
 {
-    const size_t smem = kUpdSmemFixed + 2 * sizeof(float) * (size_t)(p > 0 ? p : 1);
+    return launch_update_df_ex(w, p, coef, false, alpha, src, out, nullptr, nullptr, norm_last, false, false, s);
+}
+
+cudaError_t launch_update_df_ex(const Workspace &w, int p, const double *coef, bool neg_coef, double alpha,
+                                const double *src, double *out, float2 *out_df, const double *wsrc, bool norm_last,
+                                bool p_from_state, bool vdf, cudaStream_t s)
+{
+    const int pmax = p_from_state ? w.mmax + 1 : p;
+    const size_t smem = kUpdSmemFixed + 2 * sizeof(float) * (size_t)(pmax > 0 ? pmax : 1);
     const int grid = w.num_sms * kUpdateBlocksPerSM;
-    launch_k(false, k_update_df, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef, alpha, src, out,
-             norm_last ? 1 : 0, w.st, 1);
+    if (vdf)
+        launch_k(false, k_update_df<true>, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef,
+                 neg_coef ? 1 : 0, alpha, src, out, out_df, wsrc, norm_last ? 1 : 0, p_from_state ? 1 : 0, w.st, 1);
+    else
+        launch_k(false, k_update_df<false>, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef,
+                 neg_coef ? 1 : 0, alpha, src, out, out_df, wsrc, norm_last ? 1 : 0, p_from_state ? 1 : 0, w.st, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_df(const Workspace &w, const double *src, float2 *dst_df, double *dst64, int which,
+                            bool check_halt, cudaStream_t s)
+{
+    launch_k(false, k_scale_df, dim3(w.num_sms * kBlocksPerSM), dim3(kStreamThreads), 0, s, w.n, src, dst_df, dst64,
+             which, (const DevState *)w.st, check_halt ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xupdate_vdf(const Workspace &w, cudaStream_t s)
+{
+    const size_t smem = sizeof(double) * (size_t)(w.mmax + 1);
+    launch_k(false, k_xupdate_vdf, dim3(w.num_sms * kUpdateBlocksPerSM), dim3(kStreamThreads), smem, s,
+             (const double *)w.V, w.ld, w.n, (const double *)w.y, w.x, (const DevState *)w.st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_df_to_f64(double *V, int64_t count, int num_sms, cudaStream_t s)
+{
+    launch_k(false, k_df_to_f64, dim3(num_sms * kBlocksPerSM), dim3(kStreamThreads), 0, s, V, count);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dots_df(const Workspace &w, int p, const double *x0, const double *x1, bool check_halt,
                            cudaStream_t s, DotsPlan *plan_out)
 {
+    return launch_dots_df_ex(w, p, x0, x1, check_halt, false, false, s, plan_out);
+}
+
+cudaError_t launch_dots_df_ex(const Workspace &w, int p, const double *x0, const double *x1, bool check_halt,
+                              bool vdf, bool x0df, cudaStream_t s, DotsPlan *plan_out)
+{
     const DotsPlan pl = plan_dots(w, p);
     if (plan_out) *plan_out = pl;
     if ((p + pl.groups - 1) / pl.groups > kDotsColsPerBlock) return cudaErrorInvalidValue;
     const int64_t n4 = (w.n + 3) & ~int64_t(3);
     dim3 grid(pl.rblocks, pl.groups);
-    if (x1)
-        launch_k(false, k_dots_df<2>, grid, dim3(kStreamThreads), kDfDotsSmem, s, w.V, w.ld, p, n4, pl.rows, x0, x1,
-                 w.part, (const DevState *)w.st, check_halt ? 1 : 0);
-    else
-        launch_k(false, k_dots_df<1>, grid, dim3(kStreamThreads), kDfDotsSmem, s, w.V, w.ld, p, n4, pl.rows, x0,
-                 (const double *)nullptr, w.part, (const DevState *)w.st, check_halt ? 1 : 0);
+    const DevState *st = w.st;
+    const int ch = check_halt ? 1 : 0;
+    const size_t sm = kDfDotsSmem;
+    const dim3 bl(kStreamThreads);
+    if (x1) {
+        if (vdf && x0df)
+            launch_k(false, k_dots_df<2, true, true>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, x1, w.part, st, ch);
+        else if (vdf)
+            launch_k(false, k_dots_df<2, true, false>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, x1, w.part, st, ch);
+        else
+            launch_k(false, k_dots_df<2, false, false>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, x1, w.part, st, ch);
+    } else {
+        const double *none = nullptr;
+        if (vdf && x0df)
+            launch_k(false, k_dots_df<1, true, true>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, none, w.part, st, ch);
+        else if (vdf)
+            launch_k(false, k_dots_df<1, true, false>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, none, w.part, st, ch);
+        else
+            launch_k(false, k_dots_df<1, false, false>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, none, w.part, st, ch);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t configure_df_kernels()
 {
     // 48 KiB of stage buffers per block (3 blocks per SM): above the default dynamic limit
-    cudaError_t e = cudaFuncSetAttribute(k_dots_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDfDotsSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dots_df<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDfDotsSmem);
+    const int dm = (int)kDfDotsSmem;
+    const int um = (int)(kUpdSmemFixed + 2 * sizeof(float) * (kMaxRestart + 1));
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_dots_df<1, false, false>, A, dm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<2, false, false>, A, dm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<1, true, false>, A, dm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<2, true, false>, A, dm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<1, true, true>, A, dm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<2, true, true>, A, dm);
     // stage buffers (48 KiB) plus the coefficient splits of up to kMaxRestart + 1 columns
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kUpdSmemFixed + 2 * sizeof(float) * (kMaxRestart + 1)));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_df<false>, A, um);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_df<true>, A, um);
     return e;
 }
 

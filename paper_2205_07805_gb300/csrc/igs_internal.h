@@ -150,6 +150,24 @@ cudaError_t configure_df_kernels();
 // column p-1 normalised in place first when norm_last, a = st->inv_gamma then).
 cudaError_t launch_update_df(const Workspace &w, int p, const double *coef, double alpha, const double *src,
                              double *out, bool norm_last, cudaStream_t s);
+// The split basis (vdf: each basis element stored as its FP32 (hi, lo) pair in V's bytes) of
+// the double-float Alg. 4.1 cycle.  Update: also out_df = split(out) when given; with
+// norm_last and vdf the FP64 w comes from wsrc and split(w * inv_gamma) goes to column p-1;
+// neg_coef and p_from_state as in launch_update.  Multi-dot: vdf reads V split; x0df reads
+// x0 split (x1, when given, is FP64).
+cudaError_t launch_update_df_ex(const Workspace &w, int p, const double *coef, bool neg_coef, double alpha,
+                                const double *src, double *out, float2 *out_df, const double *wsrc, bool norm_last,
+                                bool p_from_state, bool vdf, cudaStream_t s);
+cudaError_t launch_dots_df_ex(const Workspace &w, int p, const double *x0, const double *x1, bool check_halt,
+                              bool vdf, bool x0df, cudaStream_t s, DotsPlan *plan_out);
+// dst_df = split(src * st->inv_rho (which 0) or st->inv_gamma (which 1)), dst64 (nullable) the
+// same in FP64.
+cudaError_t launch_scale_df(const Workspace &w, const double *src, float2 *dst_df, double *dst64, int which,
+                            bool check_halt, cudaStream_t s);
+// x += V y over the split basis in FP64 (p = st->ncols).
+cudaError_t launch_xupdate_vdf(const Workspace &w, cudaStream_t s);
+// In place: count split elements of V back to FP64.
+cudaError_t launch_df_to_f64(double *V, int64_t count, int num_sms, cudaStream_t s);
 // Partial sums of squares of up to three vectors (part[blk*nvec + q]).
 cudaError_t launch_norms(const Workspace &w, const double *a, const double *b,
                          const double *c, int *blocks_out, cudaStream_t s);

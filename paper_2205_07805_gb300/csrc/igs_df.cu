@@ -104,9 +104,9 @@ __device__ __forceinline__ void df_add(float &A, float &a, float B, float b)
 // row sub-slice (so each X row is loaded and split once per block, not once per column)
 // and the products are accumulated in double-float.  Each lane handles two consecutive rows
 // per 64-row segment: one copy instruction of a warp moves 512 contiguous bytes of a column.
-// The segments are double-buffered in shared memory by cp.async: while a warp computes on
-// segment g (about 370 instructions per lane), the copies of segment g+1 are in flight, so
-// the HBM latency is hidden without holding the next segment in registers.  Each lane
+// The segments are staged in shared memory by cp.async, kDfStages deep: while a warp
+// computes on segment g, the copies of the next two segments are in flight, so the HBM
+// latency is hidden without holding them in registers.  Each lane
 // reads back only the 16-byte chunks it copied itself, so no barrier is needed.  Lane sums
 // are folded into a double-float total every 32 elements, combined over the warp by a
 // double-float shuffle tree and over the block's warps in order, and converted to FP64 once
@@ -114,7 +114,8 @@ __device__ __forceinline__ void df_add(float &A, float &a, float B, float b)
 // =====================================================================================
 constexpr int kDfStreams = kDotsColsPerBlock + 2;           // up to 4 columns and 2 vectors
 constexpr int kDfStageDoubles = kDfStreams * 64;            // one 64-row segment of each stream
-constexpr size_t kDfDotsSmem = sizeof(double) * 2 * kDfStageDoubles * (kStreamThreads / 32);
+constexpr int kDfStages = 3;                                // segments in flight + the one in use
+constexpr size_t kDfDotsSmem = sizeof(double) * kDfStages * kDfStageDoubles * (kStreamThreads / 32);
 
 __device__ __forceinline__ void cp_async16(double *dst, const double *src)
 {
@@ -141,7 +142,7 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int64_t r_lo = (int64_t)rb * rows;
     const int64_t r_hi = r_lo + rows < n4 ? r_lo + rows : n4;
-    double *stage0 = dsm + (size_t)wid * 2 * kDfStageDoubles + 2 * lane;  // this lane's slots
+    double *stage0 = dsm + (size_t)wid * kDfStages * kDfStageDoubles + 2 * lane;  // this lane's slots
     const double *vbase = V + (int64_t)c_lo * ld;
     float A[CW][NQ], a[CW][NQ], S[CW][NQ], s[CW][NQ];  // fold total and running chunk
 #pragma unroll
@@ -168,15 +169,22 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    if (g0 < g1) issue(g0, 0);
-    int since = 0;
-    for (int64_t g = g0; g < g1; ++g) {
-        const int b = (int)((g - g0) & 1);
-        if (g + 1 < g1)
-            issue(g + 1, b ^ 1);
+    // prologue: the first kDfStages - 1 segments (an empty group where there are fewer)
+#pragma unroll
+    for (int j = 0; j < kDfStages - 1; ++j) {
+        if (g0 + j < g1)
+            issue(g0 + j, j);
         else
             asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
+    }
+    int since = 0;
+    for (int64_t g = g0; g < g1; ++g) {
+        const int b = (int)((g - g0) % kDfStages);
+        if (g + kDfStages - 1 < g1)
+            issue(g + kDfStages - 1, (int)((g + kDfStages - 1 - g0) % kDfStages));
+        else
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(kDfStages - 1) : "memory");
         const int64_t i = r_lo + (g << 6) + 2 * lane;
         if (i < r_hi) {
             const double *src = stage0 + b * kDfStageDoubles;
@@ -313,6 +321,11 @@ k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ 
     for (int64_t pr = pr_lo + t; pr < pr_hi; pr += blockDim.x) {
         const int64_t i = 2 * pr;
         const double *vi = V + i;
+        // this row pair's FP64 operands, loaded before the column stream so that their latency
+        // is not exposed at the end
+        const double2 sv = *reinterpret_cast<const double2 *>(src + i);
+        double2 wv = make_double2(0.0, 0.0);
+        if (norm_last) wv = *reinterpret_cast<const double2 *>((VDF ? wsrc : V + (int64_t)(p - 1) * ld) + i);
         auto issue = [&](int j) {
             if (j < nchunks) {
                 double2 *dst = stg + (size_t)(j % kUpdStages) * kUpdChunk * kStreamThreads + t;
@@ -358,12 +371,7 @@ k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ 
         }
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         if (norm_last) {
-            double2 v;
-            if (VDF) {
-                v = *reinterpret_cast<const double2 *>(wsrc + i);
-            } else {
-                v = *reinterpret_cast<const double2 *>(V + (int64_t)(p - 1) * ld + i);
-            }
+            double2 v = wv;
             v.x *= a;
             v.y *= a;
             float h0, l0, h1, l1;
@@ -376,7 +384,6 @@ k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ 
             df_acc(S0, s0, h0, l0, scf[p - 1], scf[2 * p - 1]);
             df_acc(S1, s1, h1, l1, scf[p - 1], scf[2 * p - 1]);
         }
-        const double2 sv = *reinterpret_cast<const double2 *>(src + i);
         double2 o;
         o.x = fma(a, sv.x, -(f2d_bits(S0) + f2d_bits(s0)));
         o.y = fma(a, sv.y, -(f2d_bits(S1) + f2d_bits(s1)));
@@ -527,7 +534,8 @@ cudaError_t launch_dots_df_ex(const Workspace &w, int p, const double *x0, const
 
 cudaError_t configure_df_kernels()
 {
-    // 48 KiB of stage buffers per block (3 blocks per SM): above the default dynamic limit
+    // 72 KiB of stage buffers per block (3 blocks per SM fit the 228 KiB of an SM): above the
+    // default dynamic limit
     const int dm = (int)kDfDotsSmem;
     const int um = (int)(kUpdSmemFixed + 2 * sizeof(float) * (kMaxRestart + 1));
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;

@@ -104,9 +104,9 @@ __device__ __forceinline__ void df_add(float &A, float &a, float B, float b)
 // row sub-slice (so each X row is loaded and split once per block, not once per column)
 // and the products are accumulated in double-float.  Each lane handles two consecutive rows
 // per 64-row segment: one copy instruction of a warp moves 512 contiguous bytes of a column.
-// The segments are staged in shared memory by cp.async, kDfStages deep: while a warp
-// computes on segment g, the copies of the next two segments are in flight, so the HBM
-// latency is hidden without holding them in registers.  Each lane
+// The segments are staged in shared memory by cp.async, double-buffered: while a warp
+// computes on segment g, the copies of segment g+1 are in flight, so the HBM latency is
+// hidden without holding the next segment in registers.  Each lane
 // reads back only the 16-byte chunks it copied itself, so no barrier is needed.  Lane sums
 // are folded into a double-float total every 32 elements, combined over the warp by a
 // double-float shuffle tree and over the block's warps in order, and converted to FP64 once
@@ -114,7 +114,9 @@ __device__ __forceinline__ void df_add(float &A, float &a, float B, float b)
 // =====================================================================================
 constexpr int kDfStreams = kDotsColsPerBlock + 2;           // up to 4 columns and 2 vectors
 constexpr int kDfStageDoubles = kDfStreams * 64;            // one 64-row segment of each stream
-constexpr int kDfStages = 3;                                // segments in flight + the one in use
+constexpr int kDfStages = 2;  // a power of two: segment in use + one in flight (a third
+                               // stage measured slower: its index arithmetic cost more issue
+                               // slots than the deeper pipeline saved)
 constexpr size_t kDfDotsSmem = sizeof(double) * kDfStages * kDfStageDoubles * (kStreamThreads / 32);
 
 __device__ __forceinline__ void cp_async16(double *dst, const double *src)
@@ -179,9 +181,9 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
     }
     int since = 0;
     for (int64_t g = g0; g < g1; ++g) {
-        const int b = (int)((g - g0) % kDfStages);
+        const int b = (int)(g - g0) & (kDfStages - 1);
         if (g + kDfStages - 1 < g1)
-            issue(g + kDfStages - 1, (int)((g + kDfStages - 1 - g0) % kDfStages));
+            issue(g + kDfStages - 1, (int)(g + kDfStages - 1 - g0) & (kDfStages - 1));
         else
             asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group %0;" ::"n"(kDfStages - 1) : "memory");
@@ -534,8 +536,7 @@ cudaError_t launch_dots_df_ex(const Workspace &w, int p, const double *x0, const
 
 cudaError_t configure_df_kernels()
 {
-    // 72 KiB of stage buffers per block (3 blocks per SM fit the 228 KiB of an SM): above the
-    // default dynamic limit
+    // 48 KiB of stage buffers per block (3 blocks per SM): above the default dynamic limit
     const int dm = (int)kDfDotsSmem;
     const int um = (int)(kUpdSmemFixed + 2 * sizeof(float) * (kMaxRestart + 1));
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;

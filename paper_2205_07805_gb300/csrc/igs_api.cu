@@ -273,8 +273,9 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
 // as its FP32 (hi, lo) pair in V's bytes, written once when its column is formed) and the
 // multi-dots and basis updates in double-float arithmetic.  FP64 vectors: the current
 // unnormalised w (in w.t; the SpMV input and the source of step 7's v = w / gamma), z = A w,
-// u, x and r.  u is also kept split (in w.r's bytes, which hold r only at the cycle's start
-// and end) for step 14.  x = x0 + V y and r = b - A x stay FP64.
+// u, x and r.  z is also kept split (in w.u's bytes: step 5 reads it before step 13 writes
+// u), and u (in w.r's bytes, which hold r only at the cycle's start and end) for step 14.
+// x = x0 + V y and r = b - A x stay FP64.
 cudaError_t enqueue_cycle_vdf(igs_ctx *ctx, Issuer &is, int m, int gs)
 {
     const igs::Workspace &w = ctx->w;
@@ -284,6 +285,8 @@ cudaError_t enqueue_cycle_vdf(igs_ctx *ctx, Issuer &is, int m, int gs)
     auto cold = [&](int c) { return reinterpret_cast<float2 *>(w.V + (int64_t)c * ld); };
     double *wb = w.t;                               // FP64 w
     float2 *ud = reinterpret_cast<float2 *>(w.r);   // split u (between the cycle's start and end)
+    float2 *zd = reinterpret_cast<float2 *>(w.u);   // split z (from the SpMV until step 13 writes u)
+    const double *zdd = reinterpret_cast<const double *>(zd);
     cudaError_t e;
 #define RUN(cls, bytes, flops, on, expr)                                          \
     do {                                                                          \
@@ -295,9 +298,8 @@ cudaError_t enqueue_cycle_vdf(igs_ctx *ctx, Issuer &is, int m, int gs)
     RUN(igs::KC_CYCLE, 16.0 * w.n, w.n, s, igs::launch_scale_df(w, w.r, cold(0), wb, 0, false, st_));
     // Step 2: w2 = A v1, H11 = v1^T w2, w2 -= H11 v1.
     igs::DotsPlan pl{};
-    RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wb, w.z, nullptr, false, st_));
-    RUN(igs::KC_DOTS, dots_bytes(w, 1, 1), 2.0 * w.n, s,
-        igs::launch_dots_df_ex(w, 1, w.z, nullptr, false, true, false, st_, &pl));
+    RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wb, w.z, nullptr, false, st_, zd));
+    RUN(igs::KC_DOTS, dots_bytes(w, 1, 1), 2.0 * w.n, s, igs::launch_dots_df_ex(w, 1, zdd, nullptr, false, true, st_, &pl));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_prime(w, pl, st_));
     RUN(igs::KC_UPDATE, upd_bytes(w, 1), 2.0 * w.n, s,
         igs::launch_update_df_ex(w, 1, w.r1v, false, 1.0, w.z, wb, cold(1), nullptr, false, false, true, st_));
@@ -331,11 +333,11 @@ cudaError_t enqueue_cycle_vdf(igs_ctx *ctx, Issuer &is, int m, int gs)
 
     for (int k = 3; k <= m + 1; ++k) {
         const int p = k - 1;
-        // Step 4: v_k = A w_{k-1} (FP64 w).
-        RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wb, w.z, nullptr, true, st_));
+        // Step 4: v_k = A w_{k-1} (FP64 w; z in FP64 and split).
+        RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wb, w.z, nullptr, true, st_, zd));
         // Step 5: [V_{k-2}, w_{k-1}]^T [w_{k-1}, v_k]: the split basis (w is its column p-1) and z.
         RUN(igs::KC_DOTS, dots_bytes(w, p, 2), 4.0 * w.n * p, s,
-            igs::launch_dots_df_ex(w, p, col(p - 1), w.z, true, true, true, st_, &pl));
+            igs::launch_dots_df_ex(w, p, col(p - 1), zdd, true, true, st_, &pl));
         if ((e = join_side()) != cudaSuccess) return e;
         // Steps 6-12 (+ step 17 for one iteration).
         RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_a(w, k, gs, pl, st_));
@@ -349,7 +351,7 @@ cudaError_t enqueue_cycle_vdf(igs_ctx *ctx, Issuer &is, int m, int gs)
         if (gs == 2) {
             // Step 14: r^(2) = V_{k-1}^T u_k.
             RUN(igs::KC_DOTS, dots_bytes(w, p, 1), 2.0 * w.n * p, s,
-                igs::launch_dots_df_ex(w, p, reinterpret_cast<const double *>(ud), nullptr, true, true, true, st_, &pl));
+                igs::launch_dots_df_ex(w, p, reinterpret_cast<const double *>(ud), nullptr, true, true, st_, &pl));
             // Steps 15, 17.
             RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_b(w, k, pl, st_));
             // Step 16: w_k = u_k - V_{k-1} r^(3) (FP64 into wb, split into column p).
@@ -359,7 +361,7 @@ cudaError_t enqueue_cycle_vdf(igs_ctx *ctx, Issuer &is, int m, int gs)
     }
     // Flush: gamma_{m+1} = ||w_{m+1}||, H_{m+1,m}, last L row, v_{m+1} = split(w_{m+1} / gamma).
     RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
-        igs::launch_dots_df_ex(w, m + 1, col(m), nullptr, true, true, true, st_, &pl));
+        igs::launch_dots_df_ex(w, m + 1, col(m), nullptr, true, true, st_, &pl));
     if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_flush(w, m, pl, st_));
     RUN(igs::KC_CYCLE, 16.0 * w.n, w.n, s, igs::launch_scale_df(w, wb, cold(m), nullptr, 1, true, st_));

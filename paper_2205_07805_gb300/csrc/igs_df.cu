@@ -31,30 +31,6 @@ namespace {
 
 __device__ __forceinline__ bool df_halted(const DevState *st) { return st->halt != 0; }
 
-// a = hi + lo + r, |r| <= 2^-47 |a| for 2^-100 <= |a| < 2^127 (integer and FP32 operations
-// only, none on the narrow FP64 pipe: the remaining 29 bits are rounded to 23 and turned
-// into a float exactly by placing them in the mantissa of 2^23 and subtracting 2^23; two
-// power-of-two scalings follow, exact unless lo is subnormal).
-__device__ __forceinline__ void df_split(double a, float &hi, float &lo)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
-    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
-    const unsigned sign = hw & 0x80000000u, ahw = hw & 0x7fffffffu;
-    // (hw:lw) << 3 puts the top 23 fraction bits in bits 22..0 and the low 9 exponent bits
-    // in bits 31..23; subtracting 384 << 23 turns FP64's exponent bias (1023) into FP32's
-    // (127) for every exponent of the FP32 normal range.
-    unsigned hb = (__funnelshift_l(lw, hw, 3) - 0xC0000000u) | sign;
-    hb = ahw < (897u << 20) ? sign : hb;                                // |a| < 2^-126: 0
-    hb = ahw >= (1150u << 20) ? (sign | 0x7f800000u) : hb;             // |a| >= 2^127: inf
-    hi = __uint_as_float(hb);
-    // the remaining 29 fraction bits times 2^(e - 1075) = rem * 2^-52 * (+-2^(e - 1023)),
-    // with rem rounded to a multiple of 64: ((rem + 32) >> 6) * 2^-46 * (+-2^(e - 1023))
-    const float scale = __uint_as_float(hb & 0xff800000u);
-    const unsigned r23 = ((lw & 0x1fffffffu) + 32u) >> 6;  // <= 2^23
-    const float fr = __fsub_rn(__uint_as_float(0x4B000000u | r23), 8388608.0f);
-    lo = __fmul_rn(__fmul_rn(fr, 0x1p-46f), scale);
-}
-
 // (S, s) += (ah + al) * (xh + xl): exact product of the high parts by FMA, cross terms in
 // FP32, TwoSum of the high part into S (the intrinsics are never contracted into FMAs).
 __device__ __forceinline__ void df_acc(float &S, float &s, float ah, float al, float xh, float xl)
@@ -125,7 +101,8 @@ __device__ __forceinline__ void cp_async16(double *dst, const double *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
 
-template <int NQ, bool VDF, bool X0DF>
+// VDF false: V and the vectors are FP64, split on the fly; true: all of them stored split.
+template <int NQ, bool VDF>
 __global__ void __launch_bounds__(kStreamThreads, kDotsBlocksPerSM)
 k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t rows,
           const double *__restrict__ x0, const double *__restrict__ x1, double *__restrict__ part,
@@ -193,12 +170,12 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
             float xh[NQ][2], xl[NQ][2];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                if (q == 0 && X0DF) {  // stored split: (hi, lo) of two rows
-                    const float4 xv = *reinterpret_cast<const float4 *>(src);
-                    xh[0][0] = xv.x;
-                    xl[0][0] = xv.y;
-                    xh[0][1] = xv.z;
-                    xl[0][1] = xv.w;
+                if (VDF) {  // stored split: (hi, lo) of two rows
+                    const float4 xv = *reinterpret_cast<const float4 *>(src + 64 * q);
+                    xh[q][0] = xv.x;
+                    xl[q][0] = xv.y;
+                    xh[q][1] = xv.z;
+                    xl[q][1] = xv.w;
                 } else {
                     const double2 xv = *reinterpret_cast<const double2 *>(src + 64 * q);
                     df_split(xv.x, xh[q][0], xl[q][0]);
@@ -500,11 +477,11 @@ cudaError_t launch_df_to_f64(double *V, int64_t count, int num_sms, cudaStream_t
 cudaError_t launch_dots_df(const Workspace &w, int p, const double *x0, const double *x1, bool check_halt,
                            cudaStream_t s, DotsPlan *plan_out)
 {
-    return launch_dots_df_ex(w, p, x0, x1, check_halt, false, false, s, plan_out);
+    return launch_dots_df_ex(w, p, x0, x1, check_halt, false, s, plan_out);
 }
 
 cudaError_t launch_dots_df_ex(const Workspace &w, int p, const double *x0, const double *x1, bool check_halt,
-                              bool vdf, bool x0df, cudaStream_t s, DotsPlan *plan_out)
+                              bool vdf, cudaStream_t s, DotsPlan *plan_out)
 {
     const DotsPlan pl = plan_dots(w, p);
     if (plan_out) *plan_out = pl;
@@ -515,22 +492,15 @@ cudaError_t launch_dots_df_ex(const Workspace &w, int p, const double *x0, const
     const int ch = check_halt ? 1 : 0;
     const size_t sm = kDfDotsSmem;
     const dim3 bl(kStreamThreads);
-    if (x1) {
-        if (vdf && x0df)
-            launch_k(false, k_dots_df<2, true, true>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, x1, w.part, st, ch);
-        else if (vdf)
-            launch_k(false, k_dots_df<2, true, false>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, x1, w.part, st, ch);
-        else
-            launch_k(false, k_dots_df<2, false, false>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, x1, w.part, st, ch);
-    } else {
-        const double *none = nullptr;
-        if (vdf && x0df)
-            launch_k(false, k_dots_df<1, true, true>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, none, w.part, st, ch);
-        else if (vdf)
-            launch_k(false, k_dots_df<1, true, false>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, none, w.part, st, ch);
-        else
-            launch_k(false, k_dots_df<1, false, false>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, none, w.part, st, ch);
-    }
+    const double *none = nullptr;
+    if (x1 && vdf)
+        launch_k(false, k_dots_df<2, true>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, x1, w.part, st, ch);
+    else if (x1)
+        launch_k(false, k_dots_df<2, false>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, x1, w.part, st, ch);
+    else if (vdf)
+        launch_k(false, k_dots_df<1, true>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, none, w.part, st, ch);
+    else
+        launch_k(false, k_dots_df<1, false>, grid, bl, sm, s, w.V, w.ld, p, n4, pl.rows, x0, none, w.part, st, ch);
     return cudaGetLastError();
 }
 
@@ -540,12 +510,10 @@ cudaError_t configure_df_kernels()
     const int dm = (int)kDfDotsSmem;
     const int um = (int)(kUpdSmemFixed + 2 * sizeof(float) * (kMaxRestart + 1));
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(k_dots_df<1, false, false>, A, dm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<2, false, false>, A, dm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<1, true, false>, A, dm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<2, true, false>, A, dm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<1, true, true>, A, dm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<2, true, true>, A, dm);
+    cudaError_t e = cudaFuncSetAttribute(k_dots_df<1, false>, A, dm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<2, false>, A, dm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<1, true>, A, dm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<2, true>, A, dm);
     // stage buffers (48 KiB) plus the coefficient splits of up to kMaxRestart + 1 columns
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_df<false>, A, um);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_df<true>, A, um);

@@ -56,6 +56,32 @@ inline cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// Double-float split of an FP64 value (the IGS_PREC_FP64_DF form, igs_df.cu; also used by the
+// SpMV when it writes a split copy of its output).
+// a = hi + lo + r, |r| <= 2^-47 |a| for 2^-100 <= |a| < 2^127 (integer and FP32 operations
+// only, none on the narrow FP64 pipe: the remaining 29 bits are rounded to 23 and turned
+// into a float exactly by placing them in the mantissa of 2^23 and subtracting 2^23; two
+// power-of-two scalings follow, exact unless lo is subnormal).
+__device__ __forceinline__ void df_split(double a, float &hi, float &lo)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const unsigned sign = hw & 0x80000000u, ahw = hw & 0x7fffffffu;
+    // (hw:lw) << 3 puts the top 23 fraction bits in bits 22..0 and the low 9 exponent bits
+    // in bits 31..23; subtracting 384 << 23 turns FP64's exponent bias (1023) into FP32's
+    // (127) for every exponent of the FP32 normal range.
+    unsigned hb = (__funnelshift_l(lw, hw, 3) - 0xC0000000u) | sign;
+    hb = ahw < (897u << 20) ? sign : hb;                                // |a| < 2^-126: 0
+    hb = ahw >= (1150u << 20) ? (sign | 0x7f800000u) : hb;             // |a| >= 2^127: inf
+    hi = __uint_as_float(hb);
+    // the remaining 29 fraction bits times 2^(e - 1075) = rem * 2^-52 * (+-2^(e - 1023)),
+    // with rem rounded to a multiple of 64: ((rem + 32) >> 6) * 2^-46 * (+-2^(e - 1023))
+    const float scale = __uint_as_float(hb & 0xff800000u);
+    const unsigned r23 = ((lw & 0x1fffffffu) + 32u) >> 6;  // <= 2^23
+    const float fr = __fsub_rn(__uint_as_float(0x4B000000u | r23), 8388608.0f);
+    lo = __fmul_rn(__fmul_rn(fr, 0x1p-46f), scale);
+}
+
 // Scalars of one solve, kept in device memory so that no step needs the host.
 struct DevState {
     double rho;        // ||r0|| of the current cycle
@@ -127,8 +153,9 @@ enum KClass { KC_SPMV = 0, KC_DOTS = 1, KC_UPDATE = 2, KC_SMALL = 3, KC_CYCLE = 
 
 // ---- launchers (enqueue on `s`; return cudaGetLastError()) ----
 // y = A x, or y = b - A x when b != nullptr.
+// With y_df, also its split copy (the double-float form).
 cudaError_t launch_spmv(const Workspace &w, const double *x, double *y, const double *b,
-                        bool check_halt, cudaStream_t s);
+                        bool check_halt, cudaStream_t s, float2 *y_df = nullptr);
 // Partial sums part[rb*(nq*p) + q*p + c] = sum over row block rb of V[:,c] . X_q, q < nq.
 cudaError_t launch_dots(const Workspace &w, int p, const double *x0, const double *x1,
                         bool check_halt, cudaStream_t s, DotsPlan *plan_out);
@@ -153,13 +180,12 @@ cudaError_t launch_update_df(const Workspace &w, int p, const double *coef, doub
 // The split basis (vdf: each basis element stored as its FP32 (hi, lo) pair in V's bytes) of
 // the double-float Alg. 4.1 cycle.  Update: also out_df = split(out) when given; with
 // norm_last and vdf the FP64 w comes from wsrc and split(w * inv_gamma) goes to column p-1;
-// neg_coef and p_from_state as in launch_update.  Multi-dot: vdf reads V split; x0df reads
-// x0 split (x1, when given, is FP64).
+// neg_coef and p_from_state as in launch_update.  Multi-dot: vdf reads V, x0 and x1 split.
 cudaError_t launch_update_df_ex(const Workspace &w, int p, const double *coef, bool neg_coef, double alpha,
                                 const double *src, double *out, float2 *out_df, const double *wsrc, bool norm_last,
                                 bool p_from_state, bool vdf, cudaStream_t s);
 cudaError_t launch_dots_df_ex(const Workspace &w, int p, const double *x0, const double *x1, bool check_halt,
-                              bool vdf, bool x0df, cudaStream_t s, DotsPlan *plan_out);
+                              bool vdf, cudaStream_t s, DotsPlan *plan_out);
 // dst_df = split(src * st->inv_rho (which 0) or st->inv_gamma (which 1)), dst64 (nullable) the
 // same in FP64.
 cudaError_t launch_scale_df(const Workspace &w, const double *src, float2 *dst_df, double *dst64, int which,

@@ -330,7 +330,7 @@ __device__ void last_warp_sumsq(const double *__restrict__ col, int len, double 
 __global__ void __launch_bounds__(kStreamThreads)
 k_spmv_rows(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ colind,
             const double *__restrict__ val, const double *__restrict__ x, double *__restrict__ y,
-            const double *__restrict__ b, const DevState *st, int check_halt)
+            const double *__restrict__ b, const DevState *st, int check_halt, float2 *__restrict__ ydf)
 {
     IGS_PDL_ENTER();
     if (check_halt && halted(st)) return;
@@ -345,7 +345,13 @@ k_spmv_rows(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ c
         }
         if (q < hi) s0 = fma(val[q], x[colind[q]], s0);
         const double s = s0 + s1;
-        y[i] = b ? b[i] - s : s;
+        const double o = b ? b[i] - s : s;
+        y[i] = o;
+        if (ydf) {
+            float h, l;
+            df_split(o, h, l);
+            ydf[i] = make_float2(h, l);
+        }
     }
 }
 
@@ -356,7 +362,7 @@ k_spmv_rows(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ c
 __global__ void __launch_bounds__(kStreamThreads)
 k_spmv_sell(int64_t n, const int64_t *__restrict__ sell_off, const int *__restrict__ sell_col,
             const double *__restrict__ sell_val, const double *__restrict__ x, double *__restrict__ y,
-            const double *__restrict__ b, const DevState *st, int check_halt)
+            const double *__restrict__ b, const DevState *st, int check_halt, float2 *__restrict__ ydf)
 {
     IGS_PDL_ENTER();
     if (check_halt && halted(st)) return;
@@ -379,14 +385,20 @@ k_spmv_sell(int64_t n, const int64_t *__restrict__ sell_off, const int *__restri
         if (c0 >= 0) s0 = fma(vs[32 * k], x[c0], s0);
     }
     const double s = s0 + s1;
-    y[i] = b ? b[i] - s : s;
+    const double o = b ? b[i] - s : s;
+    y[i] = o;
+    if (ydf) {  // the split copy the double-float form's multi-dot reads
+        float h, l;
+        df_split(o, h, l);
+        ydf[i] = make_float2(h, l);
+    }
 }
 
 // Warp per row: long rows (dense or wide-band matrices).
 __global__ void __launch_bounds__(kStreamThreads)
 k_spmv_warp(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ colind,
             const double *__restrict__ val, const double *__restrict__ x, double *__restrict__ y,
-            const double *__restrict__ b, const DevState *st, int check_halt)
+            const double *__restrict__ b, const DevState *st, int check_halt, float2 *__restrict__ ydf)
 {
     IGS_PDL_ENTER();
     if (check_halt && halted(st)) return;
@@ -403,7 +415,15 @@ k_spmv_warp(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ c
         if (q < hi) s0 = fma(val[q], x[colind[q]], s0);
         double s = s0 + s1;
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) y[i] = b ? b[i] - s : s;
+        if (lane == 0) {
+            const double o = b ? b[i] - s : s;
+            y[i] = o;
+            if (ydf) {
+                float h, l;
+                df_split(o, h, l);
+                ydf[i] = make_float2(h, l);
+            }
+        }
     }
 }
 
@@ -1298,7 +1318,7 @@ DotsPlan plan_dots_slots(const Workspace &w, int p, int slots)
 }
 
 cudaError_t launch_spmv(const Workspace &w, const double *x, double *y, const double *b,
-                        bool check_halt, cudaStream_t s)
+                        bool check_halt, cudaStream_t s, float2 *y_df)
 {
     // one thread (short rows) or one warp (long rows) per row, so that every row's three
     // dependent loads (row pointer, column index, x) are in flight at once
@@ -1307,13 +1327,13 @@ cudaError_t launch_spmv(const Workspace &w, const double *x, double *y, const do
     const int grid = (int)(want < (int64_t)1 << 30 ? want : (int64_t)1 << 30);
     if (w.spmv_warp_rows)
         launch_k(false, k_spmv_warp, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.rowptr, w.colind, w.val, x, y, b, w.st,
-                                                    check_halt);
+                 check_halt, y_df);
     else if (w.sell_col)
         launch_k(false, k_spmv_sell, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.sell_off, w.sell_col, w.sell_val, x, y,
-                 b, (const DevState *)w.st, check_halt ? 1 : 0);
+                 b, (const DevState *)w.st, check_halt ? 1 : 0, y_df);
     else
         launch_k(false, k_spmv_rows, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.rowptr, w.colind, w.val, x, y, b, w.st,
-                                                    check_halt);
+                 check_halt, y_df);
     return cudaGetLastError();
 }
 
@@ -1486,14 +1506,14 @@ cudaError_t estimate_norm2(const Workspace &w, const int *at_rowptr, const int *
     for (int it = 0; it < iters; ++it) {
         if (w.spmv_warp_rows) {
             launch_k(false, k_spmv_warp, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.rowptr, w.colind, w.val, w.t, w.z,
-                                                        nullptr, w.st, 0);
+                                                        nullptr, w.st, 0, (float2 *)nullptr);
             launch_k(false, k_spmv_warp, dim3(grid), dim3(kStreamThreads), 0, s, w.n, at_rowptr, at_colind, at_val, w.z, w.u,
-                                                        nullptr, w.st, 0);
+                                                        nullptr, w.st, 0, (float2 *)nullptr);
         } else {
             launch_k(false, k_spmv_rows, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.rowptr, w.colind, w.val, w.t, w.z,
-                                                        nullptr, w.st, 0);
+                                                        nullptr, w.st, 0, (float2 *)nullptr);
             launch_k(false, k_spmv_rows, dim3(grid), dim3(kStreamThreads), 0, s, w.n, at_rowptr, at_colind, at_val, w.z, w.u,
-                                                        nullptr, w.st, 0);
+                                                        nullptr, w.st, 0, (float2 *)nullptr);
         }
         launch_k(false, k_norms, dim3(w.num_sms), dim3(kStreamThreads), 0, s, w.n, w.u, nullptr, nullptr, w.part, 1);
         launch_k(false, k_power_norm, dim3(1), dim3(kSmallThreads), 0, s, w.part, w.num_sms, w.y);

@@ -300,11 +300,6 @@ k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ 
     for (int64_t pr = pr_lo + t; pr < pr_hi; pr += blockDim.x) {
         const int64_t i = 2 * pr;
         const double *vi = V + i;
-        // this row pair's FP64 operands, loaded before the column stream so that their latency
-        // is not exposed at the end
-        const double2 sv = *reinterpret_cast<const double2 *>(src + i);
-        double2 wv = make_double2(0.0, 0.0);
-        if (norm_last) wv = *reinterpret_cast<const double2 *>((VDF ? wsrc : V + (int64_t)(p - 1) * ld) + i);
         auto issue = [&](int j) {
             if (j < nchunks) {
                 double2 *dst = stg + (size_t)(j % kUpdStages) * kUpdChunk * kStreamThreads + t;
@@ -350,7 +345,7 @@ k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ 
         }
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         if (norm_last) {
-            double2 v = wv;
+            double2 v = *reinterpret_cast<const double2 *>((VDF ? wsrc : V + (int64_t)(p - 1) * ld) + i);
             v.x *= a;
             v.y *= a;
             float h0, l0, h1, l1;
@@ -363,6 +358,7 @@ k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ 
             df_acc(S0, s0, h0, l0, scf[p - 1], scf[2 * p - 1]);
             df_acc(S1, s1, h1, l1, scf[p - 1], scf[2 * p - 1]);
         }
+        const double2 sv = *reinterpret_cast<const double2 *>(src + i);
         double2 o;
         o.x = fma(a, sv.x, -(f2d_bits(S0) + f2d_bits(s0)));
         o.y = fma(a, sv.y, -(f2d_bits(S1) + f2d_bits(s1)));

@@ -954,8 +954,15 @@ def main():
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     total_ms = sum(v["ms"] for v in prof.values())
+    # the FP64 FMA rate this GPU actually sustains (igs_probe_fma, outside the timed region)
+    try:
+        probe_tf = 2 * pkg.probe_fma(local)["fp64_fma_per_s"] / 1e12
+    except Exception:
+        probe_tf = None
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak_tflops,
+                "probe_fp64_tflops": probe_tf,
+                "frac_of_probe": achieved_tflops / probe_tf if probe_tf else None,
                 # DRAM bytes per launch: ncu's dram__bytes_read.sum + dram__bytes_write.sum of the
                 # two multi-dots at p = 49 on this workload were 1.011 (k_dots<2>) and 1.013
                 # (k_dots<1>) times their algorithmic bytes; scaled to the average launch

@@ -819,7 +819,7 @@ def main():
         clk = clocks.stop()
         f64 = statistics.median(r["fp64_fma_per_s"] for r in reps)
         f32 = statistics.median(r["fp32_fma_per_s"] for r in reps)
-        line = {"probe": "igs_probe_fma: every SM full of independent FMA chains, median of 5",
+        line = {"probe": "igs_probe_fma: best of 2/4/8 blocks per SM x 4/8/16 FMA chains per thread, median of 5 calls",
                 "fp64_tflops": 2 * f64 / 1e12, "fp32_tflops": 2 * f32 / 1e12,
                 "fp64_fma_per_clk_per_sm_at_max_clock": f64 / (torch.cuda.get_device_properties(local).multi_processor_count
                                                                * 2070e6),

@@ -336,6 +336,10 @@ def run_batched(args, pkg, torch, local, dist, with_one_at_a_time=True):
     ns = [A.n for A in As]
     nnzs = [A.nnz for A in As]
     fma = batch_fma(ns, nnzs, steps_b, cycles_b, BATCH_M, args.gs)
+    try:
+        probe_tf = 2 * pkg.probe_fma(local)["fp64_fma_per_s"] / 1e12  # outside the timed region
+    except Exception:
+        probe_tf = None
     # DRAM bytes per launch: the ncu capture of the same kernel on the first 1024 systems of
     # this generator (profiles/k_batch_solve_banded1024_m50.md: 42.4 GB read + 0.90 GB written)
     # scaled by the FMA work of this batch over that of those 1024 systems (each system's
@@ -357,6 +361,7 @@ def run_batched(args, pkg, torch, local, dist, with_one_at_a_time=True):
                        "tuned": not args.batch_launch, "tune_table_ms": info["tune"], "create_s": t_create},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "traffic_source": traffic_src,
+                         "probe_fp64_tflops": probe_tf, "frac_of_probe": achieved / probe_tf if probe_tf else None,
                          "kernel": "k_batch_solve (persistent; all steps of Alg. 4.1 per system)",
                          "flops_per_launch": 2 * fma,
                          "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2070 MHz"},

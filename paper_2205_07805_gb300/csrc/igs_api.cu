@@ -850,11 +850,20 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
                 // SELL form of it measured 33 % slower on the 3-D 7-point matrices)
                 const int64_t nsl = (n + 31) / 32;
                 std::vector<int64_t> soff((size_t)nsl + 1, 0);
+                int64_t wall = 0;
                 for (int64_t k = 0; k < nsl; ++k) {
                     int64_t wmax = 0;
                     for (int64_t i = 32 * k; i < std::min<int64_t>(n, 32 * k + 32); ++i)
                         wmax = std::max<int64_t>(wmax, rowptr[i + 1] - rowptr[i]);
                     soff[(size_t)k + 1] = soff[(size_t)k] + 32 * wmax;
+                    wall = std::max(wall, wmax);
+                }
+                // ELL (every slice as wide as the widest) when that is narrow and costs little
+                // padding: the SpMV then computes slice offsets instead of loading them
+                if (wall >= 1 && wall <= igs::kMaxEllWidth &&
+                    (double)(32 * wall * nsl) <= igs::kEllMaxPadding * (double)soff[(size_t)nsl]) {
+                    for (int64_t k = 0; k <= nsl; ++k) soff[(size_t)k] = 32 * wall * k;
+                    w.ell_width = (int)wall;
                 }
                 const int64_t ne = std::max<int64_t>(soff[(size_t)nsl], 1);
                 std::vector<int> scol((size_t)ne, -1);

@@ -26,6 +26,10 @@ constexpr int kUpdateBlocksPerSM = 4;
 // Largest restart length supported.  The small single-block steps hold L_p packed in shared
 // memory: 8 (5p + p(p-1)/2) bytes <= 227 KiB gives p <= 232.
 constexpr int kMaxRestart = 232;
+// Widest uniform slice the ELL SpMV handles, and the largest padding (relative to SELL-32)
+// accepted to use it.
+constexpr int kMaxEllWidth = 8;
+constexpr double kEllMaxPadding = 1.25;
 // Breakdown threshold factor: gamma <= 64 eps ||H(1:j, j)||.
 constexpr double kBreakdownFactor = 64.0 * 2.220446049250313e-16;
 
@@ -134,6 +138,9 @@ struct Workspace {
     const int64_t *sell_off = nullptr;
     const int *sell_col = nullptr;
     const double *sell_val = nullptr;
+    // > 0: every slice of the SELL-32 copy is this many entries wide (ELL; offset of slice k
+    // = 32 * ell_width * k, sell_off unused by the SpMV), 1..kMaxEllWidth
+    int ell_width = 0;
     int ldh() const { return mmax + 1; }
     int ldl() const { return mmax + 1; }
 };

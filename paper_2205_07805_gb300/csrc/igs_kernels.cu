@@ -394,6 +394,50 @@ k_spmv_sell(int64_t n, const int64_t *__restrict__ sell_off, const int *__restri
     }
 }
 
+// Thread per row over the ELL form of the SELL-32 copy (every slice W entries wide, padding
+// column -1): the slice offset is arithmetic, so a thread issues all W column-index and value
+// loads at once, then all its gathers of x, instead of waiting on the offset first.  The two
+// chains take the entries in the same order as k_spmv_rows / k_spmv_sell (bitwise the same sums).
+template <int W>
+__global__ void __launch_bounds__(kStreamThreads)
+k_spmv_ell(int64_t n, const int *__restrict__ col, const double *__restrict__ val, const double *__restrict__ x,
+           double *__restrict__ y, const double *__restrict__ b, const DevState *st, int check_halt,
+           float2 *__restrict__ ydf)
+{
+    IGS_PDL_ENTER();
+    if (check_halt && halted(st)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // the grid covers n
+    if (i >= n) return;
+    const int64_t base = (i >> 5) * (32 * W) + (i & 31);
+    int c[W];
+    double v[W], xv[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        c[k] = col[base + 32 * k];
+        v[k] = val[base + 32 * k];
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) xv[k] = c[k] >= 0 ? x[c[k]] : 0.0;
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        if (c[k] >= 0) {
+            if (k & 1)
+                s1 = fma(v[k], xv[k], s1);
+            else
+                s0 = fma(v[k], xv[k], s0);
+        }
+    }
+    const double s = s0 + s1;
+    const double o = b ? b[i] - s : s;
+    y[i] = o;
+    if (ydf) {
+        float h, l;
+        df_split(o, h, l);
+        ydf[i] = make_float2(h, l);
+    }
+}
+
 // Warp per row: long rows (dense or wide-band matrices).
 __global__ void __launch_bounds__(kStreamThreads)
 k_spmv_warp(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ colind,
@@ -1328,7 +1372,21 @@ cudaError_t launch_spmv(const Workspace &w, const double *x, double *y, const do
     if (w.spmv_warp_rows)
         launch_k(false, k_spmv_warp, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.rowptr, w.colind, w.val, x, y, b, w.st,
                  check_halt, y_df);
-    else if (w.sell_col)
+    else if (w.ell_width > 0) {
+        const dim3 g(grid), bl(kStreamThreads);
+        const DevState *st = w.st;
+        const int ch = check_halt ? 1 : 0;
+        switch (w.ell_width) {
+        case 1: launch_k(false, k_spmv_ell<1>, g, bl, 0, s, w.n, w.sell_col, w.sell_val, x, y, b, st, ch, y_df); break;
+        case 2: launch_k(false, k_spmv_ell<2>, g, bl, 0, s, w.n, w.sell_col, w.sell_val, x, y, b, st, ch, y_df); break;
+        case 3: launch_k(false, k_spmv_ell<3>, g, bl, 0, s, w.n, w.sell_col, w.sell_val, x, y, b, st, ch, y_df); break;
+        case 4: launch_k(false, k_spmv_ell<4>, g, bl, 0, s, w.n, w.sell_col, w.sell_val, x, y, b, st, ch, y_df); break;
+        case 5: launch_k(false, k_spmv_ell<5>, g, bl, 0, s, w.n, w.sell_col, w.sell_val, x, y, b, st, ch, y_df); break;
+        case 6: launch_k(false, k_spmv_ell<6>, g, bl, 0, s, w.n, w.sell_col, w.sell_val, x, y, b, st, ch, y_df); break;
+        case 7: launch_k(false, k_spmv_ell<7>, g, bl, 0, s, w.n, w.sell_col, w.sell_val, x, y, b, st, ch, y_df); break;
+        default: launch_k(false, k_spmv_ell<8>, g, bl, 0, s, w.n, w.sell_col, w.sell_val, x, y, b, st, ch, y_df); break;
+        }
+    } else if (w.sell_col)
         launch_k(false, k_spmv_sell, dim3(grid), dim3(kStreamThreads), 0, s, w.n, w.sell_off, w.sell_col, w.sell_val, x, y,
                  b, (const DevState *)w.st, check_halt ? 1 : 0, y_df);
     else

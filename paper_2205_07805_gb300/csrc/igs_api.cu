@@ -155,6 +155,7 @@ double upd_bytes(const igs::Workspace &w, int p) { return 8.0 * w.n * (p + 2); }
 cudaError_t enqueue_cycle32(igs_ctx *ctx, Issuer &is, int m, int gs);
 cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m, bool df);
 cudaError_t enqueue_cycle_vdf(igs_ctx *ctx, Issuer &is, int m, int gs);
+cudaError_t enqueue_cycle_1r_vdf(igs_ctx *ctx, Issuer &is, int m);
 
 // The block multi-dot of the FP64 cycles: FP64 FMAs, or double-float products on the FP32
 // pipes for the IGS_PREC_FP64_DF form (from kDfMinRows rows on; same partial-sum layout).
@@ -168,6 +169,7 @@ DotsLauncher dots_launcher(const igs::Workspace &w, bool df)
 // gs = 0 selects Alg. 4.2 (one-reduce); 1 or 2 Alg. 4.1 with that many GS iterations.
 cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
 {
+    if (gs == 0 && prec == IGS_PREC_FP64_DF && igs::dots_df_applies(ctx->w)) return enqueue_cycle_1r_vdf(ctx, is, m);
     if (gs == 0) return enqueue_cycle_1r(ctx, is, m, prec == IGS_PREC_FP64_DF);
     if (prec == IGS_PREC_FP32_IR) return enqueue_cycle32(ctx, is, m, gs);
     if (prec == IGS_PREC_FP64_DF && igs::dots_df_applies(ctx->w)) return enqueue_cycle_vdf(ctx, is, m, gs);
@@ -365,6 +367,97 @@ cudaError_t enqueue_cycle_vdf(igs_ctx *ctx, Issuer &is, int m, int gs)
     if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_flush(w, m, pl, st_));
     RUN(igs::KC_CYCLE, 16.0 * w.n, w.n, s, igs::launch_scale_df(w, wb, cold(m), nullptr, 1, true, st_));
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));
+    // Least squares y = argmin ||rho e1 - H y||, x_m = x_0 + V_m y_m (FP64).
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_lsq(w, m, st_));
+    RUN(igs::KC_CYCLE, upd_bytes(w, m), 2.0 * w.n * m, s, igs::launch_xupdate_vdf(w, st_));
+    // r = b - A x, ||r||, ||x||, beta(x).
+    RUN(igs::KC_CYCLE, spmv_bytes(w) + 8.0 * w.n, 2.0 * w.nnz, s, igs::launch_spmv(w, w.x, w.r, w.b, false, st_));
+    int nblk = 0;
+    RUN(igs::KC_CYCLE, 16.0 * w.n, 4.0 * w.n, s, igs::launch_norms(w, w.r, w.x, nullptr, &nblk, st_));
+    RUN(igs::KC_CYCLE, 0, 0, s, igs::launch_beta(w, nblk, st_));
+#undef RUN
+    return cudaSuccess;
+}
+
+// One Alg. 4.2 cycle of the double-float form (n >= kDfMinRows): the FP64 Alg. 4.2 cycle's
+// steps and single-block kernels on the split basis of enqueue_cycle_vdf.  The current u is
+// kept in FP64 in w.t (the SpMV input and the source of v = (u - V r^(2)) / gamma) and split in
+// basis column nb (the one reduction reads it there, where the FP64 cycle keeps u); z = A u in
+// FP64 and split (w.u's bytes: Alg. 4.2 keeps no other u).
+cudaError_t enqueue_cycle_1r_vdf(igs_ctx *ctx, Issuer &is, int m)
+{
+    const igs::Workspace &w = ctx->w;
+    cudaStream_t s = is.s;
+    const int64_t ld = w.ld;
+    auto col = [&](int c) { return w.V + (int64_t)c * ld; };
+    auto cold = [&](int c) { return reinterpret_cast<float2 *>(w.V + (int64_t)c * ld); };
+    double *wu = w.t;                               // FP64 u
+    float2 *zd = reinterpret_cast<float2 *>(w.u);   // split z
+    const double *zdd = reinterpret_cast<const double *>(zd);
+    cudaError_t e;
+#define RUN(cls, bytes, flops, on, expr)                                          \
+    do {                                                                          \
+        e = is.run((cls), (bytes), (flops), [&](cudaStream_t st_) { (void)st_; return (expr); }, (on)); \
+        if (e != cudaSuccess) return e;                                           \
+    } while (0)
+    // Step 1: rho = ||r0||, v1 = r0 / rho (split into the basis, FP64 into wu).
+    RUN(igs::KC_CYCLE, 0, 0, s, igs::launch_cycle_start(w, 0, st_));
+    RUN(igs::KC_CYCLE, 16.0 * w.n, w.n, s, igs::launch_scale_df(w, w.r, cold(0), wu, 0, false, st_));
+    // Step 2: w2 = A v1, H11 = v1^T w2, u_2 = w2 - v1 H11 (FP64 into wu, split into column 1).
+    igs::DotsPlan pl{};
+    RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wu, w.z, nullptr, false, st_, zd));
+    RUN(igs::KC_DOTS, dots_bytes(w, 1, 1), 2.0 * w.n, s, igs::launch_dots_df_ex(w, 1, zdd, nullptr, false, true, st_, &pl));
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_prime(w, pl, st_));
+    RUN(igs::KC_UPDATE, upd_bytes(w, 1), 2.0 * w.n, s,
+        igs::launch_update_df_ex(w, 1, w.r1v, false, 1.0, w.z, wu, cold(1), nullptr, false, false, true, st_));
+
+    bool pending_join = false;
+    auto join_side = [&]() -> cudaError_t {
+        if (pending_join && is.capture) {
+            cudaError_t ee = cudaStreamWaitEvent(s, ctx->ev_join, 0);
+            if (ee != cudaSuccess) return ee;
+        }
+        pending_join = false;
+        return cudaSuccess;
+    };
+    auto fork_givens = [&](int j) -> cudaError_t {
+        cudaStream_t on = s;
+        if (is.capture) {
+            cudaError_t ee = cudaEventRecord(ctx->ev_fork, s);
+            if (ee == cudaSuccess) ee = cudaStreamWaitEvent(is.side, ctx->ev_fork, 0);
+            if (ee != cudaSuccess) return ee;
+            on = is.side;
+        }
+        cudaError_t ee = is.run(igs::KC_SMALL, 0, 0, [&](cudaStream_t st_) { return igs::launch_givens(w, j, st_); }, on);
+        if (ee != cudaSuccess) return ee;
+        if (is.capture) {
+            ee = cudaEventRecord(ctx->ev_join, is.side);
+            if (ee != cudaSuccess) return ee;
+            pending_join = true;
+        }
+        return cudaSuccess;
+    };
+    for (int k = 3; k <= m + 1; ++k) {
+        const int nb = k - 2;
+        // Step 4: A u_{k-1} (FP64 u; z in FP64 and split), then the one reduction
+        // [V_nb, u]^T [u, A u] over the split basis (u is its column nb).
+        RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wu, w.z, nullptr, true, st_, zd));
+        RUN(igs::KC_DOTS, dots_bytes(w, nb + 1, 2), 4.0 * w.n * (nb + 1), s,
+            igs::launch_dots_df_ex(w, nb + 1, col(nb), zdd, true, true, st_, &pl));
+        if ((e = join_side()) != cudaSuccess) return e;
+        // Steps 5-9, 12, 14, 15: column nb-1 complete; its Givens rotation on the side.
+        RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, nb, false, pl, st_));
+        if ((e = fork_givens(nb - 1)) != cudaSuccess) return e;
+        // Steps 10-11, 13: v_{k-1} and u_k in one pass over the split basis.
+        RUN(igs::KC_UPDATE, 8.0 * w.n * (nb + 4), 4.0 * w.n * nb, s, igs::launch_update_1r_df(w, nb, w.z, wu, false, st_));
+    }
+    // Flush: the reduction of u_{m+1} (no product), column m-1 complete, v_{m+1}.
+    RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
+        igs::launch_dots_df_ex(w, m + 1, col(m), nullptr, true, true, st_, &pl));
+    if ((e = join_side()) != cudaSuccess) return e;
+    RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, m, true, pl, st_));
+    RUN(igs::KC_UPDATE, 8.0 * w.n * (m + 2), 2.0 * w.n * m, s, igs::launch_update_1r_df(w, m, w.z, wu, true, st_));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));
     // Least squares y = argmin ||rho e1 - H y||, x_m = x_0 + V_m y_m (FP64).
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_lsq(w, m, st_));
@@ -1158,8 +1251,8 @@ int igs_arnoldi_ex(igs_ctx *ctx, const double *r0, int m, int method, int gs, in
             igs::DevState hs{};
             if ((rc = read_state(ctx, &hs)) != IGS_OK) return rc;
             const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-            if (V && precision == IGS_PREC_FP64_DF && gs != 0 && igs::dots_df_applies(w)) {
-                // the double-float Alg. 4.1 cycle keeps the basis split: hand it out in FP64
+            if (V && precision == IGS_PREC_FP64_DF && igs::dots_df_applies(w)) {
+                // the double-float cycles keep the basis split: hand it out in FP64
                 CK(igs::launch_df_to_f64(w.V, w.ld * (int64_t)(m + 1), w.num_sms, ctx->stream));
                 ctx->launches += 1;
             }

@@ -372,6 +372,103 @@ k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ 
     }
 }
 
+// Alg. 4.2's fused update (steps 10-11 and 13) on the split basis, double-float: per row
+//   v_{k-1} = (u - V_nb r^(2)) / gamma        (split into column nb, where split(u) was)
+//   u_k     = z / gamma - V_nb r^(1) - v_{k-1} r^(1)_nb   (FP64 into wu, split into column nb+1)
+// with u taken in FP64 from wu (each thread reads its rows of wu before writing them) and the
+// two sums over the nb split columns accumulated in double-float (two products per basis
+// element, one pass over V).  vonly (the flush): v_{k-1} only.  Same row ownership and
+// column staging as k_update_df.
+__global__ void __launch_bounds__(kStreamThreads, kUpdateBlocksPerSM)
+k_update_1r_df(double *V, int64_t ld, int nb, int64_t n, const double *__restrict__ r2,
+               const double *__restrict__ r1, const double *__restrict__ z, double *wu, int vonly,
+               const DevState *st)
+{
+    IGS_PDL_ENTER();
+    if (df_halted(st)) return;
+    extern __shared__ double usm[];
+    double2 *stg = reinterpret_cast<double2 *>(usm);
+    float *sc = reinterpret_cast<float *>(usm + kUpdSmemFixed / sizeof(double));
+    float *r2h = sc, *r2l = sc + nb, *r1h = sc + 2 * nb, *r1l = sc + 3 * nb;
+    for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+        float h, l;
+        df_split(r2[c], h, l);
+        r2h[c] = h;
+        r2l[c] = l;
+        df_split(vonly ? 0.0 : r1[c], h, l);
+        r1h[c] = h;
+        r1l[c] = l;
+    }
+    __syncthreads();
+    const double ig = st->inv_gamma;
+    const double r1nb = vonly ? 0.0 : r1[nb];
+    const int nchunks = (nb + kUpdChunk - 1) / kUpdChunk;
+    const int64_t npairs = (n + 1) >> 1;
+    const int64_t ppb = (npairs + gridDim.x - 1) / gridDim.x;
+    const int64_t pr_lo = (int64_t)blockIdx.x * ppb;
+    const int64_t pr_hi = pr_lo + ppb < npairs ? pr_lo + ppb : npairs;
+    const int t = threadIdx.x;
+    for (int64_t pr = pr_lo + t; pr < pr_hi; pr += blockDim.x) {
+        const int64_t i = 2 * pr;
+        const double *vi = V + i;
+        auto issue = [&](int j) {
+            if (j < nchunks) {
+                double2 *dst = stg + (size_t)(j % kUpdStages) * kUpdChunk * kStreamThreads + t;
+#pragma unroll
+                for (int q = 0; q < kUpdChunk; ++q) {
+                    const int c = j * kUpdChunk + q;
+                    if (c < nb) {
+                        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + q * kStreamThreads);
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(vi + (int64_t)c * ld)
+                                     : "memory");
+                    }
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+#pragma unroll
+        for (int j = 0; j < kUpdStages - 1; ++j) issue(j);
+        float A0 = 0.f, a0 = 0.f, A1 = 0.f, a1 = 0.f, B0 = 0.f, b0 = 0.f, B1 = 0.f, b1 = 0.f;
+        for (int j = 0; j < nchunks; ++j) {
+            issue(j + kUpdStages - 1);
+            asm volatile("cp.async.wait_group %0;" ::"n"(kUpdStages - 1) : "memory");
+            const double2 *cur = stg + (size_t)(j % kUpdStages) * kUpdChunk * kStreamThreads + t;
+#pragma unroll
+            for (int q = 0; q < kUpdChunk; ++q) {
+                const int c = j * kUpdChunk + q;
+                if (c < nb) {
+                    const float4 v = *reinterpret_cast<const float4 *>(cur + q * kStreamThreads);
+                    df_acc(A0, a0, v.x, v.y, r2h[c], r2l[c]);
+                    df_acc(A1, a1, v.z, v.w, r2h[c], r2l[c]);
+                    if (!vonly) {
+                        df_acc(B0, b0, v.x, v.y, r1h[c], r1l[c]);
+                        df_acc(B1, b1, v.z, v.w, r1h[c], r1l[c]);
+                    }
+                }
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        const double2 u = *reinterpret_cast<const double2 *>(wu + i);
+        double2 vn;
+        vn.x = (u.x - (f2d_bits(A0) + f2d_bits(a0))) * ig;
+        vn.y = (u.y - (f2d_bits(A1) + f2d_bits(a1))) * ig;
+        float h0, l0, h1, l1;
+        df_split(vn.x, h0, l0);
+        df_split(vn.y, h1, l1);
+        *reinterpret_cast<float4 *>(V + (int64_t)nb * ld + i) = make_float4(h0, l0, h1, l1);
+        if (!vonly) {
+            const double2 zz = *reinterpret_cast<const double2 *>(z + i);
+            double2 un;
+            un.x = fma(zz.x, ig, -((f2d_bits(B0) + f2d_bits(b0)) + vn.x * r1nb));
+            un.y = fma(zz.y, ig, -((f2d_bits(B1) + f2d_bits(b1)) + vn.y * r1nb));
+            *reinterpret_cast<double2 *>(wu + i) = un;
+            df_split(un.x, h0, l0);
+            df_split(un.y, h1, l1);
+            *reinterpret_cast<float4 *>(V + (int64_t)(nb + 1) * ld + i) = make_float4(h0, l0, h1, l1);
+        }
+    }
+}
+
 // dst_df[i] = split(src[i] * scale) and, when dst64 is given, dst64[i] = src[i] * scale, with
 // scale = st->inv_rho (which = 0) or st->inv_gamma (which = 1): v_1 = r_0 / rho at a cycle's
 // start and the flush's v_{m+1} = w_{m+1} / gamma into the split basis.
@@ -448,6 +545,14 @@ cudaError_t launch_update_df_ex(const Workspace &w, int p, const double *coef, b
     return cudaGetLastError();
 }
 
+cudaError_t launch_update_1r_df(const Workspace &w, int nb, const double *z, double *wu, bool vonly, cudaStream_t s)
+{
+    const size_t smem = kUpdSmemFixed + 4 * sizeof(float) * (size_t)(nb + 1);
+    launch_k(false, k_update_1r_df, dim3(w.num_sms * kUpdateBlocksPerSM), dim3(kStreamThreads), smem, s, w.V, w.ld,
+             nb, w.n, (const double *)w.r2v, (const double *)w.r1v, z, wu, vonly ? 1 : 0, (const DevState *)w.st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scale_df(const Workspace &w, const double *src, float2 *dst_df, double *dst64, int which,
                             bool check_halt, cudaStream_t s)
 {
@@ -513,6 +618,8 @@ cudaError_t configure_df_kernels()
     // stage buffers (48 KiB) plus the coefficient splits of up to kMaxRestart + 1 columns
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_df<false>, A, um);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_df<true>, A, um);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_update_1r_df, A, (int)(kUpdSmemFixed + 4 * sizeof(float) * (kMaxRestart + 2)));
     return e;
 }
 

@@ -197,6 +197,10 @@ cudaError_t launch_dots_df_ex(const Workspace &w, int p, const double *x0, const
 // same in FP64.
 cudaError_t launch_scale_df(const Workspace &w, const double *src, float2 *dst_df, double *dst64, int which,
                             bool check_halt, cudaStream_t s);
+// Alg. 4.2's fused update on the split basis (v_{k-1} split into column nb; unless vonly, the
+// next u in FP64 into wu, which holds u on entry, and split into column nb+1).
+cudaError_t launch_update_1r_df(const Workspace &w, int nb, const double *z, double *wu, bool vonly,
+                                cudaStream_t s);
 // x += V y over the split basis in FP64 (p = st->ncols).
 cudaError_t launch_xupdate_vdf(const Workspace &w, cudaStream_t s);
 // In place: count split elements of V back to FP64.

@@ -226,12 +226,14 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
 
     for (int k = 3; k <= m + 1; ++k) {
         const int p = k - 1;
+        // the previous column's Givens kernel (side branch) is complete before this
+        // column's step kernel reads its stop decision
+        if ((e = join_side()) != cudaSuccess) return e;
         double *wv = col(p - 1);
         // Step 4: v_k = A w_{k-1}.
         RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wv, w.z, nullptr, true, st_));
         // Step 5: [V_{k-2}, w_{k-1}]^T [w_{k-1}, v_k] (block partial sums).
         RUN(igs::KC_DOTS, dots_bytes(w, p, 2), 4.0 * w.n * p, s, dots(w, p, wv, w.z, true, st_, &pl));
-        if ((e = join_side()) != cudaSuccess) return e;
         // Steps 6-12 (+ step 17 for one iteration).
         RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_a(w, k, gs, pl, st_));
         // Givens least squares for the column completed by step 6 (column k-2, 1-based).
@@ -251,9 +253,9 @@ cudaError_t enqueue_cycle(igs_ctx *ctx, Issuer &is, int m, int gs, int prec)
         }
     }
     // Flush: gamma_{m+1} = ||w_{m+1}||, H_{m+1,m}, last L row, v_{m+1} = w_{m+1}/gamma.
+    if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
         dots(w, m + 1, col(m), nullptr, true, st_, &pl));
-    if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_flush(w, m, pl, st_));
     RUN(igs::KC_CYCLE, 16.0 * w.n, w.n, s, igs::launch_scale(w, col(m), col(m), 1, true, st_));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));
@@ -335,12 +337,14 @@ cudaError_t enqueue_cycle_vdf(igs_ctx *ctx, Issuer &is, int m, int gs)
 
     for (int k = 3; k <= m + 1; ++k) {
         const int p = k - 1;
+        // the previous column's Givens kernel (side branch) is complete before this
+        // column's step kernel reads its stop decision
+        if ((e = join_side()) != cudaSuccess) return e;
         // Step 4: v_k = A w_{k-1} (FP64 w; z in FP64 and split).
         RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wb, w.z, nullptr, true, st_, zd));
         // Step 5: [V_{k-2}, w_{k-1}]^T [w_{k-1}, v_k]: the split basis (w is its column p-1) and z.
         RUN(igs::KC_DOTS, dots_bytes(w, p, 2), 4.0 * w.n * p, s,
             igs::launch_dots_df_ex(w, p, col(p - 1), zdd, true, true, st_, &pl));
-        if ((e = join_side()) != cudaSuccess) return e;
         // Steps 6-12 (+ step 17 for one iteration).
         RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_a(w, k, gs, pl, st_));
         if ((e = fork_givens(k - 3)) != cudaSuccess) return e;
@@ -362,9 +366,9 @@ cudaError_t enqueue_cycle_vdf(igs_ctx *ctx, Issuer &is, int m, int gs)
         }
     }
     // Flush: gamma_{m+1} = ||w_{m+1}||, H_{m+1,m}, last L row, v_{m+1} = split(w_{m+1} / gamma).
+    if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
         igs::launch_dots_df_ex(w, m + 1, col(m), nullptr, true, true, st_, &pl));
-    if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_flush(w, m, pl, st_));
     RUN(igs::KC_CYCLE, 16.0 * w.n, w.n, s, igs::launch_scale_df(w, wb, cold(m), nullptr, 1, true, st_));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));
@@ -440,12 +444,14 @@ cudaError_t enqueue_cycle_1r_vdf(igs_ctx *ctx, Issuer &is, int m)
     };
     for (int k = 3; k <= m + 1; ++k) {
         const int nb = k - 2;
+        // the previous column's Givens kernel (side branch) is complete before this
+        // column's step kernel reads its stop decision
+        if ((e = join_side()) != cudaSuccess) return e;
         // Step 4: A u_{k-1} (FP64 u; z in FP64 and split), then the one reduction
         // [V_nb, u]^T [u, A u] over the split basis (u is its column nb).
         RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wu, w.z, nullptr, true, st_, zd));
         RUN(igs::KC_DOTS, dots_bytes(w, nb + 1, 2), 4.0 * w.n * (nb + 1), s,
             igs::launch_dots_df_ex(w, nb + 1, col(nb), zdd, true, true, st_, &pl));
-        if ((e = join_side()) != cudaSuccess) return e;
         // Steps 5-9, 12, 14, 15: column nb-1 complete; its Givens rotation on the side.
         RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, nb, false, pl, st_));
         if ((e = fork_givens(nb - 1)) != cudaSuccess) return e;
@@ -453,9 +459,9 @@ cudaError_t enqueue_cycle_1r_vdf(igs_ctx *ctx, Issuer &is, int m)
         RUN(igs::KC_UPDATE, 8.0 * w.n * (nb + 4), 4.0 * w.n * nb, s, igs::launch_update_1r_df(w, nb, w.z, wu, false, st_));
     }
     // Flush: the reduction of u_{m+1} (no product), column m-1 complete, v_{m+1}.
+    if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
         igs::launch_dots_df_ex(w, m + 1, col(m), nullptr, true, true, st_, &pl));
-    if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, m, true, pl, st_));
     RUN(igs::KC_UPDATE, 8.0 * w.n * (m + 2), 2.0 * w.n * m, s, igs::launch_update_1r_df(w, m, w.z, wu, true, st_));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));
@@ -531,12 +537,14 @@ cudaError_t enqueue_cycle32(igs_ctx *ctx, Issuer &is, int m, int gs)
 
     for (int k = 3; k <= m + 1; ++k) {
         const int p = k - 1;
+        // the previous column's Givens kernel (side branch) is complete before this
+        // column's step kernel reads its stop decision
+        if ((e = join_side()) != cudaSuccess) return e;
         float *wv = col(p - 1);
         // Step 4: z = A w_{k-1} (FP32).
         RUN(igs::KC_SPMV, spmv32b, 2.0 * w.nnz, s, igs::launch_spmv32(w, wv, w.z32, st_));
         // Step 5: [V_{k-2}, w_{k-1}]^T [w_{k-1}, z] (FP32 chunks, FP64 partial sums).
         RUN(igs::KC_DOTS, dots32b(p, 2), 4.0 * w.n * p, s, igs::launch_dots32(w, p, wv, w.z32, st_, &pl));
-        if ((e = join_side()) != cudaSuccess) return e;
         // Steps 6-12 (+ step 17 for one iteration), FP64.
         RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_a(w, k, gs, pl, st_));
         if ((e = fork_givens(k - 3)) != cudaSuccess) return e;
@@ -555,9 +563,9 @@ cudaError_t enqueue_cycle32(igs_ctx *ctx, Issuer &is, int m, int gs)
         }
     }
     // Flush: gamma_{m+1} = ||w_{m+1}||, H_{m+1,m}, last L row, v_{m+1} = w_{m+1}/gamma.
+    if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_DOTS, dots32b(m + 1, 1), 2.0 * w.n * (m + 1), s,
         igs::launch_dots32(w, m + 1, col(m), nullptr, st_, &pl));
-    if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_flush(w, m, pl, st_));
     RUN(igs::KC_CYCLE, 8.0 * w.n, w.n, s, igs::launch_scale32(w, col(m), st_));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));
@@ -631,12 +639,14 @@ cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m, bool df)
     };
     for (int k = 3; k <= m + 1; ++k) {
         const int nb = k - 2;
+        // the previous column's Givens kernel (side branch) is complete before this
+        // column's step kernel reads its stop decision
+        if ((e = join_side()) != cudaSuccess) return e;
         double *u = col(nb);
         // Step 4: A u_{k-1}, then the one reduction [V_nb, u]^T [u, A u].
         RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, u, w.z, nullptr, true, st_));
         RUN(igs::KC_DOTS, dots_bytes(w, nb + 1, 2), 4.0 * w.n * (nb + 1), s,
             dots(w, nb + 1, u, w.z, true, st_, &pl));
-        if ((e = join_side()) != cudaSuccess) return e;
         // Steps 5-9, 12, 14, 15: column nb-1 complete; its Givens rotation on the side.
         RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, nb, false, pl, st_));
         if ((e = fork_givens(nb - 1)) != cudaSuccess) return e;
@@ -644,9 +654,9 @@ cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m, bool df)
         RUN(igs::KC_UPDATE, 8.0 * w.n * (nb + 4), 4.0 * w.n * nb, s, igs::launch_update_1r(w, nb, w.z, false, st_));
     }
     // Flush: the reduction of u_{m+1} (no product), column m-1 complete, v_{m+1}.
+    if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
         dots(w, m + 1, col(m), nullptr, true, st_, &pl));
-    if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, m, true, pl, st_));
     RUN(igs::KC_UPDATE, 8.0 * w.n * (m + 2), 2.0 * w.n * m, s, igs::launch_update_1r(w, m, w.z, true, st_));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));

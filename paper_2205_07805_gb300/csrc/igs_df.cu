@@ -537,10 +537,10 @@ cudaError_t launch_update_df_ex(const Workspace &w, int p, const double *coef, b
     const size_t smem = kUpdSmemFixed + 2 * sizeof(float) * (size_t)(pmax > 0 ? pmax : 1);
     const int grid = w.num_sms * kUpdateBlocksPerSM;
     if (vdf)
-        launch_k(false, k_update_df<true>, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef,
+        launch_k(w.pdl, k_update_df<true>, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef,
                  neg_coef ? 1 : 0, alpha, src, out, out_df, wsrc, norm_last ? 1 : 0, p_from_state ? 1 : 0, w.st, 1);
     else
-        launch_k(false, k_update_df<false>, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef,
+        launch_k(w.pdl, k_update_df<false>, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef,
                  neg_coef ? 1 : 0, alpha, src, out, out_df, wsrc, norm_last ? 1 : 0, p_from_state ? 1 : 0, w.st, 1);
     return cudaGetLastError();
 }
@@ -548,7 +548,7 @@ cudaError_t launch_update_df_ex(const Workspace &w, int p, const double *coef, b
 cudaError_t launch_update_1r_df(const Workspace &w, int nb, const double *z, double *wu, bool vonly, cudaStream_t s)
 {
     const size_t smem = kUpdSmemFixed + 4 * sizeof(float) * (size_t)(nb + 1);
-    launch_k(false, k_update_1r_df, dim3(w.num_sms * kUpdateBlocksPerSM), dim3(kStreamThreads), smem, s, w.V, w.ld,
+    launch_k(w.pdl, k_update_1r_df, dim3(w.num_sms * kUpdateBlocksPerSM), dim3(kStreamThreads), smem, s, w.V, w.ld,
              nb, w.n, (const double *)w.r2v, (const double *)w.r1v, z, wu, vonly ? 1 : 0, (const DevState *)w.st);
     return cudaGetLastError();
 }
@@ -564,7 +564,7 @@ cudaError_t launch_scale_df(const Workspace &w, const double *src, float2 *dst_d
 cudaError_t launch_xupdate_vdf(const Workspace &w, cudaStream_t s)
 {
     const size_t smem = sizeof(double) * (size_t)(w.mmax + 1);
-    launch_k(false, k_xupdate_vdf, dim3(w.num_sms * kUpdateBlocksPerSM), dim3(kStreamThreads), smem, s,
+    launch_k(w.pdl, k_xupdate_vdf, dim3(w.num_sms * kUpdateBlocksPerSM), dim3(kStreamThreads), smem, s,
              (const double *)w.V, w.ld, w.n, (const double *)w.y, w.x, (const DevState *)w.st);
     return cudaGetLastError();
 }

@@ -775,13 +775,6 @@ __global__ void __launch_bounds__(kSmallThreads) k_prime(SmallArgs a, int nrb)
 // Partials: value c < p-1 is V[:,c].w, value p-1 is w.w, value p+c is V[:,c].z.
 __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, int gs, int nrb)
 {
-    IGS_PDL_ENTER();
-    DevState *st = a.st;
-    if (halted(st)) return;
-    if (st->stop_reason != 0) {  // the previous column met the stop test
-        if (threadIdx.x == 0) st->halt = 1;
-        return;
-    }
     extern __shared__ __align__(16) double dsm[];
     const int pp = k - 1;
     double *buf = dsm;              // 2p combined partials
@@ -793,12 +786,24 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_a(SmallArgs a, int k, in
     __shared__ int s_stop, s_terms, s_f32;
     __shared__ double s_hn2;
     const int p = k - 1, t = threadIdx.x;
-    // rows 0..p-2 of L (earlier steps) load while the partials are combined; row p-1 is
-    // formed below and written to shared memory directly
+    // Rows 0..p-2 of L, ||L_{p-1}||_F^2 and H column p-2 (the breakdown test needs its
+    // squared norm) come from earlier steps, which completed before the multi-dot this kernel
+    // follows was launched: they are staged before the programmatic wait, overlapping the
+    // multi-dot's tail.  Row p-1 of L is formed below and written to shared memory directly.
     lower_prefetch(a.Lrow, p - 1, Lsm);
-    const double lf2_prev = t == 0 ? a.lfro2[p - 2] : 0.0;  // issued early
-    // breakdown test needs ||H(0:p-2, p-2)||^2 (overlapped with the partial combine)
+    const double lf2_prev = t == 0 ? a.lfro2[p - 2] : 0.0;
     last_warp_sumsq(a.H + (int64_t)(p - 2) * a.ldh, p - 1, &s_hn2);
+    IGS_PDL_ENTER();
+    DevState *st = a.st;
+    if (halted(st)) {
+        lower_drain();
+        return;
+    }
+    if (st->stop_reason != 0) {  // the previous column met the stop test
+        if (t == 0) st->halt = 1;
+        lower_drain();
+        return;
+    }
     reduce_partials(a.part, 2 * p, nrb, buf);
     const double hn2 = s_hn2;
     if (t == 0) {
@@ -960,24 +965,20 @@ __global__ void __launch_bounds__(kSmallThreads) k_flush(SmallArgs a, int m, int
 // reduction gives (partials of the step-5 multi-dot over p = nb+1 columns with x0 = u,
 // x1 = A u): value c < nb is r^(2)_c = V[:,c].u, value nb is ||u||^2, value nb+1+c is
 // V[:,c].(A u), value 2nb+1 is u.(A u).  The first-projection coefficients q of the pending
-// Hessenberg column live in r0v (for nb = 1: H_11 from the prime, in H[0]).
+// Hessenberg column are formed from the previous iteration's r^(1) and r^(3) / gamma (r1v,
+// r3v) and the completed columns of H (for nb = 1: H_11 from the prime, in H[0]).
 // =====================================================================================
 // Steps 5-9, 12, 14, 15 (and the flush, step 14 only with the normalisation's data):
 //   r^(3) = (I + L_nb)^{-1} r^(2), gamma = sqrt(||u||^2 - ||r^(2)||^2) (lagged norm),
 //   H_{0:nb-1, nb-1} = q + r^(3), H_{nb, nb-1} = gamma (column nb-1 complete), breakdown test;
 //   L row nb = r^(2) / gamma; with flush == 0 also r^(0) / gamma (its last entry twice),
-//   r^(1) = [r^(0)_{0:nb-1}; r^(0)_nb - L_nb . r^(0)_{0:nb-1}] (Stephen's trick) and the new
-//   q = r^(1) - H_{0:nb, 0:nb-1} r^(3) / gamma.  Outputs: r2v = r^(2), r1v = r^(1), r0v = q,
-//   st->inv_gamma.
+//   r^(1) = [r^(0)_{0:nb-1}; r^(0)_nb - L_nb . r^(0)_{0:nb-1}] (Stephen's trick).  Outputs:
+//   r2v = r^(2), r1v = r^(1), r3v = r^(3) / gamma, st->inv_gamma.  Step 15 of this iteration,
+//   q = r^(1) - H_{0:nb, 0:nb-1} r^(3) / gamma, is needed only by the next iteration's step 14:
+//   the next launch forms it before its programmatic wait, while the multi-dot runs, so that
+//   the nb (nb+1) products stay off the path to the basis update.
 __global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, int flush, int nrb)
 {
-    IGS_PDL_ENTER();
-    DevState *st = a.st;
-    if (halted(st)) return;
-    if (st->stop_reason != 0) {  // the previous column met the stop test
-        if (threadIdx.x == 0) st->halt = 1;
-        return;
-    }
     extern __shared__ __align__(16) double dsm[];
     const int nv = flush ? nb + 1 : 2 * (nb + 1);
     double *buf = dsm;            // combined partials (nv)
@@ -985,13 +986,37 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, 
     double *tmp = r3s + nb;
     double *qs = tmp + nb;        // q of the completed column (nb)
     double *Lsm = dsm + ((5 * nb + 3) & ~1);  // row-packed L_nb (16-byte aligned)
-    lower_prefetch(a.Lrow, nb, Lsm);  // rows of earlier steps, while the partials combine
     __shared__ double s_ig, s_g2;
     __shared__ int s_stop;
     const int t = threadIdx.x;
-    const double lf2_prev = t == 0 ? a.lfro2[nb - 1] : 0.0;
+    // L_nb, ||L_nb||_F^2 and the previous iteration's outputs come from earlier launches,
+    // which completed before the multi-dot this kernel follows was launched: they are staged,
+    // and q formed, before the programmatic wait.
+    lower_prefetch(a.Lrow, nb, Lsm);
+    const double lf2_prev = a.lfro2[nb - 1];
+    if (nb == 1) {
+        if (t == 0) qs[0] = a.H[0];
+    } else {
+        // step 15 of the previous iteration: q_i = r^(1)_i - sum_c H(i, c) r^(3)_c / gamma over
+        // the completed columns c < nb-1 (H(i, c) = 0 for i > c+1)
+        for (int i = t; i < nb; i += blockDim.x) {
+            double hs = 0.0;
+            for (int c = i > 0 ? i - 1 : 0; c < nb - 1; ++c) hs = fma(a.H[(int64_t)c * a.ldh + i], a.r3v[c], hs);
+            qs[i] = a.r1v[i] - hs;
+        }
+    }
+    IGS_PDL_ENTER();
+    DevState *st = a.st;
+    if (halted(st)) {
+        lower_drain();
+        return;
+    }
+    if (st->stop_reason != 0) {  // the previous column met the stop test
+        if (t == 0) st->halt = 1;
+        lower_drain();
+        return;
+    }
     reduce_partials(a.part, nv, nrb, buf);
-    for (int c = t; c < nb; c += blockDim.x) qs[c] = nb == 1 ? a.H[0] : a.r0v[c];
     if (t < 32) {
         // ||r^(2)||^2 (fixed shuffle tree), the lagged norm's argument
         double rr = 0.0;
@@ -1001,8 +1026,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, 
     }
     __syncthreads();
     // step 5: r^(3) = (I + L_nb)^{-1} r^(2)
-    const int terms = neumann_terms(a.lfro2[nb - 1]);
-    const bool f32 = neumann_fp32(a.lfro2[nb - 1], nb, terms);
+    const int terms = neumann_terms(lf2_prev);
+    const bool f32 = neumann_fp32(lf2_prev, nb, terms);
     lower_wait();
     unit_lower_solve(Lsm, nb, buf, r3s, tmp, terms, f32);
     // step 14: column nb-1 complete (also kept in tmp for its norm)
@@ -1071,15 +1096,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, 
         if (t == 0) r1s[nb] = buf[2 * nb + 1] * ig * ig - lr;
     }
     __syncthreads();
-    // step 15: q = r^(1) - H_{0:nb, 0:nb-1} r^(3) / gamma
-    for (int c = t; c < nb; c += blockDim.x) r3s[c] *= ig;
-    __syncthreads();
-    for (int i = t; i <= nb; i += blockDim.x) {
-        double hs = 0.0;
-        for (int c = 0; c < nb; ++c) hs = fma(a.H[(int64_t)c * a.ldh + i], r3s[c], hs);
-        a.r0v[i] = r1s[i] - hs;
-        a.r1v[i] = r1s[i];
-    }
+    for (int i = t; i <= nb; i += blockDim.x) a.r1v[i] = r1s[i];
+    for (int c = t; c < nb; c += blockDim.x) a.r3v[c] = r3s[c] * ig;
 }
 
 // Steps 10-11 and 13 in one pass over V_nb (two FMAs per basis element):
@@ -1420,7 +1438,7 @@ cudaError_t launch_update(const Workspace &w, int p, const double *coef, bool ne
     // one row per thread: the whole vector is resident at once (occupancy, not a grid-stride
     // loop, hides the loads' latency)
     const int grid = w.num_sms * kUpdateBlocksPerSM;
-    launch_k(false, k_update, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef, neg_coef ? 1 : 0,
+    launch_k(w.pdl, k_update, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, p, w.n, coef, neg_coef ? 1 : 0,
                                                           alpha, src, out, norm_last ? 1 : 0,
                                                           p_from_state ? 1 : 0, w.st,
                                                           check_halt ? 1 : 0);
@@ -1527,7 +1545,7 @@ cudaError_t launch_update_1r(const Workspace &w, int nb, const double *z, bool v
 {
     const size_t smem = sizeof(double) * (size_t)(2 * nb + 2);
     const int grid = (int)((w.n + kStreamThreads - 1) / kStreamThreads);
-    launch_k(false, k_update_1r, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, nb, w.n,
+    launch_k(w.pdl, k_update_1r, dim3(grid), dim3(kStreamThreads), smem, s, w.V, w.ld, nb, w.n,
              (const double *)w.r2v, (const double *)w.r1v, z, vonly ? 1 : 0, (const DevState *)w.st);
     return cudaGetLastError();
 }

@@ -568,13 +568,9 @@ extern "C" int igs_batch_create(igs_batch **out, int count, const int64_t *sys_p
                 cudaFuncAttributes fa;
                 if (cudaFuncGetAttributes(&fa, batch_kernel(t)) != cudaSuccess) return bail(IGS_ECUDA);
                 if (bt->smem + fa.sharedSizeBytes > (size_t)bt->max_smem_optin) return bail(IGS_EINVAL);
-                if (cudaFuncSetAttribute(batch_kernel(t), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem) !=
-                    cudaSuccess)
-                    return bail(IGS_ECUDA);
+                if (igs::raise_smem_limit((const void *)batch_kernel(t), bt->smem) != cudaSuccess) return bail(IGS_ECUDA);
             }
-            if (cudaFuncSetAttribute(k_batch_norm2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem) !=
-                cudaSuccess)
-                return bail(IGS_ECUDA);
+            if (igs::raise_smem_limit((const void *)k_batch_norm2, bt->smem) != cudaSuccess) return bail(IGS_ECUDA);
 
             // slots: one per CTA of the largest configuration the GPU can hold (any block size)
             int slots_per_sm = 0;

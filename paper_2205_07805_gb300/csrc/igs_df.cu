@@ -608,18 +608,17 @@ cudaError_t launch_dots_df_ex(const Workspace &w, int p, const double *x0, const
 cudaError_t configure_df_kernels()
 {
     // 48 KiB of stage buffers per block (3 blocks per SM): above the default dynamic limit
-    const int dm = (int)kDfDotsSmem;
-    const int um = (int)(kUpdSmemFixed + 2 * sizeof(float) * (kMaxRestart + 1));
-    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(k_dots_df<1, false>, A, dm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<2, false>, A, dm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<1, true>, A, dm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dots_df<2, true>, A, dm);
+    const size_t dm = kDfDotsSmem;
+    const size_t um = kUpdSmemFixed + 2 * sizeof(float) * (kMaxRestart + 1);
+    cudaError_t e = raise_smem_limit((const void *)k_dots_df<1, false>, dm);
+    if (e == cudaSuccess) e = raise_smem_limit((const void *)k_dots_df<2, false>, dm);
+    if (e == cudaSuccess) e = raise_smem_limit((const void *)k_dots_df<1, true>, dm);
+    if (e == cudaSuccess) e = raise_smem_limit((const void *)k_dots_df<2, true>, dm);
     // stage buffers (48 KiB) plus the coefficient splits of up to kMaxRestart + 1 columns
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_df<false>, A, um);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_df<true>, A, um);
+    if (e == cudaSuccess) e = raise_smem_limit((const void *)k_update_df<false>, um);
+    if (e == cudaSuccess) e = raise_smem_limit((const void *)k_update_df<true>, um);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_update_1r_df, A, (int)(kUpdSmemFixed + 4 * sizeof(float) * (kMaxRestart + 2)));
+        e = raise_smem_limit((const void *)k_update_1r_df, kUpdSmemFixed + 4 * sizeof(float) * (kMaxRestart + 2));
     return e;
 }
 

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <mutex>
 
 namespace igs {
 
@@ -58,6 +59,24 @@ inline cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// Raise (never lower) a kernel's dynamic shared-memory limit to `bytes`.  The limit is an
+// attribute of the function, shared by every context of the process, so a context that
+// needs less must not lower it beneath another context's launches (contexts of different
+// restart lengths alive at once: the server's norm estimates beside its graph lanes, two
+// solvers, two batches).  One process-wide lock orders the read and the write.
+// (The default limit is 48 KiB less the kernel's static shared memory, so the comparison is
+// with the kernel's current attribute, not with 48 KiB.)
+inline cudaError_t raise_smem_limit(const void *fn, size_t bytes)
+{
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 // Double-float split of an FP64 value (the IGS_PREC_FP64_DF form, igs_df.cu; also used by the

@@ -1498,19 +1498,14 @@ size_t small_solve_smem(int p, int vecs)
     return sizeof(double) * ((size_t)vecs * p + 2 + (size_t)p * (p - 1) / 2);  // + alignment of L
 }
 
-static cudaError_t allow_smem(const void *fn, size_t bytes)
-{
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
 cudaError_t configure_kernels(const Workspace &w)
 {
-    // Dynamic shared-memory limits are set once per context, before any graph capture, to
-    // what the context's largest restart length needs.
-    cudaError_t e = allow_smem((const void *)k_step_a, small_solve_smem(w.mmax, 5));
-    if (e == cudaSuccess) e = allow_smem((const void *)k_step_b, small_solve_smem(w.mmax, 3));
-    if (e == cudaSuccess) e = allow_smem((const void *)k_step_1r, small_solve_smem(w.mmax + 1, 6));
+    // Dynamic shared-memory limits are raised (never lowered: they are per function, not per
+    // context) once per context, before any graph capture, to what the context's largest
+    // restart length needs.
+    cudaError_t e = raise_smem_limit((const void *)k_step_a, small_solve_smem(w.mmax, 5));
+    if (e == cudaSuccess) e = raise_smem_limit((const void *)k_step_b, small_solve_smem(w.mmax, 3));
+    if (e == cudaSuccess) e = raise_smem_limit((const void *)k_step_1r, small_solve_smem(w.mmax + 1, 6));
     return e;
 }
 

@@ -632,9 +632,7 @@ int igs_server_create(igs_server **out, const igs_server_opts *opts)
                 cudaFuncAttributes fa;
                 if (cudaFuncGetAttributes(&fa, kern[t]) != cudaSuccess) return bail(IGS_ECUDA);
                 if (s->smem_max[t] + fa.sharedSizeBytes > (size_t)optin) return bail(IGS_EINVAL);
-                if (cudaFuncSetAttribute(kern[t], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_max[t]) !=
-                    cudaSuccess)
-                    return bail(IGS_ECUDA);
+                if (igs::raise_smem_limit(kern[t], s->smem_max[t]) != cudaSuccess) return bail(IGS_ECUDA);
                 int nb = 0;
                 if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern[t], serve::kThreads, s->smem_max[t]) !=
                     cudaSuccess)

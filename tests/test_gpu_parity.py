@@ -252,3 +252,24 @@ def test_norm2_estimate(pkg):
     # power iteration approaches ||A||_2 from below (the top singular values of this
     # matrix are clustered, so 100 iterations give about 0.3%)
     assert 0.99 * ref <= inf["A_norm2"] <= ref * (1 + 1e-12)
+
+
+def test_contexts_of_different_restart_lengths(pkg):
+    """The step kernels' shared-memory limit is an attribute of the kernel, shared by every
+    context: creating a context with a shorter restart length (smaller shared-memory needs)
+    must not lower it beneath a longer-restart context that is still alive.  m = 200 needs
+    ~167 KB in the two-iteration step kernels at p = 200, m = 150 ~95 KB; the long context's
+    cycle, run after the short one was created, must still complete and match the oracle's
+    H at the first columns."""
+    A, b, _, _ = gen.cd2d(64, 20.0, seed=9)
+    normA = gen.norm2_power(A)
+    with pkg.Solver(A, max_restart_m=200, A_norm2=normA) as big:
+        with pkg.Solver(A, max_restart_m=150, A_norm2=normA) as small:
+            r_small = small.solve(b, m=150, gs=2, tol=0.0, max_restarts=1)
+        r_big = big.solve(b, m=200, gs=2, tol=0.0, max_restarts=1)
+        g = big.arnoldi(b, 40, gs=2)
+    assert r_small["steps"] == 150 and r_big["steps"] == 200
+    o = oracle.arnoldi(A, b, 40, oracle.IGS, 2)
+    herr = P.h_column_errors(g["H"], o["H"], 40)
+    well = P.kappa_prefix(A, b, o["V"], 40) < 1e6
+    assert well[0] and herr[well].max() <= 1e-10

@@ -107,3 +107,42 @@ def test_full_size_cd2d_one_reduce_cycle(pkg):
     assert herr[well].max() <= 1e-10, herr[well].max()
     assert P.orth_loss(g["V"], m + 1) <= 1e-13
     assert P.arnoldi_relation(A, g["V"], g["H"], m, normA) <= 1e-13
+
+
+def test_one_reduce_breakdown_invariant_subspace(pkg):
+    """b spans a 3-dimensional invariant subspace of diag(1, 2, 3, 1, 2, 3): Alg. 4.2 stops
+    with a breakdown after 3 columns (the oracle does too), and the solve returns the exact
+    solution from those 3 columns.  Covers the stop taken by the step kernels' breakdown
+    test while the basis update of the same column may already be running."""
+    D = np.diag([1.0, 2.0, 3.0, 1.0, 2.0, 3.0])
+    A = gen.csr_from_dense(D, drop_zeros=True)
+    b = np.arange(1.0, 7.0)
+    o = oracle.arnoldi(A, b, 6, oracle.ONE_REDUCE, 2)
+    with pkg.Solver(A, max_restart_m=6, A_norm2=3.0) as s:
+        g = s.arnoldi(b, 6, method="one_reduce")
+        sol = s.solve(b, m=6, tol=1e-15, max_restarts=1, method="one_reduce")
+    assert o["status"] == oracle.BREAKDOWN and o["ncols"] == 3
+    assert g["status"] == pkg.BREAKDOWN and g["ncols"] == 3
+    assert sol["status"] == pkg.OK and sol["steps"] == 3
+    assert np.allclose(sol["x"], b / np.diag(D), rtol=1e-14)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_one_reduce_short_cycles(pkg, m):
+    """m = 1 (the cycle's end only), 2 and 3 (one and two per-column steps before it)."""
+    A, b, _, _ = gen.walker(4, 10.0)
+    o = oracle.arnoldi(A, b, m, oracle.ONE_REDUCE, 2)
+    with pkg.Solver(A, max_restart_m=4, A_norm2=float(np.linalg.norm(gen.csr_to_dense(A), 2))) as s:
+        g = s.arnoldi(b, m, method="one_reduce")
+    assert g["ncols"] == o["ncols"] == m and g["status"] == o["status"]
+    assert np.all(P.h_column_errors(g["H"], o["H"], m) <= 1e-12)
+
+
+def test_one_reduce_nan_is_enumeric(pkg):
+    A, b, _, _ = gen.cd2d(8, 5.0)
+    bad = b.copy()
+    bad[5] = np.nan
+    with pkg.Solver(A, max_restart_m=5, A_norm2=8.0) as s:
+        with pytest.raises(pkg.IGSError) as ei:
+            s.solve(bad, m=5, tol=1e-14, method="one_reduce")
+    assert ei.value.code == pkg.ENUMERIC

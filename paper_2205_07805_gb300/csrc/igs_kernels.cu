@@ -559,6 +559,10 @@ k_dots(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t rows
 // Two rows per thread (16-byte loads), coalesced over rows for each column.  With
 // norm_last, column p-1 (the lagged w_{k-1}) is first normalised in place,
 // v = w * inv_gamma (step 7), and a = inv_gamma (step 11).
+// Each row's sum starts from a * src[i] (src itself when a = 1) and adds the products with
+// the negated coefficients in column order, so the result needs no closing additions: every
+// FP64 instruction but the scaling is one of the update's multiply-adds (the kernel is bound
+// by the FP64 pipe).
 // =====================================================================================
 __global__ void __launch_bounds__(kStreamThreads, kUpdateBlocksPerSM)
 k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coef, int neg_coef,
@@ -567,10 +571,11 @@ k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coe
 {
     IGS_PDL_ENTER();
     if (check_halt && halted(st)) return;
-    extern __shared__ double sc[];
+    extern __shared__ double sc[];  // -coef (the products are added)
     if (p_from_state) p = st->ncols;
     const double a = norm_last ? st->inv_gamma : alpha;
-    for (int c = threadIdx.x; c < p; c += blockDim.x) sc[c] = neg_coef ? -coef[c] : coef[c];
+    const bool unit = a == 1.0;
+    for (int c = threadIdx.x; c < p; c += blockDim.x) sc[c] = neg_coef ? coef[c] : -coef[c];
     __syncthreads();
     const int pc = norm_last ? p - 1 : p;
     // Two rows per thread (16-byte loads; ld is even and the pad rows stay zero).
@@ -583,7 +588,8 @@ k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coe
     for (int64_t pr = pr_lo + threadIdx.x; pr < pr_hi; pr += blockDim.x) {
         const int64_t i = 2 * pr;
         const double *vi = V + i;
-        double x0 = 0.0, x1 = 0.0, y0 = 0.0, y1 = 0.0;
+        const double2 sv = *reinterpret_cast<const double2 *>(src + i);
+        double x = unit ? sv.x : a * sv.x, y = unit ? sv.y : a * sv.y;
         int c = 0;
         if (pc >= 4) {
             // software pipeline: the next 4 columns load while these 4 are used
@@ -595,28 +601,24 @@ k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coe
 #pragma unroll
                 for (int q = 0; q < 4; ++q) nv[q] = *reinterpret_cast<const double2 *>(vi + (int64_t)(c + 4 + q) * ld);
 #pragma unroll
-                for (int q = 0; q < 4; q += 2) {
-                    x0 = fma(v[q].x, sc[c + q], x0);
-                    y0 = fma(v[q].y, sc[c + q], y0);
-                    x1 = fma(v[q + 1].x, sc[c + q + 1], x1);
-                    y1 = fma(v[q + 1].y, sc[c + q + 1], y1);
+                for (int q = 0; q < 4; ++q) {
+                    x = fma(v[q].x, sc[c + q], x);
+                    y = fma(v[q].y, sc[c + q], y);
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) v[q] = nv[q];
             }
 #pragma unroll
-            for (int q = 0; q < 4; q += 2) {
-                x0 = fma(v[q].x, sc[c + q], x0);
-                y0 = fma(v[q].y, sc[c + q], y0);
-                x1 = fma(v[q + 1].x, sc[c + q + 1], x1);
-                y1 = fma(v[q + 1].y, sc[c + q + 1], y1);
+            for (int q = 0; q < 4; ++q) {
+                x = fma(v[q].x, sc[c + q], x);
+                y = fma(v[q].y, sc[c + q], y);
             }
             c += 4;
         }
         for (; c < pc; ++c) {
             const double2 v = *reinterpret_cast<const double2 *>(vi + (int64_t)c * ld);
-            x0 = fma(v.x, sc[c], x0);
-            y0 = fma(v.y, sc[c], y0);
+            x = fma(v.x, sc[c], x);
+            y = fma(v.y, sc[c], y);
         }
         if (norm_last) {
             double2 *vl = reinterpret_cast<double2 *>(V + (int64_t)(p - 1) * ld + i);
@@ -624,14 +626,10 @@ k_update(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ coe
             v.x *= a;
             v.y *= a;
             *vl = v;
-            x1 = fma(v.x, sc[p - 1], x1);
-            y1 = fma(v.y, sc[p - 1], y1);
+            x = fma(v.x, sc[p - 1], x);
+            y = fma(v.y, sc[p - 1], y);
         }
-        const double2 sv = *reinterpret_cast<const double2 *>(src + i);
-        double2 o;
-        o.x = fma(a, sv.x, -(x0 + x1));
-        o.y = fma(a, sv.y, -(y0 + y1));
-        *reinterpret_cast<double2 *>(out + i) = o;
+        *reinterpret_cast<double2 *>(out + i) = make_double2(x, y);
     }
 }
 

@@ -912,7 +912,7 @@ int igs_create(igs_ctx **out, int64_t n, int64_t nnz, const int64_t *rowptr, con
                 (rc = dalloc(ctx, &w.Lrow, (size_t)(M + 1) * M / 2 + 2)) ||
                 (rc = dalloc(ctx, &w.Lout, (size_t)(M + 1) * (M + 1))) || (rc = dalloc(ctx, &w.cs, (size_t)M)) ||
                 (rc = dalloc(ctx, &w.sn, (size_t)M)) || (rc = dalloc(ctx, &w.g, (size_t)M + 1)) ||
-                (rc = dalloc(ctx, &w.lfro2, (size_t)M + 1)) || (rc = dalloc(ctx, &w.r0v, (size_t)M + 1)) ||
+                (rc = dalloc(ctx, &w.lfro2, (size_t)M + 1)) ||
                 (rc = dalloc(ctx, &w.r1v, (size_t)M + 1)) || (rc = dalloc(ctx, &w.r2v, (size_t)M + 1)) ||
                 (rc = dalloc(ctx, &w.r3v, (size_t)M + 1)) || (rc = dalloc(ctx, &w.y, (size_t)M + 1)) ||
                 (rc = dalloc(ctx, &w.hist_res, (size_t)M)) || (rc = dalloc(ctx, &w.hist_lfro, (size_t)M)) ||

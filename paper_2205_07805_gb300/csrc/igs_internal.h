@@ -143,7 +143,7 @@ struct Workspace {
     double *R = nullptr;           // Givens-rotated copy of H, same layout as H
     double *cs = nullptr, *sn = nullptr, *g = nullptr;  // rotations and rotated rhs
     double *lfro2 = nullptr;       // cumulative ||L rows 0..i||_F^2, mmax+1 entries
-    double *r0v = nullptr, *r1v = nullptr, *r2v = nullptr, *r3v = nullptr, *y = nullptr;
+    double *r1v = nullptr, *r2v = nullptr, *r3v = nullptr, *y = nullptr;
     double *part = nullptr;        // per-block partial sums
     int64_t part_cap = 0;
     double *hist_res = nullptr, *hist_lfro = nullptr;  // per-cycle history (mmax entries)

@@ -673,7 +673,7 @@ k_scale(int64_t n, const double *src, double *dst, int which, const DevState *st
 // Small single-block steps.
 // =====================================================================================
 struct SmallArgs {
-    double *H, *L, *Lrow, *R, *cs, *sn, *g, *lfro2, *r0v, *r1v, *r2v, *r3v, *y, *hist_res, *hist_lfro;
+    double *H, *L, *Lrow, *R, *cs, *sn, *g, *lfro2, *r1v, *r2v, *r3v, *y, *hist_res, *hist_lfro;
     const double *part;
     DevState *st;
     int ldh, ldl;
@@ -683,7 +683,7 @@ static SmallArgs small_args(const Workspace &w)
 {
     SmallArgs a;
     a.H = w.H; a.L = w.L; a.Lrow = w.Lrow; a.R = w.R; a.cs = w.cs; a.sn = w.sn; a.g = w.g; a.lfro2 = w.lfro2;
-    a.r0v = w.r0v; a.r1v = w.r1v; a.r2v = w.r2v; a.r3v = w.r3v; a.y = w.y;
+    a.r1v = w.r1v; a.r2v = w.r2v; a.r3v = w.r3v; a.y = w.y;
     a.hist_res = w.hist_res; a.hist_lfro = w.hist_lfro; a.part = w.part; a.st = w.st;
     a.ldh = w.ldh(); a.ldl = w.ldl();
     return a;

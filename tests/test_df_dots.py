@@ -124,3 +124,25 @@ def test_df_out_of_range_is_enumeric(pkg):
         assert ei.value.code == pkg.ENUMERIC
         ok = s.solve(b, m=20, gs=2, tol=0.0, max_restarts=1)
     assert np.all(np.isfinite(ok["x"])) and ok["steps"] == 20
+
+
+@pytest.mark.parametrize("method", ["igs", "one_reduce"])
+def test_df_largest_restart_length(pkg, method):
+    """The double-float form at the largest restart length (m = 232: multi-dots over up to
+    233 columns in 59 column groups, the updates' coefficient splits at their largest) on a
+    system above its 16384-row threshold: H against the oracle while kappa(B_k) < 1e6, the
+    Arnoldi relation, and (two iterations) orthogonality."""
+    A, b, _, _ = CASES["cd2d_130"]
+    normA = _norm(A)
+    m = 232
+    with pkg.Solver(A, max_restart_m=m, A_norm2=normA) as s:
+        g = s.arnoldi(b, m, gs=2, method=method, precision="fp64_df")
+    o = oracle.arnoldi(A, b, m, oracle.ONE_REDUCE if method == "one_reduce" else oracle.IGS, 2,
+                       impl=oracle.openmp())
+    assert g["ncols"] == o["ncols"] == m and g["status"] == o["status"]
+    kap = P.kappa_prefix(A, b, o["V"], m)
+    herr = P.h_column_errors(g["H"], o["H"], m)
+    well = kap < 1e6
+    assert well.sum() > 10 and herr[well].max() <= 1e-10
+    assert P.arnoldi_relation(A, g["V"], g["H"], m, normA) <= 1e-13
+    assert P.orth_loss(g["V"], m + 1) <= 1e-13

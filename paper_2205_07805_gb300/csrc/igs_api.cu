@@ -452,18 +452,20 @@ cudaError_t enqueue_cycle_1r_vdf(igs_ctx *ctx, Issuer &is, int m)
         RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, wu, w.z, nullptr, true, st_, zd));
         RUN(igs::KC_DOTS, dots_bytes(w, nb + 1, 2), 4.0 * w.n * (nb + 1), s,
             igs::launch_dots_df_ex(w, nb + 1, col(nb), zdd, true, true, st_, &pl));
-        // Steps 5-9, 12, 14, 15: column nb-1 complete; its Givens rotation on the side.
+        // Steps 5, 9, 14, 15 of the previous iteration (column nb-2 complete; in the launch's
+        // prologue) and steps 6-8, 12 of this one; column nb-2's Givens rotation on the side.
         RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, nb, false, pl, st_));
-        if ((e = fork_givens(nb - 1)) != cudaSuccess) return e;
+        if (nb >= 2 && (e = fork_givens(nb - 2)) != cudaSuccess) return e;
         // Steps 10-11, 13: v_{k-1} and u_k in one pass over the split basis.
         RUN(igs::KC_UPDATE, 8.0 * w.n * (nb + 4), 4.0 * w.n * nb, s, igs::launch_update_1r_df(w, nb, w.z, wu, false, st_));
     }
-    // Flush: the reduction of u_{m+1} (no product), column m-1 complete, v_{m+1}.
+    // Flush: the reduction of u_{m+1} (no product), columns m-2 and m-1 complete, v_{m+1}.
     if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
         igs::launch_dots_df_ex(w, m + 1, col(m), nullptr, true, true, st_, &pl));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, m, true, pl, st_));
     RUN(igs::KC_UPDATE, 8.0 * w.n * (m + 2), 2.0 * w.n * m, s, igs::launch_update_1r_df(w, m, w.z, wu, true, st_));
+    if (m >= 2) RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 2, st_));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));
     // Least squares y = argmin ||rho e1 - H y||, x_m = x_0 + V_m y_m (FP64).
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_lsq(w, m, st_));
@@ -583,9 +585,10 @@ cudaError_t enqueue_cycle32(igs_ctx *ctx, Issuer &is, int m, int gs)
 
 // One cycle of Alg. 4.2 (one-reduce hybrid MGS-CGS GMRES; the readings are the oracle's).
 // Per column: the SpMV on u_{k-1} (held in V[:, nb]), the one reduction [V_nb, u]^T [u, A u]
-// (the step-5 multi-dot), the single-block step (r^(3), the lagged norm, column nb-1 of H,
-// L, Stephen's trick, q), and one fused pass over V_nb forming v_{k-1} and u_k.  The Givens
-// rotation of each completed column runs on a side branch as in Alg. 4.1.
+// (the step-5 multi-dot), the single-block step (the lagged norm and Stephen's trick for
+// r^(1); its prologue completes the previous column: r^(3), H, L, q), and one fused pass over
+// V_nb forming v_{k-1} and u_k.  The Givens rotation of each completed column runs on a side
+// branch as in Alg. 4.1.
 cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m, bool df)
 {
     const igs::Workspace &w = ctx->w;
@@ -647,18 +650,20 @@ cudaError_t enqueue_cycle_1r(igs_ctx *ctx, Issuer &is, int m, bool df)
         RUN(igs::KC_SPMV, spmv_bytes(w), 2.0 * w.nnz, s, igs::launch_spmv(w, u, w.z, nullptr, true, st_));
         RUN(igs::KC_DOTS, dots_bytes(w, nb + 1, 2), 4.0 * w.n * (nb + 1), s,
             dots(w, nb + 1, u, w.z, true, st_, &pl));
-        // Steps 5-9, 12, 14, 15: column nb-1 complete; its Givens rotation on the side.
+        // Steps 5, 9, 14, 15 of the previous iteration (column nb-2 complete; in the launch's
+        // prologue) and steps 6-8, 12 of this one; column nb-2's Givens rotation on the side.
         RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, nb, false, pl, st_));
-        if ((e = fork_givens(nb - 1)) != cudaSuccess) return e;
+        if (nb >= 2 && (e = fork_givens(nb - 2)) != cudaSuccess) return e;
         // Steps 10-11, 13: v_{k-1} and u_k in one pass.
         RUN(igs::KC_UPDATE, 8.0 * w.n * (nb + 4), 4.0 * w.n * nb, s, igs::launch_update_1r(w, nb, w.z, false, st_));
     }
-    // Flush: the reduction of u_{m+1} (no product), column m-1 complete, v_{m+1}.
+    // Flush: the reduction of u_{m+1} (no product), columns m-2 and m-1 complete, v_{m+1}.
     if ((e = join_side()) != cudaSuccess) return e;
     RUN(igs::KC_DOTS, dots_bytes(w, m + 1, 1), 2.0 * w.n * (m + 1), s,
         dots(w, m + 1, col(m), nullptr, true, st_, &pl));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_step_1r(w, m, true, pl, st_));
     RUN(igs::KC_UPDATE, 8.0 * w.n * (m + 2), 2.0 * w.n * m, s, igs::launch_update_1r(w, m, w.z, true, st_));
+    if (m >= 2) RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 2, st_));
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_givens(w, m - 1, st_));
     // Least squares y = argmin ||rho e1 - H y||, x_m = x_0 + V_m y_m.
     RUN(igs::KC_SMALL, 0, 0, s, igs::launch_lsq(w, m, st_));

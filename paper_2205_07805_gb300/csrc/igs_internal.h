@@ -117,6 +117,7 @@ struct DevState {
     double rnorm, xnorm, beta;  // end-of-cycle residual norm, ||x||, backward error
     double inner_tol;  // FP32 cycles of the precision form: stop when |g| <= inner_tol * rho
     double stop_floor; // inner_tol * rho of the current cycle (0 for FP64 solves)
+    double lag_g2;     // Alg. 4.2: gamma^2 of the last step (its column's breakdown test)
     int halt;          // nonzero: the remaining step kernels of this cycle do nothing
     int stop_cols;     // > 0: columns the cycle ends with (early stop or breakdown)
     int stop_reason;   // 0 running, 1 converged, 2 breakdown, -4 numeric error

@@ -962,113 +962,222 @@ __global__ void __launch_bounds__(kSmallThreads) k_flush(SmallArgs a, int m, int
 // previous iteration's single projection (nb = k-2 normalised columns before it); the one
 // reduction gives (partials of the step-5 multi-dot over p = nb+1 columns with x0 = u,
 // x1 = A u): value c < nb is r^(2)_c = V[:,c].u, value nb is ||u||^2, value nb+1+c is
-// V[:,c].(A u), value 2nb+1 is u.(A u).  The first-projection coefficients q of the pending
-// Hessenberg column are formed from the previous iteration's r^(1) and r^(3) / gamma (r1v,
-// r3v) and the completed columns of H (for nb = 1: H_11 from the prime, in H[0]).
+// V[:,c].(A u), value 2nb+1 is u.(A u).
+//
+// Of an iteration's small steps, the fused basis update that follows needs only r^(2), gamma
+// and r^(1).  The rest -- r^(3) = (I + L)^{-1} r^(2), the completed Hessenberg column, its
+// breakdown test, the new row of L and the next first-projection coefficients q -- depends
+// only on what the iteration stores (r2v, r1v, 1/gamma, gamma^2), so the next launch does it
+// in its prologue, before its programmatic wait: on an SM the multi-dot has already left,
+// while the multi-dot's last blocks still run.  Hence the launch for nb (k = nb+2) first
+// completes column nb-2 (the previous launch's), then forms this iteration's r^(2), gamma and
+// r^(1).  The Givens rotation of column nb-2 follows it on the side branch.  The cycle's end
+// (flush) completes columns m-2 and m-1.
 // =====================================================================================
-// Steps 5-9, 12, 14, 15 (and the flush, step 14 only with the normalisation's data):
-//   r^(3) = (I + L_nb)^{-1} r^(2), gamma = sqrt(||u||^2 - ||r^(2)||^2) (lagged norm),
-//   H_{0:nb-1, nb-1} = q + r^(3), H_{nb, nb-1} = gamma (column nb-1 complete), breakdown test;
-//   L row nb = r^(2) / gamma; with flush == 0 also r^(0) / gamma (its last entry twice),
-//   r^(1) = [r^(0)_{0:nb-1}; r^(0)_nb - L_nb . r^(0)_{0:nb-1}] (Stephen's trick).  Outputs:
-//   r2v = r^(2), r1v = r^(1), r3v = r^(3) / gamma, st->inv_gamma.  Step 15 of this iteration,
-//   q = r^(1) - H_{0:nb, 0:nb-1} r^(3) / gamma, is needed only by the next iteration's step 14:
-//   the next launch forms it before its programmatic wait, while the multi-dot runs, so that
-//   the nb (nb+1) products stay off the path to the basis update.
+// Steps 5, 9, 14 and 15 of the previous iteration (nbp = nb-1 columns before its u), from its
+// r2v, r1v, st->inv_gamma, st->lag_g2 and q (r3v; H_11 in H[0] when nbp = 1), with
+// L_{nbp} staged in Lsm: r^(3) = (I + L_{nbp})^{-1} r^(2) (into r3s), H_{0:nbp-1, nbp-1} =
+// q + r^(3) (into hcol and H), the breakdown test gamma^2 <= (64 eps)^2 ||column||^2, then
+// (no stop) L row nbp = r^(2) / gamma (global, and into Lsm) with ||L_{nbp+1}||_F^2 (*lf2),
+// and the next q = r^(1) - H_{0:nbp, 0:nbp-1} r^(3) / gamma (into qs and r3v).  Returns the
+// stop reason the column ends with (0: none).  Block-wide.
+__device__ int complete_column_1r(const SmallArgs &a, int nbp, double *Lsm, double *r2s, double *r3s, double *qs,
+                                  double *hcol, double *tmp, double *lf2)
+{
+    __shared__ double s_hn2;
+    __shared__ int s_stop;
+    DevState *st = a.st;
+    const int t = threadIdx.x;
+    const double ig = st->inv_gamma, g2 = st->lag_g2, lf2_prev = a.lfro2[nbp - 1];
+    for (int c = t; c < nbp; c += blockDim.x) {
+        r2s[c] = a.r2v[c];
+        qs[c] = nbp == 1 ? a.H[0] : a.r3v[c];
+    }
+    const int terms = neumann_terms(lf2_prev);
+    const bool f32 = neumann_fp32(lf2_prev, nbp, terms);
+    lower_wait();  // also orders the loads above before their use
+    unit_lower_solve(Lsm, nbp, r2s, r3s, tmp, terms, f32);
+    for (int c = t; c < nbp; c += blockDim.x) {
+        const double h = qs[c] + r3s[c];
+        a.H[(int64_t)(nbp - 1) * a.ldh + c] = h;
+        hcol[c] = h;
+    }
+    __syncthreads();
+    if (t < 32) {
+        double hn2 = 0.0;
+        for (int c = t; c < nbp; c += 32) hn2 = fma(hcol[c], hcol[c], hn2);
+        for (int o = 16; o > 0; o >>= 1) hn2 += __shfl_down_sync(0xffffffffu, hn2, o);
+        if (t == 0) {
+            int stop = st->stop_reason;  // the previous launch's own stop (this column still completes)
+            if (stop == 0 && g2 <= kBreakdownFactor * kBreakdownFactor * hn2) {
+                stop = 2;
+                st->halt = 1;
+                st->stop_reason = 2;
+                st->stop_cols = nbp;
+            }
+            s_stop = stop;
+        }
+    }
+    __syncthreads();
+    if (s_stop != 0) return s_stop;
+    // step 9: L row nbp = r^(2) / gamma
+    if (t < 32) {
+        double rowsq = 0.0;
+        for (int c = t; c < nbp; c += 32) {
+            const double l = r2s[c] * ig;
+            a.L[(int64_t)c * a.ldl + nbp] = l;
+            a.Lrow[packed_row(nbp) + c] = l;
+            Lsm[packed_row(nbp) + c] = l;
+            rowsq = fma(l, l, rowsq);
+        }
+        for (int o = 16; o > 0; o >>= 1) rowsq += __shfl_down_sync(0xffffffffu, rowsq, o);
+        if (t == 0) {
+            a.lfro2[nbp] = lf2_prev + rowsq;
+            *lf2 = lf2_prev + rowsq;
+        }
+    }
+    // step 15: q_i = r^(1)_i - sum_c H(i, c) r^(3)_c / gamma over the columns c < nbp
+    // (H(i, c) = 0 for i > c+1; column nbp-1 is hcol with H_{nbp, nbp-1} = gamma)
+    for (int c = t; c < nbp; c += blockDim.x) r3s[c] *= ig;
+    __syncthreads();
+    for (int i = t; i <= nbp; i += blockDim.x) {
+        double hs = 0.0;
+        for (int c = i > 0 ? i - 1 : 0; c < nbp - 1; ++c) hs = fma(a.H[(int64_t)c * a.ldh + i], r3s[c], hs);
+        hs = fma(i < nbp ? hcol[i] : a.H[(int64_t)(nbp - 1) * a.ldh + nbp], r3s[nbp - 1], hs);
+        const double q = a.r1v[i] - hs;
+        a.r3v[i] = q;
+        qs[i] = q;
+    }
+    __syncthreads();
+    return 0;
+}
+
+// Iteration k = nb+2 of Alg. 4.2, steps 6-8 and 12 (what the fused update needs), after the
+// previous iteration's column has been completed in the prologue (complete_column_1r):
+//   gamma^2 = ||u||^2 - ||r^(2)||^2 (lagged norm), 1/gamma, H_{nb, nb-1} = gamma,
+//   r^(1) = [V^T A u / gamma; u.A u / gamma^2 - r^(2).(V^T A u) / gamma^2] (Stephen's trick:
+//   the last entry is r^(0)_nb - L_nb . r^(0)_{0:nb-1} with L_nb = r^(2) / gamma).
+// Stops the cycle where gamma^2 is not finite (IGS_ENUMERIC) or gamma = 0 (breakdown).
+// Outputs: r2v = r^(2), r1v = r^(1), st->inv_gamma, st->lag_g2 = gamma^2.
+// With flush (nb = m, the reduction of u_{m+1}: value c < m is V[:,c].u, value m is ||u||^2)
+// the column m-1 is completed here as well (steps 5, 9 and 14; no r^(1)), for the last
+// v_{m+1} = (u - V_m r^(2)) / gamma.
 __global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, int flush, int nrb)
 {
     extern __shared__ __align__(16) double dsm[];
-    const int nv = flush ? nb + 1 : 2 * (nb + 1);
-    double *buf = dsm;            // combined partials (nv)
-    double *r3s = buf + 2 * (nb + 1);
-    double *tmp = r3s + nb;
-    double *qs = tmp + nb;        // q of the completed column (nb)
-    double *Lsm = dsm + ((5 * nb + 3) & ~1);  // row-packed L_nb (16-byte aligned)
-    __shared__ double s_ig, s_g2;
-    __shared__ int s_stop;
+    double *buf = dsm;              // r^(2) of the previous iteration, then the combined partials
+    double *r3s = buf + (nb + 1);   // (with buf: 2 nb + 2 partials)
+    double *qs = r3s + (nb + 1);    // q of the column being completed
+    double *hcol = qs + nb;         // that column
+    double *tmp = hcol + nb;        // solve scratch (nb + 1)
+    double *Lsm = dsm + ((5 * nb + 4) & ~1);  // row-packed L (16-byte aligned)
+    __shared__ double s_ig, s_g2, s_r1last, s_lf2, s_hn2;
+    __shared__ int s_stop, s_pro;
+    DevState *st = a.st;
     const int t = threadIdx.x;
-    // L_nb, ||L_nb||_F^2 and the previous iteration's outputs come from earlier launches,
-    // which completed before the multi-dot this kernel follows was launched: they are staged,
-    // and q formed, before the programmatic wait.
-    lower_prefetch(a.Lrow, nb, Lsm);
-    const double lf2_prev = a.lfro2[nb - 1];
-    if (nb == 1) {
-        if (t == 0) qs[0] = a.H[0];
+    const int nbp = nb - 1;
+    // ---- prologue: everything read here was written by launches that completed before the
+    // multi-dot this kernel follows was launched
+    lower_prefetch(a.Lrow, nbp, Lsm);  // rows 0..nb-2
+    if (nb >= 2) {
+        // completes column nb-2 unless an earlier column already ended the cycle
+        const bool skip = st->stop_reason != 0 && st->stop_cols < nbp;
+        int pro = skip ? 1 : complete_column_1r(a, nbp, Lsm, buf, r3s, qs, hcol, tmp, &s_lf2);
+        if (t == 0) s_pro = pro;
     } else {
-        // step 15 of the previous iteration: q_i = r^(1)_i - sum_c H(i, c) r^(3)_c / gamma over
-        // the completed columns c < nb-1 (H(i, c) = 0 for i > c+1)
-        for (int i = t; i < nb; i += blockDim.x) {
-            double hs = 0.0;
-            for (int c = i > 0 ? i - 1 : 0; c < nb - 1; ++c) hs = fma(a.H[(int64_t)c * a.ldh + i], a.r3v[c], hs);
-            qs[i] = a.r1v[i] - hs;
+        if (t == 0) {
+            qs[0] = a.H[0];
+            s_lf2 = a.lfro2[0];
+            s_pro = 0;
         }
     }
+    lower_drain();
+    __syncthreads();
     IGS_PDL_ENTER();
-    DevState *st = a.st;
-    if (halted(st)) {
-        lower_drain();
-        return;
-    }
+    if (s_pro != 0 || halted(st)) return;
     if (st->stop_reason != 0) {  // the previous column met the stop test
         if (t == 0) st->halt = 1;
-        lower_drain();
         return;
     }
+    const int nv = flush ? nb + 1 : 2 * (nb + 1);
     reduce_partials(a.part, nv, nrb, buf);
     if (t < 32) {
-        // ||r^(2)||^2 (fixed shuffle tree), the lagged norm's argument
-        double rr = 0.0;
-        for (int c = t; c < nb; c += 32) rr = fma(buf[c], buf[c], rr);
-        for (int o = 16; o > 0; o >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, o);
-        if (t == 0) s_g2 = buf[nb] - rr;
-    }
-    __syncthreads();
-    // step 5: r^(3) = (I + L_nb)^{-1} r^(2)
-    const int terms = neumann_terms(lf2_prev);
-    const bool f32 = neumann_fp32(lf2_prev, nb, terms);
-    lower_wait();
-    unit_lower_solve(Lsm, nb, buf, r3s, tmp, terms, f32);
-    // step 14: column nb-1 complete (also kept in tmp for its norm)
-    for (int c = t; c < nb; c += blockDim.x) {
-        const double h = qs[c] + r3s[c];
-        a.H[(int64_t)(nb - 1) * a.ldh + c] = h;
-        tmp[c] = h;
-    }
-    __syncthreads();
-    if (t < 32) {
-        // warp 0: ||H_{0:nb-1, nb-1}||^2 (fixed shuffle tree), then the scalar step on lane 0
-        // (1/gamma by rsqrt, the breakdown test on squares: no DSQRT or DDIV)
-        double hn2 = 0.0;
-        for (int c = t; c < nb; c += 32) hn2 = fma(tmp[c], tmp[c], hn2);
-        for (int o = 16; o > 0; o >>= 1) hn2 += __shfl_down_sync(0xffffffffu, hn2, o);
+        // ||r^(2)||^2 and r^(2).(V^T A u) (fixed shuffle trees), then the scalars on lane 0
+        // (1/gamma by rsqrt: no DSQRT or DDIV)
+        double rr = 0.0, dr = 0.0;
+        for (int c = t; c < nb; c += 32) {
+            rr = fma(buf[c], buf[c], rr);
+            if (!flush) dr = fma(buf[c], buf[nb + 1 + c], dr);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            rr += __shfl_down_sync(0xffffffffu, rr, o);
+            dr += __shfl_down_sync(0xffffffffu, dr, o);
+        }
         if (t == 0) {
-            const double g2 = s_g2;
+            const double g2 = buf[nb] - rr;
             int stop = 0;
-            double gam = 0.0, ig = 0.0;
+            double ig = 0.0;
             if (g2 != g2 || isinf(g2)) {
                 stop = -4;
             } else {
+                double gam = 0.0;
                 if (g2 > 0.0) {
                     ig = rsqrt(g2);
                     gam = g2 * ig;
                 }
                 a.H[(int64_t)(nb - 1) * a.ldh + nb] = gam;
-                if (gam == 0.0 || g2 <= kBreakdownFactor * kBreakdownFactor * hn2) stop = 2;
+                if (gam == 0.0) stop = 2;
             }
-            if (stop != 0) {
+            if (stop != 0 && !(flush && stop == 2)) {  // the flush decides breakdown below
                 st->halt = 1;
                 st->stop_reason = stop;
                 st->stop_cols = nb;
             }
             st->inv_gamma = ig;
+            st->lag_g2 = g2;
             s_ig = ig;
+            s_g2 = g2;
+            s_r1last = flush ? 0.0 : (buf[2 * nb + 1] - dr) * (ig * ig);
             s_stop = stop;
         }
     }
     __syncthreads();
-    if (s_stop != 0) return;
+    if (s_stop < 0) return;
     const double ig = s_ig;
-    // step 9: L row nb = r^(2) / gamma, and ||L_{nb+1}||_F^2
+    if (!flush) {
+        // r^(2) also where gamma = 0 ended the cycle: the next launch completes this column
+        for (int c = t; c < nb; c += blockDim.x) a.r2v[c] = buf[c];
+        if (s_stop != 0) return;
+        for (int c = t; c < nb; c += blockDim.x) a.r1v[c] = buf[nb + 1 + c] * ig;
+        if (t == 0) a.r1v[nb] = s_r1last;
+        return;
+    }
+    // ---- the flush: column m-1 (q in qs, L_m in Lsm with row m-1 from the prologue)
+    const int terms = neumann_terms(s_lf2);
+    const bool f32 = neumann_fp32(s_lf2, nb, terms);
+    unit_lower_solve(Lsm, nb, buf, r3s, tmp, terms, f32);
+    for (int c = t; c < nb; c += blockDim.x) {
+        const double h = qs[c] + r3s[c];
+        a.H[(int64_t)(nb - 1) * a.ldh + c] = h;
+        hcol[c] = h;
+    }
+    __syncthreads();
+    if (t < 32) {
+        double hn2 = 0.0;
+        for (int c = t; c < nb; c += 32) hn2 = fma(hcol[c], hcol[c], hn2);
+        for (int o = 16; o > 0; o >>= 1) hn2 += __shfl_down_sync(0xffffffffu, hn2, o);
+        if (t == 0) {
+            s_hn2 = hn2;
+            if (s_stop != 0 || s_g2 <= kBreakdownFactor * kBreakdownFactor * hn2) {
+                st->halt = 1;
+                st->stop_reason = 2;
+                st->stop_cols = nb;
+                s_stop = 2;
+            }
+        }
+    }
+    __syncthreads();
+    if (s_stop != 0) return;
     if (t < 32) {
         double rowsq = 0.0;
         for (int c = t; c < nb; c += 32) {
@@ -1078,24 +1187,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_step_1r(SmallArgs a, int nb, 
             rowsq = fma(l, l, rowsq);
         }
         for (int o = 16; o > 0; o >>= 1) rowsq += __shfl_down_sync(0xffffffffu, rowsq, o);
-        if (t == 0) a.lfro2[nb] = lf2_prev + rowsq;
+        if (t == 0) a.lfro2[nb] = s_lf2 + rowsq;
     }
     for (int c = t; c < nb; c += blockDim.x) a.r2v[c] = buf[c];
-    if (flush) return;
-    __syncthreads();
-    // steps 7-8 and 12 (Stephen's trick for the last entry of r^(1))
-    double *r1s = tmp;  // reuse (nb + 1 entries fit: tmp, qs are contiguous)
-    for (int c = t; c < nb; c += blockDim.x) r1s[c] = buf[nb + 1 + c] * ig;
-    __syncthreads();
-    if (t < 32) {
-        double lr = 0.0;
-        for (int c = t; c < nb; c += 32) lr = fma(buf[c] * ig, r1s[c], lr);
-        for (int o = 16; o > 0; o >>= 1) lr += __shfl_down_sync(0xffffffffu, lr, o);
-        if (t == 0) r1s[nb] = buf[2 * nb + 1] * ig * ig - lr;
-    }
-    __syncthreads();
-    for (int i = t; i <= nb; i += blockDim.x) a.r1v[i] = r1s[i];
-    for (int c = t; c < nb; c += blockDim.x) a.r3v[c] = r3s[c] * ig;
 }
 
 // Steps 10-11 and 13 in one pass over V_nb (two FMAs per basis element):

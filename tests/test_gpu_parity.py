@@ -273,3 +273,26 @@ def test_contexts_of_different_restart_lengths(pkg):
     herr = P.h_column_errors(g["H"], o["H"], 40)
     well = P.kappa_prefix(A, b, o["V"], 40) < 1e6
     assert well[0] and herr[well].max() <= 1e-10
+
+
+@pytest.mark.parametrize("method,gs,precision", [("igs", 2, "fp64"), ("igs", 1, "fp64"), ("one_reduce", 2, "fp64"),
+                                                 ("igs", 2, "fp64_df"), ("one_reduce", 2, "fp64_df"),
+                                                 ("igs", 2, "fp32_ir")])
+def test_profiled_launches_match_the_graph(pkg, method, gs, precision):
+    """With per-kernel profiling on, a cycle is issued kernel by kernel (no CUDA graph, an
+    event pair around every kernel, the Givens kernels inline) instead of replayed from its
+    graph: the same kernels in the same order, so x, beta and the step count are bitwise the
+    graph path's, for every algorithm and precision form.  The profile accounts the
+    streaming kernel classes."""
+    A, b, _, _ = gen.cd2d(130, 50.0, seed=21)  # n = 16900: the double-float kernels engage
+    normA = gen.norm2_power(A)
+    kw = dict(m=30, gs=gs, tol=1e-12, max_restarts=4, method=method, precision=precision)
+    with pkg.Solver(A, max_restart_m=30, A_norm2=normA, fp32_basis=precision == "fp32_ir") as s:
+        g = s.solve(b, **kw)
+        s.profile_enable(True)
+        e = s.solve(b, **kw)
+        prof = s.profile()
+        s.profile_enable(False)
+    assert np.array_equal(g["x"], e["x"]) and g["beta"] == e["beta"] and g["steps"] == e["steps"]
+    assert g["status"] == e["status"]
+    assert all(prof[c]["launches"] > 0 and prof[c]["ms"] > 0 for c in ("spmv", "dots", "update"))

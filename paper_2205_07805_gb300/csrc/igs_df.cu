@@ -148,63 +148,48 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    // prologue: the first kDfStages - 1 segments (an empty group where there are fewer)
-#pragma unroll
-    for (int j = 0; j < kDfStages - 1; ++j) {
-        if (g0 + j < g1)
-            issue(g0 + j, j);
-        else
-            asm volatile("cp.async.commit_group;" ::: "memory");
-    }
     int since = 0;
-    for (int64_t g = g0; g < g1; ++g) {
-        const int b = (int)(g - g0) & (kDfStages - 1);
-        if (g + kDfStages - 1 < g1)
-            issue(g + kDfStages - 1, (int)(g + kDfStages - 1 - g0) & (kDfStages - 1));
-        else
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group %0;" ::"n"(kDfStages - 1) : "memory");
-        const int64_t i = r_lo + (g << 6) + 2 * lane;
-        if (i < r_hi) {
-            const double *src = stage0 + b * kDfStageDoubles;
-            float xh[NQ][2], xl[NQ][2];
+    // the products of one staged segment (ncol of the group's columns) and the periodic fold
+    auto consume = [&](const double *src, int ncol) {
+        float xh[NQ][2], xl[NQ][2];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                if (VDF) {  // stored split: (hi, lo) of two rows
-                    const float4 xv = *reinterpret_cast<const float4 *>(src + 64 * q);
-                    xh[q][0] = xv.x;
-                    xl[q][0] = xv.y;
-                    xh[q][1] = xv.z;
-                    xl[q][1] = xv.w;
-                } else {
-                    const double2 xv = *reinterpret_cast<const double2 *>(src + 64 * q);
-                    df_split(xv.x, xh[q][0], xl[q][0]);
-                    df_split(xv.y, xh[q][1], xl[q][1]);
-                }
+        for (int q = 0; q < NQ; ++q) {
+            if (VDF) {  // stored split: (hi, lo) of two rows
+                const float4 xv = *reinterpret_cast<const float4 *>(src + 64 * q);
+                xh[q][0] = xv.x;
+                xl[q][0] = xv.y;
+                xh[q][1] = xv.z;
+                xl[q][1] = xv.w;
+            } else {
+                const double2 xv = *reinterpret_cast<const double2 *>(src + 64 * q);
+                df_split(xv.x, xh[q][0], xl[q][0]);
+                df_split(xv.y, xh[q][1], xl[q][1]);
             }
+        }
 #pragma unroll
-            for (int c = 0; c < CW; ++c) {
-                if (c < cw) {
-                    float h0, l0, h1, l1;
-                    if (VDF) {
-                        const float4 v = *reinterpret_cast<const float4 *>(src + 64 * (NQ + c));
-                        h0 = v.x;
-                        l0 = v.y;
-                        h1 = v.z;
-                        l1 = v.w;
-                    } else {
-                        const double2 v = *reinterpret_cast<const double2 *>(src + 64 * (NQ + c));
-                        df_split(v.x, h0, l0);
-                        df_split(v.y, h1, l1);
-                    }
+        for (int c = 0; c < CW; ++c) {
+            if (c < ncol) {
+                float h0, l0, h1, l1;
+                if (VDF) {
+                    const float4 v = *reinterpret_cast<const float4 *>(src + 64 * (NQ + c));
+                    h0 = v.x;
+                    l0 = v.y;
+                    h1 = v.z;
+                    l1 = v.w;
+                } else {
+                    const double2 v = *reinterpret_cast<const double2 *>(src + 64 * (NQ + c));
+                    df_split(v.x, h0, l0);
+                    df_split(v.y, h1, l1);
+                }
 #pragma unroll
-                    for (int q = 0; q < NQ; ++q) {
-                        df_acc(S[c][q], s[c][q], h0, l0, xh[q][0], xl[q][0]);
-                        df_acc(S[c][q], s[c][q], h1, l1, xh[q][1], xl[q][1]);
-                    }
+                for (int q = 0; q < NQ; ++q) {
+                    df_acc(S[c][q], s[c][q], h0, l0, xh[q][0], xl[q][0]);
+                    df_acc(S[c][q], s[c][q], h1, l1, xh[q][1], xl[q][1]);
                 }
             }
         }
+    };
+    auto fold = [&]() {
         if (++since == kFold) {
             since = 0;
 #pragma unroll
@@ -215,6 +200,65 @@ k_dots_df(const double *__restrict__ V, int64_t ld, int p, int64_t n4, int64_t r
                     S[c][q] = 0.f;
                     s[c][q] = 0.f;
                 }
+        }
+    };
+    if (cw == CW && r_lo + (g1 << 6) <= r_hi) {
+        // Fast path (warp-uniform: every segment of this warp lies inside the row block, and
+        // the group has all CW columns): the copies come from running source pointers into
+        // fixed shared-memory addresses, with no per-lane bounds or column tests.  Same
+        // segments, same order, same arithmetic as the general path below.
+        const int nsg = (int)(g1 - g0);
+        const int64_t i0 = r_lo + (g0 << 6) + 2 * lane;
+        const double *sp[NQ + CW];
+        sp[0] = x0 + i0;
+        if (NQ == 2) sp[1] = x1 + i0;
+#pragma unroll
+        for (int c = 0; c < CW; ++c) sp[NQ + c] = vbase + (int64_t)c * ld + i0;
+        const unsigned d0 = (unsigned)__cvta_generic_to_shared(stage0);
+        auto issue_next = [&](int b) {  // the next segment into stage b, then advance
+            const unsigned d = d0 + (unsigned)(b * kDfStageDoubles * sizeof(double));
+#pragma unroll
+            for (int k = 0; k < NQ + CW; ++k) {
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 512u * k), "l"(sp[k]) : "memory");
+                sp[k] += 64;
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        static_assert(kDfStages == 2, "the fast path alternates two stage buffers");
+        if (nsg > 0)
+            issue_next(0);
+        else
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        for (int j = 0; j < nsg; ++j) {
+            const int b = j & 1;
+            if (j + 1 < nsg)
+                issue_next(b ^ 1);
+            else
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            consume(stage0 + b * kDfStageDoubles, CW);
+            fold();
+        }
+    } else {
+        // general path: a ragged last row block or a narrower column group
+        // prologue: the first kDfStages - 1 segments (an empty group where there are fewer)
+#pragma unroll
+        for (int j = 0; j < kDfStages - 1; ++j) {
+            if (g0 + j < g1)
+                issue(g0 + j, j);
+            else
+                asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        for (int64_t g = g0; g < g1; ++g) {
+            const int b = (int)(g - g0) & (kDfStages - 1);
+            if (g + kDfStages - 1 < g1)
+                issue(g + kDfStages - 1, (int)(g + kDfStages - 1 - g0) & (kDfStages - 1));
+            else
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group %0;" ::"n"(kDfStages - 1) : "memory");
+            const int64_t i = r_lo + (g << 6) + 2 * lane;
+            if (i < r_hi) consume(stage0 + b * kDfStageDoubles, cw);
+            fold();
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");

@@ -344,28 +344,36 @@ k_update_df(double *V, int64_t ld, int p, int64_t n, const double *__restrict__ 
     for (int64_t pr = pr_lo + t; pr < pr_hi; pr += blockDim.x) {
         const int64_t i = 2 * pr;
         const double *vi = V + i;
-        auto issue = [&](int j) {
-            if (j < nchunks) {
-                double2 *dst = stg + (size_t)(j % kUpdStages) * kUpdChunk * kStreamThreads + t;
+        // the next chunk to copy (js), its stage (ss) and its first column's address; the
+        // stages rotate without a modulo and the columns advance by pointer increments
+        const unsigned sbase = (unsigned)__cvta_generic_to_shared(stg + t);
+        const double *colp = vi;
+        int js = 0, ss = 0;
+        auto issue = [&]() {
+            if (js < nchunks) {
+                const unsigned d = sbase + (unsigned)(ss * kUpdChunk * kStreamThreads * 16);
+                const int left = pc - js * kUpdChunk;
 #pragma unroll
-                for (int q = 0; q < kUpdChunk; ++q) {
-                    const int c = j * kUpdChunk + q;
-                    if (c < pc) {
-                        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + q * kStreamThreads);
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(vi + (int64_t)c * ld)
+                for (int q = 0; q < kUpdChunk; ++q)
+                    if (q < left)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                                     ::"r"(d + (unsigned)(q * kStreamThreads * 16)), "l"(colp + (int64_t)q * ld)
                                      : "memory");
-                    }
-                }
+                colp += (int64_t)kUpdChunk * ld;
+                if (++ss == kUpdStages) ss = 0;
+                ++js;
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
 #pragma unroll
-        for (int j = 0; j < kUpdStages - 1; ++j) issue(j);
+        for (int j = 0; j < kUpdStages - 1; ++j) issue();
         float S0 = 0.f, s0 = 0.f, S1 = 0.f, s1 = 0.f;
+        int cs = 0;  // the stage chunk j was copied into
         for (int j = 0; j < nchunks; ++j) {
-            issue(j + kUpdStages - 1);
+            issue();
             asm volatile("cp.async.wait_group %0;" ::"n"(kUpdStages - 1) : "memory");
-            const double2 *cur = stg + (size_t)(j % kUpdStages) * kUpdChunk * kStreamThreads + t;
+            const double2 *cur = stg + (size_t)cs * kUpdChunk * kStreamThreads + t;
+            if (++cs == kUpdStages) cs = 0;
 #pragma unroll
             for (int q = 0; q < kUpdChunk; ++q) {
                 const int c = j * kUpdChunk + q;
@@ -455,28 +463,36 @@ k_update_1r_df(double *V, int64_t ld, int nb, int64_t n, const double *__restric
     for (int64_t pr = pr_lo + t; pr < pr_hi; pr += blockDim.x) {
         const int64_t i = 2 * pr;
         const double *vi = V + i;
-        auto issue = [&](int j) {
-            if (j < nchunks) {
-                double2 *dst = stg + (size_t)(j % kUpdStages) * kUpdChunk * kStreamThreads + t;
+        // the next chunk to copy (js), its stage (ss) and its first column's address; the
+        // stages rotate without a modulo and the columns advance by pointer increments
+        const unsigned sbase = (unsigned)__cvta_generic_to_shared(stg + t);
+        const double *colp = vi;
+        int js = 0, ss = 0;
+        auto issue = [&]() {
+            if (js < nchunks) {
+                const unsigned d = sbase + (unsigned)(ss * kUpdChunk * kStreamThreads * 16);
+                const int left = nb - js * kUpdChunk;
 #pragma unroll
-                for (int q = 0; q < kUpdChunk; ++q) {
-                    const int c = j * kUpdChunk + q;
-                    if (c < nb) {
-                        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + q * kStreamThreads);
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(vi + (int64_t)c * ld)
+                for (int q = 0; q < kUpdChunk; ++q)
+                    if (q < left)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                                     ::"r"(d + (unsigned)(q * kStreamThreads * 16)), "l"(colp + (int64_t)q * ld)
                                      : "memory");
-                    }
-                }
+                colp += (int64_t)kUpdChunk * ld;
+                if (++ss == kUpdStages) ss = 0;
+                ++js;
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
 #pragma unroll
-        for (int j = 0; j < kUpdStages - 1; ++j) issue(j);
+        for (int j = 0; j < kUpdStages - 1; ++j) issue();
         float A0 = 0.f, a0 = 0.f, A1 = 0.f, a1 = 0.f, B0 = 0.f, b0 = 0.f, B1 = 0.f, b1 = 0.f;
+        int cs = 0;  // the stage chunk j was copied into
         for (int j = 0; j < nchunks; ++j) {
-            issue(j + kUpdStages - 1);
+            issue();
             asm volatile("cp.async.wait_group %0;" ::"n"(kUpdStages - 1) : "memory");
-            const double2 *cur = stg + (size_t)(j % kUpdStages) * kUpdChunk * kStreamThreads + t;
+            const double2 *cur = stg + (size_t)cs * kUpdChunk * kStreamThreads + t;
+            if (++cs == kUpdStages) cs = 0;
 #pragma unroll
             for (int q = 0; q < kUpdChunk; ++q) {
                 const int c = j * kUpdChunk + q;
